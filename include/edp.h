@@ -1,0 +1,188 @@
+/*
+ * edp.h -- C ABI of libedp.so, a GB300 (sm_103a) implementation of the
+ * energy minimisation of M. G. Mozerov, "Extended Dynamic Programming and
+ * Fast Multidimensional Search Algorithm for Energy Minimization in Stereo
+ * and Motion" (arXiv 1410.7922).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named `*_host` are host memory; every other pointer is device
+ *    memory on the current CUDA device.  All memory is owned by the caller;
+ *    the library never allocates.  Scratch space is the caller's workspace
+ *    `ws` of `ws_bytes` bytes (query the size with edp_workspace_size; the
+ *    pointer must be 256-byte aligned).
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and the call returns without synchronising, except where noted.
+ *  - Images are uint8 luminance, row-major [H][pitch] (pitch >= W bytes).
+ *  - Cost volumes and sums are int32, layout [H][W][Q]: the Q label costs of
+ *    one pixel are contiguous.  Labels are int32 [H][W] linear label indexes.
+ *  - Return value: EDP_OK or an EDP_ERR_* code.  Argument errors are detected
+ *    on the host before anything is enqueued.  Errors detected on the device
+ *    (a bounded inter-block wait that expired) are written to the status word
+ *    inside the workspace; read it with edp_get_device_status.
+ *
+ * Label space (Sec. 2, Eq. v_r_x_d)
+ * ----------------------------------
+ *  R label axes (1..3), Q[r] labels on axis r, axis 0 fastest:
+ *      q = q0 + Q[0] * (q1 + Q[1] * q2),   Q = Q[0] * Q[1] * Q[2].
+ *  Label coordinate q_r means the displacement  vmin[r] + step[r] * q_r
+ *  (step[r] = +1 or -1: the affine relabelling the paper allows below
+ *  Eq. v_r_x_d).  Axis 0 displaces x into I1, axis 1 displaces y into I1;
+ *  axis 2 (R = 3) displaces x into a third image I2.  Unused entries of
+ *  Q must be 1.  A stereo pair is R = 1, vmin = 0, step = -1 (label d reads
+ *  I1 at x - d).
+ *
+ * Parameters (Sec. 5: lambda, g, l1, l2, C_max, j)
+ * -------------------------------------------------
+ *  Prior, Eq. Smooth_value_t with f(u) = |u|^l1:
+ *    EDP_PRIOR_JOINT     V(q, q') = lambda * min(sum_r |q_r - q'_r|^l1, g^l1)
+ *    EDP_PRIOR_PER_AXIS  V(q, q') = sum_r lambda * min(|q_r - q'_r|^l1, g^l1)
+ *  (identical for R = 1).  This build supports l1 = 1 (truncated linear,
+ *  the LRMS of Sec. 3.2); l1 = 2 returns EDP_ERR_UNSUPPORTED.
+ *  Cost, Eq. Cost_value: C(x, q) = min(|I1(x + o(q)) - I0(x)|^l2, cmax),
+ *  cmax where x + o(q) leaves the image.
+ */
+#ifndef EDP_H
+#define EDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *edp_stream_t; /* == cudaStream_t */
+
+enum edp_status {
+    EDP_OK = 0,
+    EDP_ERR_INVALID_ARG = 1, /* null pointer, bad size, bad enum value        */
+    EDP_ERR_UNSUPPORTED = 2, /* valid by the paper but not built (e.g. l1=2)  */
+    EDP_ERR_WORKSPACE = 3,   /* ws_bytes smaller than edp_workspace_size      */
+    EDP_ERR_RANGE = 4,       /* sizes or values could overflow int32          */
+    EDP_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired            */
+    EDP_ERR_CUDA = 6         /* a CUDA runtime call failed                    */
+};
+
+enum { EDP_PRIOR_JOINT = 0, EDP_PRIOR_PER_AXIS = 1 };
+
+/* Cost models (edp_params.cost_mode):
+ *  EDP_COST_PAIR          Eq. Cost_value between I0 and I1 (R = 1 or 2).
+ *  EDP_COST_PAIR_STEREO3  R = 3: min(|I1(x+o0, y+o1) - I0|^l2
+ *                                    + |I2(x+o2, y) - I0|^l2, cmax),
+ *                         cmax if either displaced pixel leaves the image.
+ *  EDP_COST_COMPOSITE     Eq. Cost_cmp (occlusion handling with a third
+ *                         image): min(C_{I0->I1}(x, o), C_{I0->I2}(x, -o)),
+ *                         each term truncated by Eq. Cost_value (R = 1, 2). */
+enum { EDP_COST_PAIR = 0, EDP_COST_PAIR_STEREO3 = 1, EDP_COST_COMPOSITE = 2 };
+
+typedef struct {
+    int32_t R;       /* number of label axes, 1..3                      */
+    int32_t Q[3];    /* labels per axis (unused axes: 1)                */
+    int32_t vmin[3]; /* displacement of label coordinate 0 on each axis */
+    int32_t step[3]; /* +1 or -1                                        */
+} edp_label_space;
+
+typedef struct {
+    int32_t lambda;     /* prior weight, >= 0                            */
+    int32_t g;          /* truncation threshold, >= 1                    */
+    int32_t l1;         /* prior power (1 supported)                     */
+    int32_t prior_mode; /* EDP_PRIOR_*                                   */
+    int32_t l2;         /* cost power, 1 or 2                            */
+    int32_t cmax;       /* cost truncation C_max, >= 0                   */
+    int32_t cost_mode;  /* EDP_COST_*                                    */
+    int32_t iters;      /* EDP iterations j (Algorithm 1, step 3), >= 1  */
+} edp_params;
+
+/* Operations for edp_workspace_size. */
+enum {
+    EDP_OP_SCANLINE_DP = 1,
+    EDP_OP_SOLVE = 2,
+    EDP_OP_SOLVE_IMAGES = 3 /* edp_solve_images and edp_solve_images_host */
+};
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int edp_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *edp_status_string(int status);
+
+/* Bytes of workspace `op` needs for a W x H image (params->iters matters
+ * for the EDP operations).  Returns 0 for invalid arguments. */
+size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
+                          const edp_params *params);
+
+/* Process-wide launch shape of the DP kernels: rows per block and target
+ * labels per lane on one label line (0 = automatic, the default).  Used by
+ * the autotuner; results never depend on it.  Not thread-safe with
+ * concurrent solves. */
+int edp_set_tuning(int rows_per_block, int labels_per_lane);
+
+/* Cost volume (DSI), Eq. Cost_value (Algorithm 1, step 1).
+ *  I0, I1: uint8 [H][pitch]; I2: third image for EDP_COST_PAIR_STEREO3 and
+ *  EDP_COST_COMPOSITE, else NULL.  Writes C int32 [H][W][Q].
+ *  Uses params->l2, cmax, cost_mode. */
+int edp_cost_volume(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H,
+                    int pitch, const edp_label_space *space, const edp_params *params,
+                    int32_t *C, edp_stream_t stream);
+
+/* Scanline DP, Sec. 4.1: every row is an independent chain (Eq. One_d, the
+ * vertical prior set to zero).  Forward recurrence Eq. base with the
+ * boundary of Eq. DP_1D_2 (S(0) = C(0)), the min search done by the RMS
+ * (Sec. 3), optimal-choice indexes stored during the forward pass, then the
+ * backward recovery from argmin_q S(W-1, q).  Ties take the lowest label
+ * index: at the last column, and at each back-pointer.
+ *  C: int32 [H][W][Q].  labels: int32 [H][W].  row_energy: int64 [H]
+ *  (min_q S(W-1, q), the optimal chain energy), or NULL. */
+int edp_scanline_dp(const int32_t *C, int W, int H, const edp_label_space *space,
+                    const edp_params *params, int32_t *labels, int64_t *row_energy, void *ws,
+                    size_t ws_bytes, edp_stream_t stream);
+
+/* EDP, Sec. 4.2 / Algorithm 1 steps 2-5: params->iters iterations of the
+ * four scan passes P1..P4 (Eq. DP_2D_base with the data term added, D = 2,
+ * messages M(floor(S_k(x_k) / 2)), zero outside the image), then the
+ * marginal estimate S_Omega = C + sum_k M(floor(S_k(x_k) / 2)) (Eq. DP_2D_1)
+ * and its argmin (Eq. DP_2D_2), lowest label index on ties.
+ *  C: int32 [H][W][Q].  labels: int32 [H][W].  ws: >= edp_workspace_size(
+ *  EDP_OP_SOLVE, ...) bytes.  Device status word: EDP_ERR_TIMEOUT if a wait
+ *  between row bands expired (the labels are then undefined).
+ *  Returns EDP_ERR_RANGE when N * (cmax + 2 * R * lambda * g) * 2 >= 2^31
+ *  (the sums could leave int32). */
+int edp_solve(const int32_t *C, int W, int H, const edp_label_space *space,
+              const edp_params *params, int32_t *labels, void *ws, size_t ws_bytes,
+              edp_stream_t stream);
+
+/* Energy, Eq. GE_objective_function on the 4-connected grid:
+ *  out4[0] = sum_x C(x, v(x))                 (data term)
+ *  out4[1] = sum over horizontal edges V       (x, x+1)
+ *  out4[2] = sum over vertical edges V         (y, y+1)
+ *  out4[3] = out4[0] + out4[1] + out4[2].
+ *  C may be NULL (data term 0).  out4: int64 [4], device memory. */
+int edp_energy(const int32_t *C, const int32_t *labels, int W, int H,
+               const edp_label_space *space, const edp_params *params, int64_t *out4,
+               edp_stream_t stream);
+
+/* Images to labels on the device: edp_cost_volume into the workspace,
+ * edp_solve, edp_energy.  labels: int32 [H][W]; energy4: int64 [4] or NULL. */
+int edp_solve_images(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H,
+                     int pitch, const edp_label_space *space, const edp_params *params,
+                     int32_t *labels, int64_t *energy4, void *ws, size_t ws_bytes,
+                     edp_stream_t stream);
+
+/* Same as edp_solve_images with HOST images and HOST outputs: copies the
+ * images (dense [H][W]) into the workspace, runs the pipeline and copies the
+ * labels and the energy back.  Synchronises `stream` before returning.
+ * Pinned host buffers give the fastest copies. */
+int edp_solve_images_host(const uint8_t *I0_host, const uint8_t *I1_host,
+                          const uint8_t *I2_host, int W, int H, const edp_label_space *space,
+                          const edp_params *params, int32_t *labels_host,
+                          int64_t *energy4_host, void *ws, size_t ws_bytes, edp_stream_t stream);
+
+/* Reads the device status word of a workspace used by edp_solve /
+ * edp_solve_images / edp_scanline_dp.  Synchronises `stream`. */
+int edp_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EDP_H */

@@ -1,0 +1,499 @@
+// api.cu -- the extern "C" entry points of libedp.so (see include/edp.h):
+// argument validation, workspace layout, launch configuration and the pass
+// schedule of Algorithm 1.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "edp.h"
+#include "kernels.h"
+
+using namespace edp;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kHeader = 256;  // status word + reserved
+constexpr int kMaxSmem = 227 * 1024;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int g_tune_rb = 0;       // rows per block override (0 = automatic)
+int g_tune_e = 0;        // labels per lane target override (0 = automatic)
+
+struct Geometry {
+    int R;       // label axes after dropping axes with one label
+    int Qr[3];   // their sizes
+    int Q;       // total labels
+};
+
+// Validation shared by every entry point.  Axes with a single label carry no
+// prior term and are dropped for the DP kernels (the linear label index is
+// unchanged by that).
+int check_space(const edp_label_space *s, Geometry *g) {
+    if (!s) return EDP_ERR_INVALID_ARG;
+    if (s->R < 1 || s->R > 3) return EDP_ERR_INVALID_ARG;
+    long long Q = 1;
+    g->R = 0;
+    for (int r = 0; r < 3; ++r) {
+        if (s->Q[r] < 1) return EDP_ERR_INVALID_ARG;
+        if (r >= s->R && s->Q[r] != 1) return EDP_ERR_INVALID_ARG;
+        if (r < s->R && s->step[r] != 1 && s->step[r] != -1) return EDP_ERR_INVALID_ARG;
+        Q *= s->Q[r];
+        if (s->Q[r] > 1) g->Qr[g->R++] = s->Q[r];
+    }
+    if (Q > (1 << 20)) return EDP_ERR_UNSUPPORTED;
+    if (g->R == 0) {
+        g->R = 1;
+        g->Qr[0] = 1;
+    }
+    for (int r = g->R; r < 3; ++r) g->Qr[r] = 1;
+    g->Q = (int)Q;
+    return EDP_OK;
+}
+
+int check_prior(const edp_params *p) {
+    if (!p) return EDP_ERR_INVALID_ARG;
+    if (p->lambda < 0 || p->g < 1 || p->cmax < 0) return EDP_ERR_INVALID_ARG;
+    if (p->l1 != 1 && p->l1 != 2) return EDP_ERR_INVALID_ARG;
+    if (p->prior_mode != EDP_PRIOR_JOINT && p->prior_mode != EDP_PRIOR_PER_AXIS) return EDP_ERR_INVALID_ARG;
+    return EDP_OK;
+}
+
+long long cap_value(const edp_params *p) {
+    const long long gg = p->l1 == 1 ? p->g : (long long)p->g * p->g;
+    return (long long)p->lambda * gg;
+}
+
+int pow2ceil(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Lanes per line G and labels per lane E for a line of L labels.
+bool choose_axis(int L, int etarget, AxisCfg *a) {
+    int G = pow2ceil((L + etarget - 1) / etarget);
+    if (G > 32) G = 32;
+    int E = (L + G - 1) / G;
+    if (E > kEM) return false;
+    a->L = L;
+    a->G = G;
+    a->E = E;
+    return true;
+}
+
+int em_for(int E) {
+    if (E <= 2) return 2;
+    if (E <= 4) return 4;
+    if (E <= 8) return 8;
+    return 16;
+}
+
+struct DpConfig {
+    AxisCfg ax[3];
+    int em;
+    int RB;
+    int threads;
+    size_t smem;
+};
+
+// smem bytes of one EDP pass block / scanline block
+size_t pass_smem(int RB, int Q, int R) {
+    // argk, gmin, msgA, ringB[2], staging[2][3], tmpA/tmpB (R >= 2)
+    return (size_t)RB * 2 * 8 + (size_t)RB * 4 * 4 + (size_t)RB * Q * 4 * (R >= 2 ? 11 : 9);
+}
+size_t scan_smem(int RB, int Q, int R, int W, int ptr_bytes, bool ptr_smem) {
+    // gkey, tmpk (R >= 2), S, staging[2]
+    size_t s = (size_t)RB * 2 * 8 + (size_t)RB * Q * (R >= 2 ? 8 : 0) + (size_t)RB * Q * 4 * 3;
+    if (ptr_smem) s += (size_t)RB * W * Q * ptr_bytes;
+    return s;
+}
+
+int configure(const Geometry &g, int H, bool scan, int W, int ptr_bytes, bool *ptr_smem, DpConfig *c) {
+    const int etarget = g_tune_e > 0 ? g_tune_e : (g.R == 1 ? 4 : 5);
+    int stride = 1;
+    int maxE = 1;
+    for (int r = 0; r < g.R; ++r) {
+        if (g.Qr[r] > kMaxLine) return EDP_ERR_UNSUPPORTED;
+        if (!choose_axis(g.Qr[r], etarget, &c->ax[r])) return EDP_ERR_UNSUPPORTED;
+        c->ax[r].nlines = g.Q / g.Qr[r];
+        c->ax[r].stride = stride;
+        stride *= g.Qr[r];
+        maxE = std::max(maxE, c->ax[r].E);
+    }
+    for (int r = g.R; r < 3; ++r) c->ax[r] = AxisCfg{1, 1, 1, g.Q, stride};
+    c->em = em_for(maxE);
+    const int gpw0 = 32 / c->ax[0].G;
+    auto threads_for = [&](int RB) { return ((RB * c->ax[0].nlines + gpw0 - 1) / gpw0) * 32; };
+    int RB;
+    if (g_tune_rb > 0) {
+        RB = g_tune_rb;
+    } else {
+        const int per_row = threads_for(1);
+        RB = std::max(1, 256 / per_row);
+    }
+    RB = std::min(RB, H);
+    RB = std::max(RB, 1);
+    bool psm = false;
+    if (scan) {
+        psm = scan_smem(RB, g.Q, g.R, W, ptr_bytes, true) <= (size_t)kMaxSmem / 2;
+        while (RB > 1 && scan_smem(RB, g.Q, g.R, W, ptr_bytes, psm) > (size_t)kMaxSmem) --RB;
+        c->smem = scan_smem(RB, g.Q, g.R, W, ptr_bytes, psm);
+    } else {
+        while (RB > 1 && pass_smem(RB, g.Q, g.R) > (size_t)kMaxSmem) --RB;
+        c->smem = pass_smem(RB, g.Q, g.R);
+    }
+    if (c->smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
+    c->RB = RB;
+    c->threads = std::min(kMaxThreads, std::max(32, threads_for(RB)));
+    if (ptr_smem) *ptr_smem = psm;
+    return EDP_OK;
+}
+
+int ptr_bytes_for(int Q) { return Q <= 256 ? 1 : (Q <= 65536 ? 2 : 4); }
+
+// Workspace of edp_solve: header | progress [4*iters][H] | counters [4*iters] | M[4][N*Q]
+struct SolveLayout {
+    size_t progress, counters, msg[4], end;
+};
+SolveLayout solve_layout(int W, int H, int Q, int iters) {
+    SolveLayout L;
+    const size_t npass = 4 * (size_t)iters;
+    L.progress = kHeader;
+    L.counters = align_up(L.progress + npass * H * 4);
+    size_t off = align_up(L.counters + npass * 4);
+    for (int k = 0; k < 4; ++k) {
+        L.msg[k] = off;
+        off = align_up(off + (size_t)W * H * Q * 4);
+    }
+    L.end = off;
+    return L;
+}
+
+struct ImagesLayout {
+    SolveLayout s;
+    size_t C, img[3], labels, energy, end;
+};
+ImagesLayout images_layout(int W, int H, int Q, int iters) {
+    ImagesLayout L;
+    L.s = solve_layout(W, H, Q, iters);
+    L.C = L.s.end;
+    size_t off = align_up(L.C + (size_t)W * H * Q * 4);
+    for (int k = 0; k < 3; ++k) {
+        L.img[k] = off;
+        off = align_up(off + (size_t)W * H);
+    }
+    L.labels = off;
+    off = align_up(off + (size_t)W * H * 4);
+    L.energy = off;
+    L.end = align_up(off + 4 * 8);
+    return L;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? EDP_OK : EDP_ERR_CUDA; }
+
+int check_range(int W, int H, const Geometry &g, const edp_params *p) {
+    const long long N = (long long)W * H;
+    if (p->lambda > (1 << 20)) return EDP_ERR_RANGE;
+    if (cap_value(p) * g.R > (1 << 28)) return EDP_ERR_RANGE;
+    const long long bound = N * (p->cmax + 2LL * g.R * cap_value(p)) * 2;
+    if (bound >= (1LL << 31)) return EDP_ERR_RANGE;
+    return EDP_OK;
+}
+
+int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
+              unsigned char *ws, cudaStream_t st) {
+    DpConfig cfg;
+    int rc = configure(g, H, false, W, 0, nullptr, &cfg);
+    if (rc) return rc;
+    const SolveLayout L = solve_layout(W, H, g.Q, p->iters);
+    rc = cuda_status(cudaMemsetAsync(ws, 0, L.msg[0], st));
+    if (rc) return rc;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.C = C;
+    for (int k = 0; k < 4; ++k) a.M[k] = reinterpret_cast<int *>(ws + L.msg[k]);
+    a.labels = labels;
+    a.status = reinterpret_cast<int *>(ws);
+    a.W = W;
+    a.H = H;
+    a.Q = g.Q;
+    a.R = g.R;
+    for (int r = 0; r < 3; ++r) a.ax[r] = cfg.ax[r];
+    a.lam = p->lambda;
+    a.capv = (int)cap_value(p);
+    a.mode = p->prior_mode;
+    a.RB = cfg.RB;
+    a.nbands = (H + cfg.RB - 1) / cfg.RB;
+    occ = edp_pass_occupancy(cfg.em, cfg.threads, cfg.smem);
+    a.grid = std::max(1, std::min(a.nbands, std::max(1, occ) * sms));
+    a.spin_limit = 2000000;
+    for (int it = 0; it < p->iters; ++it) {
+        const bool last_it = (it == p->iters - 1);
+        for (int pass = 0; pass < 4; ++pass) {
+            const int slot = it * 4 + pass;
+            a.pass = pass;
+            a.progress = reinterpret_cast<unsigned *>(ws + L.progress) + (size_t)slot * H;
+            a.band_counter = reinterpret_cast<unsigned *>(ws + L.counters) + slot;
+            // which old message arrays hold data yet (zero before first written)
+            a.read_c = (pass == 0) ? (it > 0) : 1;
+            a.read_d = (pass <= 1) ? (it > 0) : 1;
+            // which outputs a later pass reads (the others are overwritten first)
+            a.write_a = (pass == 3) ? !last_it : 1;
+            a.write_b = (pass == 1) ? 1 : (pass == 3 ? !last_it : 0);
+            a.final_ = (pass == 3 && last_it);
+            if (launch_edp_pass(a, cfg.em, cfg.threads, cfg.smem, st)) return EDP_ERR_CUDA;
+        }
+    }
+    return EDP_OK;
+}
+
+int check_images(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H, int pitch,
+                 const edp_label_space *s, const edp_params *p) {
+    if (!I0 || !I1 || W < 1 || H < 1 || pitch < W) return EDP_ERR_INVALID_ARG;
+    if (!s || !p) return EDP_ERR_INVALID_ARG;
+    if (p->l2 != 1 && p->l2 != 2) return EDP_ERR_INVALID_ARG;
+    if (p->cmax < 0) return EDP_ERR_INVALID_ARG;
+    switch (p->cost_mode) {
+    case EDP_COST_PAIR:
+        if (s->R > 2) return EDP_ERR_INVALID_ARG;
+        break;
+    case EDP_COST_PAIR_STEREO3:
+        if (s->R != 3 || !I2) return EDP_ERR_INVALID_ARG;
+        break;
+    case EDP_COST_COMPOSITE:
+        if (s->R > 2 || !I2) return EDP_ERR_INVALID_ARG;
+        break;
+    default:
+        return EDP_ERR_INVALID_ARG;
+    }
+    if (p->l2 == 2 && p->cmax > (1 << 24)) return EDP_ERR_RANGE;
+    return EDP_OK;
+}
+
+int run_cost(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H, int pitch,
+             const edp_label_space *s, const edp_params *p, int Q, int32_t *C, cudaStream_t st) {
+    CostArgs a;
+    memset(&a, 0, sizeof a);
+    a.I0 = I0;
+    a.I1 = I1;
+    a.I2 = I2;
+    a.W = W;
+    a.H = H;
+    a.pitch = pitch;
+    a.R = s->R;
+    a.Q = Q;
+    a.Q0 = s->Q[0];
+    a.Q1 = s->Q[1];
+    a.Q2 = s->Q[2];
+    for (int r = 0; r < 3; ++r) {
+        a.vmin[r] = s->vmin[r];
+        a.step[r] = r < s->R ? s->step[r] : 1;
+    }
+    a.l2 = p->l2;
+    a.cmax = p->cmax;
+    a.mode = p->cost_mode;
+    a.C = C;
+    return launch_cost(a, st) ? EDP_ERR_CUDA : EDP_OK;
+}
+
+int run_energy(const int32_t *C, const int32_t *labels, int W, int H, const edp_label_space *s,
+               const edp_params *p, int Q, int64_t *out4, cudaStream_t st) {
+    EnergyArgs a;
+    memset(&a, 0, sizeof a);
+    a.C = C;
+    a.labels = labels;
+    a.W = W;
+    a.H = H;
+    a.Q = Q;
+    a.R = s->R;
+    a.Q0 = s->Q[0];
+    a.Q1 = s->Q[1];
+    a.lam = p->lambda;
+    a.g = p->g;
+    a.l1 = p->l1;
+    a.mode = p->prior_mode;
+    a.out4 = reinterpret_cast<long long *>(out4);
+    return launch_energy(a, st) ? EDP_ERR_CUDA : EDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int edp_version(void) { return 10000; }
+
+const char *edp_status_string(int status) {
+    switch (status) {
+    case EDP_OK: return "EDP_OK";
+    case EDP_ERR_INVALID_ARG: return "EDP_ERR_INVALID_ARG";
+    case EDP_ERR_UNSUPPORTED: return "EDP_ERR_UNSUPPORTED";
+    case EDP_ERR_WORKSPACE: return "EDP_ERR_WORKSPACE";
+    case EDP_ERR_RANGE: return "EDP_ERR_RANGE";
+    case EDP_ERR_TIMEOUT: return "EDP_ERR_TIMEOUT";
+    case EDP_ERR_CUDA: return "EDP_ERR_CUDA";
+    default: return "EDP_ERR_UNKNOWN";
+    }
+}
+
+int edp_set_tuning(int rows_per_block, int labels_per_lane) {
+    if (rows_per_block < 0 || labels_per_lane < 0 || labels_per_lane > kEM) return EDP_ERR_INVALID_ARG;
+    g_tune_rb = rows_per_block;
+    g_tune_e = labels_per_lane;
+    return EDP_OK;
+}
+
+size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space, const edp_params *params) {
+    Geometry g;
+    if (W < 1 || H < 1 || check_space(space, &g) || !params) return 0;
+    const int iters = std::max(1, params->iters);
+    switch (op) {
+    case EDP_OP_SCANLINE_DP:
+        return align_up(kHeader + (size_t)W * H * g.Q * ptr_bytes_for(g.Q));
+    case EDP_OP_SOLVE:
+        return solve_layout(W, H, g.Q, iters).end;
+    case EDP_OP_SOLVE_IMAGES:
+        return images_layout(W, H, g.Q, iters).end;
+    default:
+        return 0;
+    }
+}
+
+int edp_cost_volume(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H, int pitch,
+                    const edp_label_space *space, const edp_params *params, int32_t *C, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_images(I0, I1, I2, W, H, pitch, space, params))) return rc;
+    if (!C) return EDP_ERR_INVALID_ARG;
+    return run_cost(I0, I1, I2, W, H, pitch, space, params, g.Q, C, (cudaStream_t)stream);
+}
+
+int edp_scanline_dp(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,
+                    int32_t *labels, int64_t *row_energy, void *ws, size_t ws_bytes, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if (!C || !labels || !ws || W < 1 || H < 1) return EDP_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
+    if (params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    if (ws_bytes < edp_workspace_size(EDP_OP_SCANLINE_DP, W, H, space, params)) return EDP_ERR_WORKSPACE;
+    // S values along a row stay below W * (cmax + R * lambda * g)
+    if ((long long)W * (params->cmax + (long long)g.R * cap_value(params)) >= (1LL << 29)) return EDP_ERR_RANGE;
+    if (params->lambda > (1 << 20)) return EDP_ERR_RANGE;
+    const int pb = ptr_bytes_for(g.Q);
+    DpConfig cfg;
+    bool psm = false;
+    if ((rc = configure(g, H, true, W, pb, &psm, &cfg))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = cuda_status(cudaMemsetAsync(ws, 0, kHeader, st)))) return rc;
+    ScanArgs a;
+    memset(&a, 0, sizeof a);
+    a.C = C;
+    a.labels = labels;
+    a.row_energy = reinterpret_cast<long long *>(row_energy);
+    a.ptr = static_cast<unsigned char *>(ws) + kHeader;
+    a.ptr_bytes = pb;
+    a.ptr_in_smem = psm;
+    a.W = W;
+    a.H = H;
+    a.Q = g.Q;
+    a.R = g.R;
+    for (int r = 0; r < 3; ++r) a.ax[r] = cfg.ax[r];
+    a.lam = params->lambda;
+    a.capv = (int)cap_value(params);
+    a.mode = params->prior_mode;
+    a.RB = cfg.RB;
+    const int grid = (H + cfg.RB - 1) / cfg.RB;
+    return launch_scanline(a, cfg.em, cfg.threads, cfg.smem, grid, st) ? EDP_ERR_CUDA : EDP_OK;
+}
+
+int edp_solve(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,
+              int32_t *labels, void *ws, size_t ws_bytes, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if (!C || !labels || !ws || W < 1 || H < 1 || params->iters < 1) return EDP_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
+    if (params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    if (ws_bytes < edp_workspace_size(EDP_OP_SOLVE, W, H, space, params)) return EDP_ERR_WORKSPACE;
+    if ((rc = check_range(W, H, g, params))) return rc;
+    return run_solve(C, W, H, g, params, labels, static_cast<unsigned char *>(ws), (cudaStream_t)stream);
+}
+
+int edp_energy(const int32_t *C, const int32_t *labels, int W, int H, const edp_label_space *space,
+               const edp_params *params, int64_t *out4, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if (!labels || !out4 || W < 1 || H < 1) return EDP_ERR_INVALID_ARG;
+    return run_energy(C, labels, W, H, space, params, g.Q, out4, (cudaStream_t)stream);
+}
+
+int edp_solve_images(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H, int pitch,
+                     const edp_label_space *space, const edp_params *params, int32_t *labels, int64_t *energy4,
+                     void *ws, size_t ws_bytes, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if ((rc = check_images(I0, I1, I2, W, H, pitch, space, params))) return rc;
+    if (!labels || !ws || params->iters < 1) return EDP_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
+    if (params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    if (ws_bytes < edp_workspace_size(EDP_OP_SOLVE_IMAGES, W, H, space, params)) return EDP_ERR_WORKSPACE;
+    if ((rc = check_range(W, H, g, params))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    const ImagesLayout L = images_layout(W, H, g.Q, params->iters);
+    int32_t *C = reinterpret_cast<int32_t *>(w + L.C);
+    if ((rc = run_cost(I0, I1, I2, W, H, pitch, space, params, g.Q, C, st))) return rc;
+    if ((rc = run_solve(C, W, H, g, params, labels, w, st))) return rc;
+    if (energy4) rc = run_energy(C, labels, W, H, space, params, g.Q, energy4, st);
+    return rc;
+}
+
+int edp_solve_images_host(const uint8_t *I0_host, const uint8_t *I1_host, const uint8_t *I2_host, int W,
+                          int H, const edp_label_space *space, const edp_params *params, int32_t *labels_host,
+                          int64_t *energy4_host, void *ws, size_t ws_bytes, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if (!I0_host || !I1_host || !labels_host || !ws || W < 1 || H < 1 || !params) return EDP_ERR_INVALID_ARG;
+    if (ws_bytes < edp_workspace_size(EDP_OP_SOLVE_IMAGES, W, H, space, params)) return EDP_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    const ImagesLayout L = images_layout(W, H, g.Q, std::max(1, params->iters));
+    const size_t npix = (size_t)W * H;
+    const uint8_t *hin[3] = {I0_host, I1_host, I2_host};
+    for (int k = 0; k < 3; ++k)
+        if (hin[k] && (rc = cuda_status(cudaMemcpyAsync(w + L.img[k], hin[k], npix, cudaMemcpyHostToDevice, st))))
+            return rc;
+    int32_t *labels = reinterpret_cast<int32_t *>(w + L.labels);
+    int64_t *energy = reinterpret_cast<int64_t *>(w + L.energy);
+    rc = edp_solve_images(w + L.img[0], w + L.img[1], I2_host ? w + L.img[2] : nullptr, W, H, W, space, params,
+                          labels, energy, ws, ws_bytes, stream);
+    if (rc) return rc;
+    if ((rc = cuda_status(cudaMemcpyAsync(labels_host, labels, npix * 4, cudaMemcpyDeviceToHost, st)))) return rc;
+    if (energy4_host &&
+        (rc = cuda_status(cudaMemcpyAsync(energy4_host, energy, 4 * 8, cudaMemcpyDeviceToHost, st))))
+        return rc;
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+int edp_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stream_t stream) {
+    if (!ws || !status || ws_bytes < kHeader) return EDP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = cuda_status(cudaStreamSynchronize(st));
+    if (rc) return rc;
+    return cuda_status(cudaMemcpy(status, ws, sizeof(int), cudaMemcpyDeviceToHost));
+}
+
+}  // extern "C"

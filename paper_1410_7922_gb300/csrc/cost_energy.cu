@@ -1,0 +1,125 @@
+// cost_energy.cu -- cost volume (Eq. Cost_value, Eq. Cost_cmp) and energy
+// (Eq. GE_objective_function) kernels, sm_103a.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace edp {
+
+__device__ __forceinline__ int cost_term(const uint8_t *I, const uint8_t *I0, int W, int H, int pitch,
+                                         int x, int y, int dx, int dy, int l2, bool &oob) {
+    const int xs = x + dx, ys = y + dy;
+    oob = (xs < 0 || xs >= W || ys < 0 || ys >= H);
+    if (oob) return 0;
+    const int d = (int)I[(size_t)ys * pitch + xs] - (int)I0[(size_t)y * pitch + x];
+    const int a = d < 0 ? -d : d;
+    return l2 == 1 ? a : a * a;
+}
+
+// One thread per (pixel, 4 consecutive labels): the label dimension is the
+// fastest, so consecutive threads write consecutive 16-byte chunks.
+__global__ void cost_kernel(CostArgs A) {
+    const long long n = (long long)A.W * A.H * A.Q;
+    const long long stride = (long long)gridDim.x * blockDim.x * 4;
+    for (long long e0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; e0 < n; e0 += stride) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long e = e0 + u;
+            if (e >= n) break;
+            const long long pix = e / A.Q;
+            const int q = (int)(e - pix * A.Q);
+            const int x = (int)(pix % A.W), y = (int)(pix / A.W);
+            const int q0 = q % A.Q0, q1 = (q / A.Q0) % A.Q1, q2 = q / (A.Q0 * A.Q1);
+            const int o0 = A.vmin[0] + A.step[0] * q0;
+            const int o1 = A.R >= 2 ? A.vmin[1] + A.step[1] * q1 : 0;
+            const int o2 = A.R >= 3 ? A.vmin[2] + A.step[2] * q2 : 0;
+            int c;
+            bool oob1, oob2;
+            if (A.mode == 0) {  // pair
+                c = cost_term(A.I1, A.I0, A.W, A.H, A.pitch, x, y, o0, o1, A.l2, oob1);
+                c = oob1 ? A.cmax : min(c, A.cmax);
+            } else if (A.mode == 1) {  // pair + stereo partner on axis 2
+                const int c1 = cost_term(A.I1, A.I0, A.W, A.H, A.pitch, x, y, o0, o1, A.l2, oob1);
+                const int c2 = cost_term(A.I2, A.I0, A.W, A.H, A.pitch, x, y, o2, 0, A.l2, oob2);
+                c = (oob1 || oob2) ? A.cmax : min(c1 + c2, A.cmax);
+            } else {  // composite: C_{I0->I1}(x, o) ^ C_{I0->I2}(x, -o)
+                int c1 = cost_term(A.I1, A.I0, A.W, A.H, A.pitch, x, y, o0, o1, A.l2, oob1);
+                int c2 = cost_term(A.I2, A.I0, A.W, A.H, A.pitch, x, y, -o0, -o1, A.l2, oob2);
+                c1 = oob1 ? A.cmax : min(c1, A.cmax);
+                c2 = oob2 ? A.cmax : min(c2, A.cmax);
+                c = min(c1, c2);
+            }
+            A.C[e] = c;
+        }
+    }
+}
+
+int launch_cost(const CostArgs &a, cudaStream_t st) {
+    const long long n = (long long)a.W * a.H * a.Q;
+    const int threads = 256;
+    long long blocks = (n + 4LL * threads - 1) / (4LL * threads);
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    if (blocks < 1) blocks = 1;
+    cost_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+// V(q, q') of Eq. Smooth_value_t (l1 = 1 or 2).
+__device__ __forceinline__ long long prior_v(int a, int b, const EnergyArgs &A) {
+    const int a0 = a % A.Q0, b0 = b % A.Q0;
+    const int a1 = (a / A.Q0) % A.Q1, b1 = (b / A.Q0) % A.Q1;
+    const int a2 = a / (A.Q0 * A.Q1), b2 = b / (A.Q0 * A.Q1);
+    int d[3] = {abs(a0 - b0), abs(a1 - b1), abs(a2 - b2)};
+    const long long cap = A.l1 == 1 ? A.g : (long long)A.g * A.g;
+    if (A.mode == 0) {
+        long long f = 0;
+        for (int r = 0; r < 3; ++r) f += A.l1 == 1 ? d[r] : (long long)d[r] * d[r];
+        return (long long)A.lam * min(f, cap);
+    }
+    long long v = 0;
+    for (int r = 0; r < 3; ++r) {
+        const long long f = A.l1 == 1 ? d[r] : (long long)d[r] * d[r];
+        v += (long long)A.lam * min(f, cap);
+    }
+    return v;
+}
+
+__global__ void energy_kernel(EnergyArgs A) {
+    long long e[3] = {0, 0, 0};
+    const long long n = (long long)A.W * A.H;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % A.W), y = (int)(i / A.W);
+        // labels outside [0, Q) are clamped so that every read stays in bounds
+        const int l = min(max(A.labels[i], 0), A.Q - 1);
+        if (A.C) e[0] += A.C[i * A.Q + l];
+        if (x + 1 < A.W) e[1] += prior_v(l, min(max(A.labels[i + 1], 0), A.Q - 1), A);
+        if (y + 1 < A.H) e[2] += prior_v(l, min(max(A.labels[i + A.W], 0), A.Q - 1), A);
+    }
+    __shared__ long long red[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < 3; ++k) {
+        long long v = e[k];
+        for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        long long s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        atomicAdd(reinterpret_cast<unsigned long long *>(A.out4 + threadIdx.x), (unsigned long long)s);
+        atomicAdd(reinterpret_cast<unsigned long long *>(A.out4 + 3), (unsigned long long)s);
+    }
+}
+
+int launch_energy(const EnergyArgs &a, cudaStream_t st) {
+    const long long n = (long long)a.W * a.H;
+    const int threads = 256;
+    long long blocks = (n + threads - 1) / threads;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    if (blocks < 1) blocks = 1;
+    if (cudaMemsetAsync(a.out4, 0, 4 * sizeof(long long), st) != cudaSuccess) return -2;
+    energy_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace edp

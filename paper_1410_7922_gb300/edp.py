@@ -1,0 +1,276 @@
+"""Thin Python binding of libedp.so (the C ABI in include/edp.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch tensors (torch provides device memory and
+streams); the functions take the same names as the C entry points without the
+``edp_`` prefix.  There is no fallback: if the library cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libedp.so")
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_RANGE, ERR_TIMEOUT, ERR_CUDA = range(7)
+PRIOR = {"joint": 0, "per_axis": 1}
+COST = {"pair": 0, "pair_stereo3": 1, "composite": 2}
+OP_SCANLINE_DP, OP_SOLVE, OP_SOLVE_IMAGES = 1, 2, 3
+
+
+class EdpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+        self.code = code
+
+
+class LabelSpace(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int32), ("Q", ctypes.c_int32 * 3), ("vmin", ctypes.c_int32 * 3),
+                ("step", ctypes.c_int32 * 3)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_int32), ("g", ctypes.c_int32), ("l1", ctypes.c_int32),
+                ("prior_mode", ctypes.c_int32), ("l2", ctypes.c_int32), ("cmax", ctypes.c_int32),
+                ("cost_mode", ctypes.c_int32), ("iters", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libedp.so (built by paper_1410_7922_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_1410_7922_gb300/build.py "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    LS, PR = ctypes.POINTER(LabelSpace), ctypes.POINTER(Params)
+    sig = {
+        "edp_version": ([], I),
+        "edp_status_string": ([I], ctypes.c_char_p),
+        "edp_workspace_size": ([I, I, I, LS, PR], SZ),
+        "edp_set_tuning": ([I, I], I),
+        "edp_cost_volume": ([P, P, P, I, I, I, LS, PR, P, P], I),
+        "edp_scanline_dp": ([P, I, I, LS, PR, P, P, P, SZ, P], I),
+        "edp_solve": ([P, I, I, LS, PR, P, P, SZ, P], I),
+        "edp_energy": ([P, P, I, I, LS, PR, P, P], I),
+        "edp_solve_images": ([P, P, P, I, I, I, LS, PR, P, P, P, SZ, P], I),
+        "edp_solve_images_host": ([P, P, P, I, I, LS, PR, P, P, P, SZ, P], I),
+        "edp_get_device_status": ([P, SZ, ctypes.POINTER(I), P], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return ["edp_version", "edp_status_string", "edp_workspace_size", "edp_set_tuning",
+            "edp_cost_volume", "edp_scanline_dp", "edp_solve", "edp_energy", "edp_solve_images",
+            "edp_solve_images_host", "edp_get_device_status"]
+
+
+def status_string(code: int) -> str:
+    return load().edp_status_string(int(code)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != OK:
+        raise EdpError(rc, what)
+
+
+def label_space(space: dict) -> LabelSpace:
+    s = LabelSpace()
+    s.R = int(space["R"])
+    Q = list(space["Q"]) + [1] * 3
+    vmin = list(space.get("vmin", (0, 0, 0))) + [0] * 3
+    step = list(space.get("step", (1, 1, 1))) + [1] * 3
+    for r in range(3):
+        s.Q[r] = int(Q[r]) if r < s.R else 1
+        s.vmin[r] = int(vmin[r])
+        s.step[r] = int(step[r])
+    return s
+
+
+def params(prior: dict, l2: int = 1, cmax: int = 20, cost_mode: str = "pair", iters: int = 1) -> Params:
+    p = Params()
+    p.lam = int(prior["lam"])
+    p.g = int(prior["g"])
+    p.l1 = int(prior.get("l1", 1))
+    p.prior_mode = PRIOR[prior.get("mode", "joint")]
+    p.l2 = int(l2)
+    p.cmax = int(cmax)
+    p.cost_mode = COST[cost_mode]
+    p.iters = int(iters)
+    return p
+
+
+def n_labels(space: dict) -> int:
+    q = 1
+    for r in range(int(space["R"])):
+        q *= int(space["Q"][r])
+    return q
+
+
+def _dev(t: torch.Tensor | None, dtype, name: str):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def version() -> int:
+    return load().edp_version()
+
+
+def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0) -> None:
+    _check(load().edp_set_tuning(int(rows_per_block), int(labels_per_lane)), "set_tuning")
+
+
+def workspace_size(op: int, W: int, H: int, space: dict, prior: dict, iters: int = 1, **kw) -> int:
+    ls, pr = label_space(space), params(prior, iters=iters, **kw)
+    n = load().edp_workspace_size(int(op), int(W), int(H), ctypes.byref(ls), ctypes.byref(pr))
+    if n == 0:
+        raise EdpError(ERR_INVALID_ARG, "workspace_size")
+    return int(n)
+
+
+def workspace(op: int, W: int, H: int, space: dict, prior: dict, iters: int = 1, device="cuda", **kw):
+    """A device workspace tensor of the right size (256-byte aligned)."""
+    n = workspace_size(op, W, H, space, prior, iters, **kw)
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def cost_volume(I0, I1, I2, space: dict, l2: int, cmax: int, cost_mode: str = "pair", out=None, stream=None):
+    """edp_cost_volume: uint8 [H][W] images -> int32 [H][W][Q]."""
+    H, W = I0.shape
+    if out is None:
+        out = torch.empty((H, W, n_labels(space)), dtype=torch.int32, device=I0.device)
+    ls = label_space(space)
+    pr = params({"lam": 0, "g": 1}, l2=l2, cmax=cmax, cost_mode=cost_mode)
+    rc = load().edp_cost_volume(_dev(I0, torch.uint8, "I0"), _dev(I1, torch.uint8, "I1"),
+                                _dev(I2, torch.uint8, "I2"), W, H, I0.stride(0), ctypes.byref(ls),
+                                ctypes.byref(pr), _dev(out, torch.int32, "C"), _stream(stream))
+    _check(rc, "cost_volume")
+    return out
+
+
+def scanline_dp(C, space: dict, prior: dict, ws=None, labels=None, row_energy=None, stream=None):
+    """edp_scanline_dp: returns (labels int32 [H][W], row_energy int64 [H])."""
+    H, W, _ = C.shape
+    if ws is None:
+        ws = workspace(OP_SCANLINE_DP, W, H, space, prior, device=C.device)
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=C.device)
+    if row_energy is None:
+        row_energy = torch.empty(H, dtype=torch.int64, device=C.device)
+    ls, pr = label_space(space), params(prior)
+    rc = load().edp_scanline_dp(_dev(C, torch.int32, "C"), W, H, ctypes.byref(ls), ctypes.byref(pr),
+                                _dev(labels, torch.int32, "labels"), _dev(row_energy, torch.int64, "row_energy"),
+                                _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(rc, "scanline_dp")
+    return labels, row_energy
+
+
+def solve(C, space: dict, prior: dict, iters: int = 1, ws=None, labels=None, stream=None):
+    """edp_solve (Algorithm 1): labels int32 [H][W]."""
+    H, W, _ = C.shape
+    if ws is None:
+        ws = workspace(OP_SOLVE, W, H, space, prior, iters, device=C.device)
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=C.device)
+    ls, pr = label_space(space), params(prior, iters=iters)
+    rc = load().edp_solve(_dev(C, torch.int32, "C"), W, H, ctypes.byref(ls), ctypes.byref(pr),
+                          _dev(labels, torch.int32, "labels"), _dev(ws, torch.uint8, "ws"), ws.numel(),
+                          _stream(stream))
+    _check(rc, "solve")
+    return labels
+
+
+def energy(C, labels, space: dict, prior: dict, out=None, stream=None):
+    """edp_energy: int64 [4] = (data, smooth_h, smooth_v, total) on the device."""
+    H, W = labels.shape
+    if out is None:
+        out = torch.empty(4, dtype=torch.int64, device=labels.device)
+    ls, pr = label_space(space), params(prior)
+    rc = load().edp_energy(_dev(C, torch.int32, "C"), _dev(labels, torch.int32, "labels"), W, H,
+                           ctypes.byref(ls), ctypes.byref(pr), _dev(out, torch.int64, "out4"), _stream(stream))
+    _check(rc, "energy")
+    return out
+
+
+def solve_images(I0, I1, I2, space: dict, prior: dict, l2: int, cmax: int, cost_mode: str = "pair",
+                 iters: int = 1, ws=None, labels=None, energy4=None, stream=None):
+    """edp_solve_images: device images -> (labels, energy4)."""
+    H, W = I0.shape
+    if ws is None:
+        ws = workspace(OP_SOLVE_IMAGES, W, H, space, prior, iters, device=I0.device)
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=I0.device)
+    if energy4 is None:
+        energy4 = torch.empty(4, dtype=torch.int64, device=I0.device)
+    ls = label_space(space)
+    pr = params(prior, l2=l2, cmax=cmax, cost_mode=cost_mode, iters=iters)
+    rc = load().edp_solve_images(_dev(I0, torch.uint8, "I0"), _dev(I1, torch.uint8, "I1"),
+                                 _dev(I2, torch.uint8, "I2"), W, H, I0.stride(0), ctypes.byref(ls),
+                                 ctypes.byref(pr), _dev(labels, torch.int32, "labels"),
+                                 _dev(energy4, torch.int64, "energy4"), _dev(ws, torch.uint8, "ws"),
+                                 ws.numel(), _stream(stream))
+    _check(rc, "solve_images")
+    return labels, energy4
+
+
+def solve_images_host(I0, I1, I2, space: dict, prior: dict, l2: int, cmax: int, ws, cost_mode: str = "pair",
+                      iters: int = 1, labels_out: np.ndarray | None = None, energy_out: np.ndarray | None = None,
+                      stream=None):
+    """edp_solve_images_host: host uint8 images (numpy or pinned CPU tensors)
+    -> host labels and energy; synchronises the stream."""
+    def hptr(a):
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            assert a.device.type == "cpu" and a.is_contiguous()
+            return ctypes.c_void_p(a.data_ptr())
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data_as(ctypes.c_void_p)
+
+    H, W = I0.shape
+    if labels_out is None:
+        labels_out = np.empty((H, W), dtype=np.int32)
+    if energy_out is None:
+        energy_out = np.empty(4, dtype=np.int64)
+    ls = label_space(space)
+    pr = params(prior, l2=l2, cmax=cmax, cost_mode=cost_mode, iters=iters)
+    rc = load().edp_solve_images_host(hptr(I0), hptr(I1), hptr(I2), W, H, ctypes.byref(ls), ctypes.byref(pr),
+                                      hptr(labels_out), hptr(energy_out), _dev(ws, torch.uint8, "ws"),
+                                      ws.numel(), _stream(stream))
+    _check(rc, "solve_images_host")
+    return labels_out, energy_out
+
+
+def get_device_status(ws, stream=None) -> int:
+    st = ctypes.c_int(0)
+    rc = load().edp_get_device_status(_dev(ws, torch.uint8, "ws"), ws.numel(), ctypes.byref(st), _stream(stream))
+    _check(rc, "get_device_status")
+    return int(st.value)

@@ -10,4 +10,15 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built libedp.so")
-    config.addinivalue_line("markers", "slow: long CPU test (full-size oracle runs)")
+
+
+@pytest.fixture(scope="session")
+def edp_lib():
+    """The CUDA library, built in-tree; GPU tests fail (not skip) without it."""
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a CUDA device"
+    from paper_1410_7922_gb300 import build
+    build.build()
+    from paper_1410_7922_gb300 import edp
+    edp.load()
+    return edp

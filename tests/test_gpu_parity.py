@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+All arithmetic is integer, so labels, costs, row energies and energies must
+match bit for bit.  Inputs are the seeded synthetic workloads and random cost
+volumes (including tie-heavy ones), at sizes the oracle finishes in seconds
+that still span several blocks, bands and a ragged tail; the full-size
+450x375 stereo and 320x240 motion workloads run once each.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1410_7922_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def sp(Q, vmin=None, step=None):
+    R = len(Q)
+    return {"R": R, "Q": tuple(Q), "vmin": tuple(vmin or [0] * R), "step": tuple(step or [1] * R)}
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+@pytest.fixture(autouse=True)
+def reset_tuning(edp_lib):
+    edp_lib.set_tuning(0, 0)
+    yield
+    edp_lib.set_tuning(0, 0)
+
+
+# --------------------------------------------------------------------------
+# cost volume
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", [
+    ("stereo", sp((16,), (0,), (-1,)), "pair", 1, 20),
+    ("stereo_l2", sp((24,), (0,), (-1,)), "pair", 2, 900),
+    ("motion", sp((9, 7), (-4, -3), (1, 1)), "pair", 1, 20),
+    ("stereo3", sp((5, 5, 4), (-2, -2, 0), (1, 1, -1)), "pair_stereo3", 1, 30),
+    ("composite", sp((12,), (0,), (1,)), "composite", 2, 400),
+    ("composite2d", sp((5, 5), (-2, -2), (1, 1)), "composite", 1, 25),
+])
+def test_cost_volume_parity(edp_lib, case):
+    name, space, mode, l2, cmax = case
+    rng = np.random.default_rng(len(name))
+    H, W = 37, 53
+    I0, I1, I2 = (rng.integers(0, 256, size=(H, W)).astype(np.uint8) for _ in range(3))
+    use2 = mode != "pair"
+    want = oracle.cost_volume(I0, I1, I2 if use2 else None, space, l2, cmax, mode)
+    got = edp_lib.cost_volume(dev(I0), dev(I1), dev(I2) if use2 else None, space, l2, cmax, mode)
+    assert np.array_equal(host(got), want)
+
+
+def test_cost_volume_pitched_rows(edp_lib):
+    rng = np.random.default_rng(1)
+    H, W, P = 20, 30, 48
+    big0 = rng.integers(0, 256, size=(H, P)).astype(np.uint8)
+    big1 = rng.integers(0, 256, size=(H, P)).astype(np.uint8)
+    space = sp((8,), (0,), (-1,))
+    want = oracle.cost_volume(big0[:, :W].copy(), big1[:, :W].copy(), None, space, 1, 20)
+    t0, t1 = dev(big0), dev(big1)
+    # the binding takes contiguous tensors; pass the pitched buffers through the C ABI directly
+    import ctypes
+    lib = edp_lib.load()
+    out = torch.empty((H, W, 8), dtype=torch.int32, device="cuda")
+    ls, pr = edp_lib.label_space(space), edp_lib.params({"lam": 0, "g": 1}, l2=1, cmax=20)
+    rc = lib.edp_cost_volume(ctypes.c_void_p(t0.data_ptr()), ctypes.c_void_p(t1.data_ptr()), None, W, H, P,
+                             ctypes.byref(ls), ctypes.byref(pr), ctypes.c_void_p(out.data_ptr()),
+                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    assert np.array_equal(host(out), want)
+
+
+# --------------------------------------------------------------------------
+# scanline DP
+# --------------------------------------------------------------------------
+
+def test_scanline_stereo_64x48(edp_lib):
+    w = synth.workload_scanline_64x48()
+    C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+    lab, row_e = oracle.scanline_dp(C, w["space"], w["prior"], tier=1)
+    glab, grow = edp_lib.scanline_dp(dev(C), w["space"], w["prior"])
+    assert np.array_equal(host(glab), lab)
+    assert np.array_equal(host(grow), row_e)
+
+
+@pytest.mark.parametrize("Q,mode", [((5,), "joint"), ((16,), "joint"), ((33,), "joint"), ((100,), "joint"),
+                                    ((256,), "joint"), ((300,), "joint"), ((5, 4), "joint"),
+                                    ((5, 4), "per_axis"), ((17, 17), "per_axis"), ((17, 17), "joint"),
+                                    ((3, 3, 2), "per_axis"), ((4, 3, 5), "joint"), ((1,), "joint")])
+def test_scanline_random(edp_lib, Q, mode):
+    rng = np.random.default_rng(sum(Q) * 7 + len(mode))
+    n = int(np.prod(Q))
+    H, W = 13, 29
+    for trial in range(2):
+        hi = 4 if trial else 21  # trial 1: many ties
+        C = rng.integers(0, hi, size=(H, W, n)).astype(np.int32)
+        prior = {"lam": int(rng.integers(0, 9)), "g": int(rng.integers(1, 5)), "l1": 1, "mode": mode}
+        lab, row_e = oracle.scanline_dp(C, sp(Q), prior, tier=1)
+        glab, grow = edp_lib.scanline_dp(dev(C), sp(Q), prior)
+        assert np.array_equal(host(grow), row_e), prior
+        assert np.array_equal(host(glab), lab), prior
+
+
+@pytest.mark.parametrize("rb,e", [(1, 1), (3, 2), (7, 3), (2, 8), (5, 16)])
+def test_scanline_launch_shapes(edp_lib, rb, e):
+    rng = np.random.default_rng(rb * 10 + e)
+    C = rng.integers(0, 15, size=(11, 23, 40)).astype(np.int32)
+    prior = {"lam": 4, "g": 3, "l1": 1, "mode": "joint"}
+    lab, row_e = oracle.scanline_dp(C, sp((40,)), prior, tier=1)
+    edp_lib.set_tuning(rb, e)
+    glab, grow = edp_lib.scanline_dp(dev(C), sp((40,)), prior)
+    assert np.array_equal(host(glab), lab) and np.array_equal(host(grow), row_e)
+
+
+# --------------------------------------------------------------------------
+# EDP
+# --------------------------------------------------------------------------
+
+def run_edp(edp_lib, C, space, prior, iters):
+    want = oracle.edp(C, space, prior, iters=iters, tier=1)
+    got = host(edp_lib.solve(dev(C), space, prior, iters=iters))
+    return want, got
+
+
+@pytest.mark.parametrize("Q,mode", [((7,), "joint"), ((64,), "joint"), ((33,), "joint"), ((130,), "joint"),
+                                    ((5, 4), "per_axis"), ((5, 4), "joint"), ((9, 9), "per_axis"),
+                                    ((33, 33), "per_axis"), ((33, 33), "joint"), ((3, 4, 3), "joint"),
+                                    ((5, 5, 3), "per_axis"), ((1,), "joint")])
+@pytest.mark.parametrize("iters", [1, 2])
+def test_edp_random(edp_lib, Q, mode, iters):
+    rng = np.random.default_rng(sum(Q) * 13 + iters)
+    n = int(np.prod(Q))
+    H, W = (9, 14) if n > 500 else (17, 23)
+    for hi in (21, 3):
+        C = rng.integers(0, hi, size=(H, W, n)).astype(np.int32)
+        prior = {"lam": int(rng.integers(1, 12)), "g": int(rng.integers(1, 5)), "l1": 1, "mode": mode}
+        want, got = run_edp(edp_lib, C, sp(Q), prior, iters)
+        assert np.array_equal(got, want), (prior, hi)
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 50), (50, 3)])
+def test_edp_degenerate_shapes(edp_lib, W, H):
+    rng = np.random.default_rng(W * 100 + H)
+    C = rng.integers(0, 20, size=(H, W, 6)).astype(np.int32)
+    prior = {"lam": 5, "g": 2, "l1": 1, "mode": "joint"}
+    for iters in (1, 3):
+        want, got = run_edp(edp_lib, C, sp((6,)), prior, iters)
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("rb,e", [(1, 1), (2, 2), (3, 4), (6, 3), (16, 8), (1, 16)])
+def test_edp_launch_shapes(edp_lib, rb, e):
+    """Results never depend on the launch shape (rows per block, labels per lane)."""
+    rng = np.random.default_rng(rb * 31 + e)
+    for Q, mode in (((24,), "joint"), ((7, 6), "per_axis"), ((7, 6), "joint")):
+        C = rng.integers(0, 21, size=(21, 19, int(np.prod(Q)))).astype(np.int32)
+        prior = {"lam": 6, "g": 3, "l1": 1, "mode": mode}
+        want = oracle.edp(C, sp(Q), prior, iters=2, tier=1)
+        edp_lib.set_tuning(rb, e)
+        got = host(edp_lib.solve(dev(C), sp(Q), prior, iters=2))
+        assert np.array_equal(got, want), (Q, mode, rb, e)
+
+
+def test_edp_stereo_450x375_full_size(edp_lib):
+    """The full Cones-sized stereo workload (Q = 64), j = 1 and j = 6."""
+    w = synth.workload_stereo_450x375()
+    C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+    gC = edp_lib.cost_volume(dev(w["I0"]), dev(w["I1"]), None, w["space"], w["l2"], w["cmax"])
+    assert np.array_equal(host(gC), C)
+    for iters in (1, 6):
+        want = oracle.edp(C, w["space"], w["prior"], iters=iters, tier=1)
+        got = edp_lib.solve(gC, w["space"], w["prior"], iters=iters)
+        assert np.array_equal(host(got), want), iters
+        e_want = oracle.energy(C, want, w["space"], w["prior"])
+        e_got = tuple(int(v) for v in host(edp_lib.energy(gC, got, w["space"], w["prior"])))
+        assert e_got == e_want
+
+
+def test_edp_motion_320x240_full_size(edp_lib):
+    """The full 320x240 motion workload, 33x33 labels, per-axis prior."""
+    w = synth.workload_motion_320x240()
+    C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+    gC = edp_lib.cost_volume(dev(w["I0"]), dev(w["I1"]), None, w["space"], w["l2"], w["cmax"])
+    assert np.array_equal(host(gC), C)
+    want = oracle.edp(C, w["space"], w["prior"], iters=1, tier=1)
+    got = edp_lib.solve(gC, w["space"], w["prior"], iters=1)
+    assert np.array_equal(host(got), want)
+
+
+def test_edp_motion_joint_crop(edp_lib):
+    w = synth.workload_motion_320x240(W=96, H=64, mode="joint")
+    C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+    want, got = run_edp(edp_lib, C, w["space"], w["prior"], 2)
+    assert np.array_equal(got, want)
+
+
+# --------------------------------------------------------------------------
+# energy and the image-level entry points
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("Q,mode,l1", [((16,), "joint", 1), ((6, 5), "per_axis", 1), ((6, 5), "joint", 2),
+                                       ((3, 3, 3), "per_axis", 2)])
+def test_energy_parity(edp_lib, Q, mode, l1):
+    rng = np.random.default_rng(3)
+    n = int(np.prod(Q))
+    C = rng.integers(0, 50, size=(31, 47, n)).astype(np.int32)
+    lab = rng.integers(0, n, size=(31, 47)).astype(np.int32)
+    prior = {"lam": 7, "g": 2, "l1": l1, "mode": mode}
+    want = oracle.energy(C, lab, sp(Q), prior)
+    got = tuple(int(v) for v in host(edp_lib.energy(dev(C), dev(lab), sp(Q), prior)))
+    assert got == want
+
+
+def test_solve_images_device_and_host(edp_lib):
+    w = synth.workload_stereo_450x375(W=120, H=90)
+    C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+    want = oracle.edp(C, w["space"], w["prior"], iters=2, tier=1)
+    e_want = oracle.energy(C, want, w["space"], w["prior"])
+    lab, e = edp_lib.solve_images(dev(w["I0"]), dev(w["I1"]), None, w["space"], w["prior"], w["l2"], w["cmax"],
+                                  iters=2)
+    assert np.array_equal(host(lab), want)
+    assert tuple(int(v) for v in host(e)) == e_want
+    ws = edp_lib.workspace(edp_lib.OP_SOLVE_IMAGES, 120, 90, w["space"], w["prior"], 2)
+    hl, he = edp_lib.solve_images_host(w["I0"], w["I1"], None, w["space"], w["prior"], w["l2"], w["cmax"], ws,
+                                       iters=2)
+    assert np.array_equal(hl, want) and tuple(int(v) for v in he) == e_want
+    assert edp_lib.get_device_status(ws) == 0
+
+
+def test_range_and_argument_errors(edp_lib):
+    C = torch.zeros((4, 4, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(edp_lib.EdpError) as ei:
+        edp_lib.solve(C, sp((8,)), {"lam": 2**21, "g": 1, "l1": 1, "mode": "joint"})
+    assert ei.value.code == edp_lib.ERR_RANGE
+    with pytest.raises(edp_lib.EdpError) as ei:
+        edp_lib.solve(C, sp((8,)), {"lam": 1, "g": 2, "l1": 2, "mode": "joint"})
+    assert ei.value.code == edp_lib.ERR_UNSUPPORTED
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(edp_lib.EdpError) as ei:
+        edp_lib.solve(C, sp((8,)), {"lam": 1, "g": 2}, ws=ws)
+    assert ei.value.code == edp_lib.ERR_WORKSPACE
