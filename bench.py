@@ -1,0 +1,451 @@
+#!/usr/bin/env python
+"""Benchmark: EDP pixel-label updates/s on the 450x375 stereo workload.
+
+One step = the whole hot path over one synthetic stereo pair (450x375, 64
+labels, truncated-abs cost T = 20, truncated-linear prior lambda = 20, K = 4):
+cost volume, one EDP iteration (four scan passes, Algorithm 1) with the
+marginal/argmin, and the energy -- one call of edp_solve_images.
+Pixel-label updates per step = N * Q * (8 * j + 1): two sums written per
+pass, four passes per iteration, plus the marginal.
+
+Prints one JSON line (rank 0).  --impl reference runs the CPU oracle on the
+host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EDP pixel-label updates/s"
+UNIT = "pixel-label updates/s"
+WORKLOAD = "stereo_edp_450x375_Q64"
+PASS_NAMES = ["P1", "P2", "P3", "P4"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--iters", type=int, default=1, help="EDP iterations j per step")
+    ap.add_argument("--impl", default="edp", choices=["edp", "reference"])
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row side measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "edp" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of one scan pass (the messages each pass must read/write)
+# ---------------------------------------------------------------------------
+
+def pass_units(pass_idx: int, it: int, iters: int) -> tuple[int, bool]:
+    """Q-vectors (of 4*Q bytes) one pass moves per pixel, and whether it
+    writes the labels.  Reads: C, and the two messages of the other
+    directions once they have been written; writes: the two new messages when
+    a later pass reads them (mirrors the pass schedule of the library)."""
+    last = it == iters - 1
+    read_c = (it > 0) if pass_idx == 0 else True
+    read_d = (it > 0) if pass_idx <= 1 else True
+    write_a = (not last) if pass_idx == 3 else True
+    write_b = True if pass_idx == 1 else ((not last) if pass_idx == 3 else False)
+    return 1 + read_c + read_d + write_a + write_b, (pass_idx == 3 and last)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("edp_pass.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1410_7922_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the pass kernel from a committed ncu summary,
+    or None if there is none for the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "edp_pass_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
+        except (OSError, ValueError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.1)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        smax = max(r[1] for r in rows)
+        load = [r for r in rows if r[0] > 0.5 * smax] or rows
+        reasons = set()
+        for r in rows:
+            for name, flag in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                  r[2:]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def bad_clocks(c) -> bool:
+    if not c:
+        return False
+    if set(c["reasons"]) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}:
+        return True
+    return c["sm_mhz"] < 0.6 * c["sm_max_mhz"] and not c["reasons"]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_sample(w, iters: int, min_seconds: float = 10.0, max_reps: int = 8):
+    """The oracle (as it is) on one host core, on the full frame, repeated
+    until about min_seconds of work."""
+    import oracle
+    H, W = w["I0"].shape
+    Q = 1
+    for r in range(w["space"]["R"]):
+        Q *= w["space"]["Q"][r]
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+        lab = oracle.edp(C, w["space"], w["prior"], iters=iters, tier=1)
+        oracle.energy(C, lab, w["space"], w["prior"])
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            break
+    updates = W * H * Q * (8 * iters + 1) * reps
+    return {"value": updates / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full {W}x{H} frame(s), j={iters}: oracle cost volume + EDP (RMS tier) + energy, "
+                      f"{el:.1f} s on 1 host core"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1410_7922_gb300 import synth
+    import oracle
+    oracle.build()
+    w = synth.workload_stereo_450x375()
+    H, W = w["I0"].shape
+    Q = 64
+    # each step: one full frame through the oracle (about 2 s on one core)
+    def step():
+        C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+        lab = oracle.edp(C, w["space"], w["prior"], iters=args.iters, tier=1)
+        oracle.energy(C, lab, w["space"], w["prior"])
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = W * H * Q * (8 * args.iters + 1) * args.steps / el
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "W": W, "H": H, "Q": Q, "iters": args.iters},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one full {W}x{H} frame per step, oracle cost volume + EDP (RMS tier) "
+                                       "+ energy on 1 host core"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def time_solve_rows(edp, synth, torch):
+    """Side measurements of the other hot-path rows (device time, CUDA events)."""
+    rows = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s, e = ev(), ev()
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return statistics.median(ts)
+
+    # scanline DP, 64x48 stereo, Q = 16 (cost volume + forward pass + backtrack)
+    w = synth.workload_scanline_64x48()
+    I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
+    C = edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"])
+    ws = edp.workspace(edp.OP_SCANLINE_DP, 64, 48, w["space"], w["prior"])
+    lab = torch.empty((48, 64), dtype=torch.int32, device="cuda")
+    re = torch.empty(48, dtype=torch.int64, device="cuda")
+    ms = timed(lambda: edp.scanline_dp(C, w["space"], w["prior"], ws=ws, labels=lab, row_energy=re))
+    rows["scanline_dp_64x48_Q16"] = {"ms": ms, "updates_per_s": 64 * 48 * 16 / (ms * 1e-3)}
+    # 2D motion EDP, 320x240, 33x33 labels
+    w = synth.workload_motion_320x240()
+    I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
+    C = edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"])
+    H, W, Q = C.shape
+    ws = edp.workspace(edp.OP_SOLVE, W, H, w["space"], w["prior"], 1)
+    lab = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    evs = [ev() for _ in range(8)]
+    edp.set_profile_events(evs)
+    ms = timed(lambda: edp.solve(C, w["space"], w["prior"], iters=1, ws=ws, labels=lab), reps=10)
+    pass_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(4)]
+    edp.set_profile_events(None)
+    nbytes = sum(pass_units(p, 0, 1)[0] * W * H * Q * 4 + (W * H * 4 if pass_units(p, 0, 1)[1] else 0)
+                 for p in range(4))
+    rows["edp_motion_320x240_Q33x33"] = {
+        "ms": ms, "updates_per_s": W * H * Q * 9 / (ms * 1e-3), "pass_ms": pass_ms,
+        "pass_gbs": nbytes / (sum(pass_ms) * 1e-3) / 1e9}
+    # cost volume alone (write-bound), 450x375x64
+    w = synth.workload_stereo_450x375()
+    I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
+    C = torch.empty((375, 450, 64), dtype=torch.int32, device="cuda")
+    ms = timed(lambda: edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"], out=C))
+    rows["cost_volume_450x375_Q64"] = {"ms": ms, "write_gbs": C.numel() * 4 / (ms * 1e-3) / 1e9}
+    lab = edp.solve(C, w["space"], w["prior"], iters=1)
+    out = torch.empty(4, dtype=torch.int64, device="cuda")
+    ms = timed(lambda: edp.energy(C, lab, w["space"], w["prior"], out=out))
+    rows["energy_450x375_Q64"] = {"ms": ms}
+    return rows
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1410_7922_gb300 import edp, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    j = args.iters
+    w = synth.workload_stereo_450x375(pair=rank)  # weak scaling: one pair per rank
+    H, W = w["I0"].shape
+    space, prior = w["space"], w["prior"]
+    Q = edp.n_labels(space)
+    I0 = torch.from_numpy(w["I0"]).to(dev)
+    I1 = torch.from_numpy(w["I1"]).to(dev)
+    ws = edp.workspace(edp.OP_SOLVE_IMAGES, W, H, space, prior, j, device=dev)
+    labels = torch.empty((H, W), dtype=torch.int32, device=dev)
+    energy4 = torch.empty(4, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    npass = 4 * j
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * npass)]
+
+    def step():
+        edp.solve_images(I0, I1, None, space, prior, w["l2"], w["cmax"], iters=j, ws=ws, labels=labels,
+                         energy4=energy4)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = 1 + npass + 1  # cost volume, scan passes, energy
+
+    def timed_region():
+        step_ms, pass_ms = [], [0.0] * npass
+        edp.set_profile_events(pev)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            step()
+            e.record()
+            e.synchronize()
+            step_ms.append(s.elapsed_time(e))
+            for i in range(npass):
+                pass_ms[i] += pev[2 * i].elapsed_time(pev[2 * i + 1])
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - t0
+        edp.set_profile_events(None)
+        return step_ms, pass_ms, wall
+
+    with ClockSampler(local) as cs:
+        step_ms, pass_ms, wall = timed_region()
+    clocks = cs.summary()
+    remeasured = False
+    if bad_clocks(clocks):
+        remeasured = True
+        with ClockSampler(local) as cs:
+            step_ms, pass_ms, wall = timed_region()
+        clocks = cs.summary()
+    status = edp.get_device_status(ws)
+    if status != 0:
+        raise RuntimeError(f"device status {edp.status_string(status)}")
+    total_ms = allreduce_max(world, sum(step_ms))
+    ms_per_step = total_ms / args.steps
+    updates = W * H * Q * (8 * j + 1)
+    value = updates * world * args.steps / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (the scan pass): algorithmic bytes / time
+    nbytes = 0
+    for i in range(npass):
+        units, lab = pass_units(i % 4, i // 4, j)
+        nbytes += units * W * H * Q * 4 + (W * H * 4 if lab else 0)
+    pass_total_s = sum(pass_ms) * 1e-3 / args.steps
+    achieved = nbytes / pass_total_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic(WORKLOAD)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": "edp_pass_kernel",
+                "bytes_per_launch_avg": nbytes / npass, "launch_ms_avg": sum(pass_ms) / args.steps / npass,
+                "pass_ms": [p / args.steps for p in pass_ms]}
+
+    # end to end through the host-buffer C call (copies inside the timed region)
+    I0h = torch.from_numpy(w["I0"]).pin_memory()
+    I1h = torch.from_numpy(w["I1"]).pin_memory()
+    lab_h = torch.empty((H, W), dtype=torch.int32).pin_memory()
+    en_h = torch.empty(4, dtype=torch.int64).pin_memory()
+
+    def e2e_step():
+        edp.solve_images_host(I0h, I1h, None, space, prior, w["l2"], w["cmax"], ws, iters=j,
+                              labels_out=lab_h.numpy(), energy_out=en_h.numpy())
+
+    for _ in range(2):
+        e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = allreduce_max(world, time.perf_counter() - t0)
+    e2e = {"value": updates * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H,
+           "d2h_bytes_per_step": W * H * 4 + 32, "ms_per_step": 1e3 * e2e_s / args.steps}
+    assert np.array_equal(lab_h.numpy(), labels.cpu().numpy())
+
+    rows = None
+    if not args.no_rows and rank == 0:
+        rows = time_solve_rows(edp, synth, torch)
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_oracle_sample(w, j)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "W": W, "H": H, "Q": Q, "iters": j,
+                           "prior": "truncated linear, lambda=20, K=4", "cost": "min(|IL-IR|, 20)",
+                           "l2_cache": "flushed between steps (256 MB write)",
+                           "parallelism": f"replicas x{world} (one independent pair per GPU)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+                "wall_s_timed_region": wall, "remeasured": remeasured, "rows": rows,
+                "energy_per_pixel": float(energy4[3].item()) / (W * H)}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -118,6 +118,21 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
  * concurrent solves. */
 int edp_set_tuning(int rows_per_block, int labels_per_lane);
 
+/* Per-pass timing hook: while set, edp_solve (and edp_solve_images) record
+ * events[2*i] / events[2*i + 1] (cudaEvent_t handles created by the caller)
+ * on the solve's stream immediately before / after the launch of scan pass
+ * i (i = 4 * iteration + pass), for i < n_events / 2.  NULL / 0 disables.
+ * The library keeps the pointer, not a copy: the array must outlive the
+ * solves that use it. */
+int edp_set_profile_events(void *const *events, int n_events);
+
+/* Per-band trace of the scan passes (tracing hook): while set, pass i of a
+ * solve writes, for every row band b, four uint64 at
+ * device_buffer[(i * nbands + b) * 4 ...]: start and end %globaltimer (ns),
+ * ns spent waiting for the previous band, and the SM id.  Passes whose
+ * record would not fit in `bytes` are not traced.  NULL / 0 disables. */
+int edp_set_trace(void *device_buffer, size_t bytes);
+
 /* Cost volume (DSI), Eq. Cost_value (Algorithm 1, step 1).
  *  I0, I1: uint8 [H][pitch]; I2: third image for EDP_COST_PAIR_STEREO3 and
  *  EDP_COST_COMPOSITE, else NULL.  Writes C int32 [H][W][Q].

@@ -20,6 +20,10 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 int g_tune_rb = 0;       // rows per block override (0 = automatic)
 int g_tune_e = 0;        // labels per lane target override (0 = automatic)
+void *const *g_prof_events = nullptr;  // optional per-pass events (profiling hook)
+int g_prof_n = 0;
+unsigned long long *g_trace = nullptr;  // optional per-band trace buffer (device)
+size_t g_trace_bytes = 0;
 
 struct Geometry {
     int R;       // label axes after dropping axes with one label
@@ -246,7 +250,14 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
             a.write_a = (pass == 3) ? !last_it : 1;
             a.write_b = (pass == 1) ? 1 : (pass == 3 ? !last_it : 0);
             a.final_ = (pass == 3 && last_it);
+            a.trace = (g_trace && (size_t)(slot + 1) * a.nbands * 32 <= g_trace_bytes)
+                          ? g_trace + (size_t)slot * a.nbands * 4
+                          : nullptr;
+            const bool prof = g_prof_events && 2 * slot + 1 < g_prof_n;
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot], st) != cudaSuccess) return EDP_ERR_CUDA;
             if (launch_edp_pass(a, cfg.em, cfg.threads, cfg.smem, st)) return EDP_ERR_CUDA;
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
+                return EDP_ERR_CUDA;
         }
     }
     return EDP_OK;
@@ -344,6 +355,20 @@ int edp_set_tuning(int rows_per_block, int labels_per_lane) {
     if (rows_per_block < 0 || labels_per_lane < 0 || labels_per_lane > kEM) return EDP_ERR_INVALID_ARG;
     g_tune_rb = rows_per_block;
     g_tune_e = labels_per_lane;
+    return EDP_OK;
+}
+
+int edp_set_profile_events(void *const *events, int n_events) {
+    if (n_events < 0 || (n_events > 0 && !events)) return EDP_ERR_INVALID_ARG;
+    g_prof_events = n_events ? events : nullptr;
+    g_prof_n = n_events;
+    return EDP_OK;
+}
+
+int edp_set_trace(void *device_buffer, size_t bytes) {
+    if (bytes > 0 && !device_buffer) return EDP_ERR_INVALID_ARG;
+    g_trace = bytes ? static_cast<unsigned long long *>(device_buffer) : nullptr;
+    g_trace_bytes = bytes;
     return EDP_OK;
 }
 

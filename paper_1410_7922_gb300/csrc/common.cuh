@@ -203,6 +203,18 @@ __device__ __forceinline__ long long wait_progress(const unsigned *p, unsigned n
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned v;
+    asm volatile("mov.u32 %0, %smid;" : "=r"(v));
+    return v;
+}
+
 __device__ __forceinline__ void publish_progress(unsigned *p, unsigned v) {
     __threadfence();
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");

@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(kMaxThreads) edp_pass_kernel(PassArgs A) {
         for (int i = tid; i < 4 * RB; i += blockDim.x) gmin[i] = kBig;
         for (int i = tid; i < 2 * RB; i += blockDim.x) argk[i] = ~0ull;
         unsigned seen = 0;  // progress of the previous band's last row seen by this warp
+        unsigned long long t_band0 = 0, t_wait = 0;
+        if (A.trace && tid == 0) t_band0 = global_ns();
 
         // Stage C, m_c, m_d of column s of every row this lane serves into
         // stg[buf]; vectors known to be zero (not written yet, or from
@@ -139,8 +141,10 @@ __global__ void __launch_bounds__(kMaxThreads) edp_pass_kernel(PassArgs A) {
                 const bool need_glob = compute && w0 == 0 && r_me > 0;
                 if (__any_sync(full, need_glob)) {
                     if (lane == 0 && seen < (unsigned)(t + 1)) {
+                        const unsigned long long tw = A.trace ? global_ns() : 0;
                         const long long got =
                             wait_progress(A.progress + (r0 - 1), (unsigned)(t + 1), A.spin_limit, A.status);
+                        if (A.trace) t_wait += global_ns() - tw;
                         if (got < 0) {
                             atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
                             s_abort = 1;
@@ -302,6 +306,12 @@ __global__ void __launch_bounds__(kMaxThreads) edp_pass_kernel(PassArgs A) {
             }
         }
         cp_async_wait_0();
+        if (A.trace && tid == 0) {
+            A.trace[band * 4 + 0] = t_band0;
+            A.trace[band * 4 + 1] = global_ns();
+            A.trace[band * 4 + 2] = t_wait;
+            A.trace[band * 4 + 3] = sm_id();
+        }
         __syncthreads();
     }
 done:

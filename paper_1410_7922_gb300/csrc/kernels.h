@@ -31,6 +31,7 @@ struct PassArgs {
     int nbands;
     int grid;
     long long spin_limit;
+    unsigned long long *trace;  // optional: per band {start ns, end ns, wait ns, sm id}
 };
 int launch_edp_pass(const PassArgs &a, int em, int threads, size_t smem, cudaStream_t st);
 int edp_pass_occupancy(int em, int threads, size_t smem);

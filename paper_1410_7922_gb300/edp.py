@@ -59,6 +59,8 @@ def load() -> ctypes.CDLL:
         "edp_status_string": ([I], ctypes.c_char_p),
         "edp_workspace_size": ([I, I, I, LS, PR], SZ),
         "edp_set_tuning": ([I, I], I),
+        "edp_set_profile_events": ([P, I], I),
+        "edp_set_trace": ([P, SZ], I),
         "edp_cost_volume": ([P, P, P, I, I, I, LS, PR, P, P], I),
         "edp_scanline_dp": ([P, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_solve": ([P, I, I, LS, PR, P, P, SZ, P], I),
@@ -76,7 +78,8 @@ def load() -> ctypes.CDLL:
 
 
 def exported_symbols() -> list[str]:
-    return ["edp_version", "edp_status_string", "edp_workspace_size", "edp_set_tuning",
+    return ["edp_version", "edp_status_string", "edp_workspace_size", "edp_set_tuning", "edp_set_profile_events",
+            "edp_set_trace",
             "edp_cost_volume", "edp_scanline_dp", "edp_solve", "edp_energy", "edp_solve_images",
             "edp_solve_images_host", "edp_get_device_status"]
 
@@ -146,6 +149,33 @@ def version() -> int:
 
 def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0) -> None:
     _check(load().edp_set_tuning(int(rows_per_block), int(labels_per_lane)), "set_tuning")
+
+
+_prof_keep = None
+
+
+def set_profile_events(events) -> None:
+    """Record torch.cuda.Event pairs around each scan-pass launch (None: off)."""
+    global _prof_keep
+    lib = load()
+    if not events:
+        _check(lib.edp_set_profile_events(None, 0), "set_profile_events")
+        _prof_keep = None
+        return
+    for e in events:  # torch creates the CUDA event lazily, on first record
+        if not e.cuda_event:
+            e.record()
+    arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _prof_keep = (arr, events)
+    _check(lib.edp_set_profile_events(arr, len(events)), "set_profile_events")
+
+
+def set_trace(buf) -> None:
+    """Per-band trace of the scan passes into a CUDA uint8/int64 tensor (None: off)."""
+    if buf is None:
+        _check(load().edp_set_trace(None, 0), "set_trace")
+        return
+    _check(load().edp_set_trace(ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size()), "set_trace")
 
 
 def workspace_size(op: int, W: int, H: int, space: dict, prior: dict, iters: int = 1, **kw) -> int:
