@@ -113,10 +113,12 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
                           const edp_params *params);
 
 /* Process-wide launch shape of the DP kernels: rows per block and target
- * labels per lane on one label line (0 = automatic, the default).  Used by
- * the autotuner; results never depend on it.  Not thread-safe with
+ * labels per lane on one label line (0 = automatic, the default), and
+ * general_kernel = 1 to run one-axis label spaces through the multi-axis
+ * scan-pass kernel instead of the warp-per-row one.  Used by the autotuner
+ * and the tests; results never depend on it.  Not thread-safe with
  * concurrent solves. */
-int edp_set_tuning(int rows_per_block, int labels_per_lane);
+int edp_set_tuning(int rows_per_block, int labels_per_lane, int general_kernel);
 
 /* Per-pass timing hook: while set, edp_solve (and edp_solve_images) record
  * events[2*i] / events[2*i + 1] (cudaEvent_t handles created by the caller)

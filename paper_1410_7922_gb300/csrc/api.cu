@@ -20,6 +20,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 int g_tune_rb = 0;       // rows per block override (0 = automatic)
 int g_tune_e = 0;        // labels per lane target override (0 = automatic)
+int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass kernel
 void *const *g_prof_events = nullptr;  // optional per-pass events (profiling hook)
 int g_prof_n = 0;
 unsigned long long *g_trace = nullptr;  // optional per-band trace buffer (device)
@@ -157,16 +158,22 @@ int configure(const Geometry &g, int H, bool scan, int W, int ptr_bytes, bool *p
 
 int ptr_bytes_for(int Q) { return Q <= 256 ? 1 : (Q <= 65536 ? 2 : 4); }
 
-// Workspace of edp_solve: header | progress [4*iters][H] | counters [4*iters] | M[4][N*Q]
+// Workspace of edp_solve:
+//   header | progress [4*iters][H] | counters [4*iters] | hand-off records | M[4][N*Q]
+// The hand-off records ({value, tag} per label of the last row of each row
+// band, one-axis kernel) are sized for bands of kMinRowsR1 rows.
+constexpr int kMinRowsR1 = 2;
 struct SolveLayout {
-    size_t progress, counters, msg[4], end;
+    size_t progress, counters, ll, ll_bytes, msg[4], end;
 };
 SolveLayout solve_layout(int W, int H, int Q, int iters) {
     SolveLayout L;
     const size_t npass = 4 * (size_t)iters;
     L.progress = kHeader;
     L.counters = align_up(L.progress + npass * H * 4);
-    size_t off = align_up(L.counters + npass * 4);
+    L.ll = align_up(L.counters + npass * 4);
+    L.ll_bytes = (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * W * Q * 8;
+    size_t off = align_up(L.ll + L.ll_bytes);
     for (int k = 0; k < 4; ++k) {
         L.msg[k] = off;
         off = align_up(off + (size_t)W * H * Q * 4);
@@ -206,8 +213,68 @@ int check_range(int W, int H, const Geometry &g, const edp_params *p) {
     return EDP_OK;
 }
 
+// One label axis with at most 256 labels: the warp-per-row kernel.
+int run_solve_r1(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
+                 unsigned char *ws, cudaStream_t st) {
+    const SolveLayout L = solve_layout(W, H, g.Q, p->iters);
+    const int E = (g.Q + 31) / 32;
+    const int EMt = E <= 1 ? 1 : E <= 2 ? 2 : E <= 4 ? 4 : 8;
+    int NWR = g_tune_rb > 0 ? g_tune_rb : 8;
+    NWR = std::max(kMinRowsR1, std::min(NWR, std::min(16, H)));
+    if (H < kMinRowsR1) NWR = kMinRowsR1;
+    while (NWR > kMinRowsR1 && pass_r1_smem(NWR, E) > (size_t)kMaxSmem) --NWR;
+    const size_t smem = pass_r1_smem(NWR, E);
+    if (smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
+    PassR1Args a;
+    memset(&a, 0, sizeof a);
+    a.C = C;
+    for (int k = 0; k < 4; ++k) a.M[k] = reinterpret_cast<int *>(ws + L.msg[k]);
+    a.labels = labels;
+    a.ll = reinterpret_cast<int2 *>(ws + L.ll);
+    a.status = reinterpret_cast<int *>(ws);
+    a.W = W;
+    a.H = H;
+    a.Q = g.Q;
+    a.E = E;
+    a.EMt = EMt;
+    a.lam = p->lambda;
+    a.capv = (int)cap_value(p);
+    a.kc = p->g <= 1 ? 0 : std::min(31, (p->g - 1 + E - 1) / E);
+    a.NWR = NWR;
+    a.nbands = (H + NWR - 1) / NWR;
+    a.grid = a.nbands;
+    a.spin_limit = 4000000;
+    // status, counters and the used hand-off records start from zero
+    int rc = cuda_status(cudaMemsetAsync(ws, 0, L.ll + (size_t)a.nbands * W * g.Q * 8, st));
+    if (rc) return rc;
+    for (int it = 0; it < p->iters; ++it) {
+        const bool last_it = (it == p->iters - 1);
+        for (int pass = 0; pass < 4; ++pass) {
+            const int slot = it * 4 + pass;
+            a.pass = pass;
+            a.band_counter = reinterpret_cast<unsigned *>(ws + L.counters) + slot;
+            a.read_c = (pass == 0) ? (it > 0) : 1;
+            a.read_d = (pass <= 1) ? (it > 0) : 1;
+            a.write_a = (pass == 3) ? !last_it : 1;
+            a.write_b = (pass == 1) ? 1 : (pass == 3 ? !last_it : 0);
+            a.final_ = (pass == 3 && last_it);
+            a.tag = slot + 1;
+            a.trace = (g_trace && (size_t)(slot + 1) * a.nbands * 32 <= g_trace_bytes)
+                          ? g_trace + (size_t)slot * a.nbands * 4
+                          : nullptr;
+            const bool prof = g_prof_events && 2 * slot + 1 < g_prof_n;
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot], st) != cudaSuccess) return EDP_ERR_CUDA;
+            if (launch_edp_pass_r1(a, 32 * NWR, smem, st)) return EDP_ERR_CUDA;
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
+                return EDP_ERR_CUDA;
+        }
+    }
+    return EDP_OK;
+}
+
 int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
               unsigned char *ws, cudaStream_t st) {
+    if (g.R == 1 && g.Q <= 256 && !g_force_general) return run_solve_r1(C, W, H, g, p, labels, ws, st);
     DpConfig cfg;
     int rc = configure(g, H, false, W, 0, nullptr, &cfg);
     if (rc) return rc;
@@ -351,10 +418,12 @@ const char *edp_status_string(int status) {
     }
 }
 
-int edp_set_tuning(int rows_per_block, int labels_per_lane) {
+int edp_set_tuning(int rows_per_block, int labels_per_lane, int general_kernel) {
     if (rows_per_block < 0 || labels_per_lane < 0 || labels_per_lane > kEM) return EDP_ERR_INVALID_ARG;
+    if (general_kernel != 0 && general_kernel != 1) return EDP_ERR_INVALID_ARG;
     g_tune_rb = rows_per_block;
     g_tune_e = labels_per_lane;
+    g_force_general = general_kernel;
     return EDP_OK;
 }
 

@@ -36,6 +36,25 @@ struct PassArgs {
 int launch_edp_pass(const PassArgs &a, int em, int threads, size_t smem, cudaStream_t st);
 int edp_pass_occupancy(int em, int threads, size_t smem);
 
+// one EDP scan pass, one label axis, one warp per row (edp_pass_r1.cu)
+struct PassR1Args {
+    const int *C;
+    int *M[4];
+    int *labels;
+    int2 *ll;               // [nbands][W][Q] {value, tag} hand-off records between blocks
+    unsigned *band_counter;
+    int *status;
+    int W, H, Q, E, EMt;    // E labels per lane (EMt: template bound)
+    int lam, capv, kc;      // kc: lanes of carry in the truncated sweeps
+    int pass, read_c, read_d, write_a, write_b, final_;
+    int NWR;                // rows (warps) per block
+    int nbands, grid, tag;
+    long long spin_limit;
+    unsigned long long *trace;
+};
+int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st);
+size_t pass_r1_smem(int NWR, int E);
+
 // scanline DP
 struct ScanArgs {
     const int *C;

@@ -31,9 +31,9 @@ def host(t):
 
 @pytest.fixture(autouse=True)
 def reset_tuning(edp_lib):
-    edp_lib.set_tuning(0, 0)
+    edp_lib.set_tuning(0, 0, False)
     yield
-    edp_lib.set_tuning(0, 0)
+    edp_lib.set_tuning(0, 0, False)
 
 
 # --------------------------------------------------------------------------
@@ -116,7 +116,7 @@ def test_scanline_launch_shapes(edp_lib, rb, e):
     C = rng.integers(0, 15, size=(11, 23, 40)).astype(np.int32)
     prior = {"lam": 4, "g": 3, "l1": 1, "mode": "joint"}
     lab, row_e = oracle.scanline_dp(C, sp((40,)), prior, tier=1)
-    edp_lib.set_tuning(rb, e)
+    edp_lib.set_tuning(rb, e, False)
     glab, grow = edp_lib.scanline_dp(dev(C), sp((40,)), prior)
     assert np.array_equal(host(glab), lab) and np.array_equal(host(grow), row_e)
 
@@ -147,14 +147,39 @@ def test_edp_random(edp_lib, Q, mode, iters):
         assert np.array_equal(got, want), (prior, hi)
 
 
-@pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 50), (50, 3)])
-def test_edp_degenerate_shapes(edp_lib, W, H):
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 50), (50, 3), (7, 33)])
+@pytest.mark.parametrize("general", [False, True])
+def test_edp_degenerate_shapes(edp_lib, W, H, general):
     rng = np.random.default_rng(W * 100 + H)
     C = rng.integers(0, 20, size=(H, W, 6)).astype(np.int32)
     prior = {"lam": 5, "g": 2, "l1": 1, "mode": "joint"}
+    edp_lib.set_tuning(0, 0, general)
     for iters in (1, 3):
         want, got = run_edp(edp_lib, C, sp((6,)), prior, iters)
         assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("Q", [1, 5, 16, 31, 32, 33, 64, 100, 129, 256])
+@pytest.mark.parametrize("g", [1, 2, 4, 9, 300])
+def test_edp_one_axis_kernel(edp_lib, Q, g):
+    """The warp-per-row kernel: label counts around the lane boundaries and
+    truncations from 1 (no carries) to untruncated."""
+    rng = np.random.default_rng(Q * 1000 + g)
+    C = rng.integers(0, 21, size=(19, 27, Q)).astype(np.int32)
+    prior = {"lam": int(rng.integers(1, 25)), "g": g, "l1": 1, "mode": "joint"}
+    want, got = run_edp(edp_lib, C, sp((Q,)), prior, 2)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("rows", [2, 3, 5, 8, 16])
+def test_edp_one_axis_rows_per_block(edp_lib, rows):
+    rng = np.random.default_rng(rows)
+    C = rng.integers(0, 21, size=(37, 41, 64)).astype(np.int32)
+    prior = {"lam": 20, "g": 4, "l1": 1, "mode": "joint"}
+    want = oracle.edp(C, sp((64,)), prior, iters=2, tier=1)
+    edp_lib.set_tuning(rows, 0, False)
+    got = host(edp_lib.solve(dev(C), sp((64,)), prior, iters=2))
+    assert np.array_equal(got, want)
 
 
 @pytest.mark.parametrize("rb,e", [(1, 1), (2, 2), (3, 4), (6, 3), (16, 8), (1, 16)])
@@ -165,7 +190,7 @@ def test_edp_launch_shapes(edp_lib, rb, e):
         C = rng.integers(0, 21, size=(21, 19, int(np.prod(Q)))).astype(np.int32)
         prior = {"lam": 6, "g": 3, "l1": 1, "mode": mode}
         want = oracle.edp(C, sp(Q), prior, iters=2, tier=1)
-        edp_lib.set_tuning(rb, e)
+        edp_lib.set_tuning(rb, e, True)
         got = host(edp_lib.solve(dev(C), sp(Q), prior, iters=2))
         assert np.array_equal(got, want), (Q, mode, rb, e)
 

@@ -1,0 +1,72 @@
+"""Pins for the CPU reference of the proposal network (oracle/net.py):
+bfloat16 rounding against torch's conversion, the convolution and its two
+gradients against torch's conv2d and autograd in float64, and the whole
+backward pass against central finite differences."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import net
+
+
+def test_bf16_rounding_matches_torch():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(0, 10, 5000), [1.0, 1 + 2**-8, 1 + 3 * 2**-9, -1 - 2**-8, 0.0, 3e38]])
+    want = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(net.bf16(x), want)
+    assert net.bf16(np.array([1 + 2**-8]))[0] == 1.0          # tie to even
+    assert net.bf16(np.array([1 + 3 * 2**-9]))[0] == 1 + 2**-7
+
+
+def test_conv_and_gradients_match_torch():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(2, 3, 7, 9))
+    w = rng.normal(size=(4, 3, 3, 3))
+    b = rng.normal(size=4)
+    g = rng.normal(size=(2, 4, 7, 9))
+    xt = torch.from_numpy(x).requires_grad_(True)
+    wt = torch.from_numpy(w).requires_grad_(True)
+    out = torch.nn.functional.conv2d(xt, wt, torch.from_numpy(b), padding=1)
+    assert np.allclose(net.conv3x3(x, w, b), out.detach().numpy(), rtol=1e-12, atol=1e-12)
+    out.backward(torch.from_numpy(g))
+    assert np.allclose(net.conv3x3_dgrad(g, w), xt.grad.numpy(), rtol=1e-12, atol=1e-12)
+    assert np.allclose(net.conv3x3_wgrad(g, x), wt.grad.numpy(), rtol=1e-12, atol=1e-12)
+
+
+def test_backward_finite_differences():
+    rng = np.random.default_rng(2)
+    params = net.init_params(3)
+    params = [(w, rng.normal(0, 0.1, size=b.shape)) for w, b in params]
+    x = rng.uniform(0, 1, size=(1, 5, 6, 5))
+    tgt = rng.normal(0, 2, size=(1, 2, 6, 5))
+    loss, grads = net.backward(x, params, tgt, rounding=None)
+    eps = 1e-6
+    for li in (0, 3, 5):
+        w, b = params[li]
+        for idx in [(0, 0, 1, 1), (1, 2, 0, 2)]:
+            if idx[1] >= w.shape[1] or idx[0] >= w.shape[0]:
+                continue
+            wp, wm = w.copy(), w.copy()
+            wp[idx] += eps
+            wm[idx] -= eps
+            pp = list(params); pp[li] = (wp, b)
+            pm = list(params); pm[li] = (wm, b)
+            lp = net.smooth_l1(net.forward(x, pp, rounding=None), tgt)[0]
+            lm = net.smooth_l1(net.forward(x, pm, rounding=None), tgt)[0]
+            assert abs((lp - lm) / (2 * eps) - grads[li][0][idx]) < 1e-6 * max(1.0, abs(grads[li][0][idx]))
+        bp, bm = b.copy(), b.copy()
+        bp[0] += eps
+        bm[0] -= eps
+        pp = list(params); pp[li] = (w, bp)
+        pm = list(params); pm[li] = (w, bm)
+        lp = net.smooth_l1(net.forward(x, pp, rounding=None), tgt)[0]
+        lm = net.smooth_l1(net.forward(x, pm, rounding=None), tgt)[0]
+        assert abs((lp - lm) / (2 * eps) - grads[li][1][0]) < 1e-6 * max(1.0, abs(grads[li][1][0]))
+
+
+def test_smooth_l1_closed_form():
+    out = np.array([0.0, 0.5, 3.0, -2.0])
+    tgt = np.zeros(4)
+    loss, g = net.smooth_l1(out, tgt)
+    assert loss == pytest.approx((0 + 0.125 + 2.5 + 1.5) / 4)
+    assert np.allclose(g, np.array([0.0, 0.5, 1.0, -1.0]) / 4)
