@@ -195,6 +195,90 @@ int edp_solve_images_host(const uint8_t *I0_host, const uint8_t *I1_host,
                           const edp_params *params, int32_t *labels_host,
                           int64_t *energy4_host, void *ws, size_t ws_bytes, edp_stream_t stream);
 
+/* Windowed EDP (the learned-proposal form; not in the paper).  Every pixel
+ * keeps only the win^R labels of a box centred on a proposed label
+ * (centre: int32 [H][W][R] label coordinates, clamped so that the box lies
+ * inside the label space).  Costs, messages and sums live in box
+ * coordinates; a message between neighbouring boxes is the exact
+ * min-convolution of Eq. M_strf restricted to the two boxes, evaluated with
+ * the RMS sweeps of Sec. 3.2 per axis.  With every box equal to the whole
+ * space this is edp_solve.  Supported: R = 1 or 2, odd win <= 15,
+ * win <= Q[r], l1 = 1.
+ *  Cw: int32 [H][W][win^R] box costs from edp_cost_window.  labels: int32
+ *  [H][W] full-space linear label indexes. */
+size_t edp_workspace_size_windowed(int W, int H, const edp_label_space *space, const edp_params *params,
+                                   int win);
+int edp_cost_window(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H, int pitch,
+                    const edp_label_space *space, const edp_params *params, const int32_t *centre, int win,
+                    int32_t *Cw, edp_stream_t stream);
+int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W, int H,
+                       const edp_label_space *space, const edp_params *params, int32_t *labels, void *ws,
+                       size_t ws_bytes, edp_stream_t stream);
+
+/* Winner-take-all over the full label space, straight from the images (no
+ * cost volume): labels[x] = lowest-index argmin_q C(x, q) of Eq. Cost_value,
+ * cost[x] = that minimum (cost may be NULL).  R = 1 or 2, EDP_COST_PAIR. */
+int edp_wta(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, const edp_label_space *space,
+            const edp_params *params, int32_t *labels, int32_t *cost, edp_stream_t stream);
+
+/* Learned proposal network (not in the paper): six 3x3 convolutions, channels
+ * 5 -> 32 -> 32 -> 32 -> 32 -> 32 -> 2, ReLU between layers, predicting the
+ * label-space centre of each pixel (R = 2) for edp_solve_windowed.
+ * bfloat16 weights and activations (round to nearest even), float32
+ * accumulation; parameters are a flat float32 array (layer by layer:
+ * W[Co][Ci][3][3], then b[Co]), edp_net_param_count() values.
+ * Features x: bf16 [N][H][W][5] (from edp_net_features).  Output and target:
+ * float32 [N][H][W][2], label coordinates relative to the space's middle. */
+long long edp_net_param_count(void);
+size_t edp_net_workspace_size(int N, int H, int W);
+/* Forward pass; keeps the activations in ws for edp_net_backward. */
+int edp_net_forward(const float *params, const void *x, int N, int H, int W, float *out, void *ws, size_t ws_bytes,
+                    edp_stream_t stream);
+/* Smooth-L1 loss (mean) of the last forward's output against target and
+ * the gradient of every parameter (grad: float32, same layout as params).
+ * loss: device float64 [1]. */
+int edp_net_backward(const float *params, const float *out, const float *target, int N, int H, int W, float *grad,
+                     double *loss, void *ws, size_t ws_bytes, edp_stream_t stream);
+/* One Adam step (step >= 1) on the float32 parameters. */
+int edp_net_adam(float *params, const float *grad, float *m, float *v, float lr, float beta1, float beta2, float eps,
+                 int step, edp_stream_t stream);
+/* Features of one image pair: I0/255, I1/255, the WTA label coordinates
+ * (centred, / scale) and the WTA cost / cmax, as bf16 [H][W][5]. */
+int edp_net_features(const uint8_t *I0, const uint8_t *I1, const int32_t *wta_labels, const int32_t *wta_cost,
+                     int W, int H, const edp_label_space *space, float scale, float cmax, void *x,
+                     edp_stream_t stream);
+/* Box centres (int32 [n][2], label coordinates) from network outputs:
+ * round to the nearest label, clamp into the space. */
+int edp_net_centres(const float *out, int n, const edp_label_space *space, int32_t *centre, edp_stream_t stream);
+
+/* One problem of a batch: a device image pair (or triple) in, labels and
+ * energy out.  Images are uint8 [H][pitch]. */
+typedef struct {
+    const uint8_t *I0, *I1, *I2;
+    int32_t W, H, pitch;
+    edp_label_space space;
+    edp_params params;
+    int32_t *labels;  /* device int32 [H][W]          */
+    int64_t *energy4; /* device int64 [4], or NULL    */
+} edp_problem;
+
+/* Workspace bytes for edp_solve_batched to keep all n problems resident at
+ * once.  A smaller workspace also works as long as it holds the largest
+ * single problem: the problems are then solved in waves that fit. */
+size_t edp_batch_workspace_size(const edp_problem *probs, int n);
+
+/* Batched form of edp_solve_images for many independent problems of uneven
+ * sizes and label spaces (one, two and three label axes mixed).  Per wave of
+ * resident problems: one launch zeroes the control words, one builds every
+ * cost volume, ONE persistent launch runs every scan pass of every problem
+ * (work items (pass, problem, row band) taken in order from a global queue,
+ * with bounded waits on the previous band and the previous pass of the same
+ * problem), and one launch evaluates every energy.  Results are identical to
+ * solving each problem alone.  `probs` is host memory and is read during the
+ * call only.  The call enqueues work and returns; it can be captured in a
+ * CUDA graph (after one uncaptured call has set the kernels' attributes). */
+int edp_solve_batched(const edp_problem *probs, int n, void *ws, size_t ws_bytes, edp_stream_t stream);
+
 /* Reads the device status word of a workspace used by edp_solve /
  * edp_solve_images / edp_scanline_dp.  Synchronises `stream`. */
 int edp_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stream_t stream);

@@ -213,81 +213,63 @@ int check_range(int W, int H, const Geometry &g, const edp_params *p) {
     return EDP_OK;
 }
 
-// One label axis with at most 256 labels: the warp-per-row kernel.
-int run_solve_r1(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
-                 unsigned char *ws, cudaStream_t st) {
-    const SolveLayout L = solve_layout(W, H, g.Q, p->iters);
-    const int E = (g.Q + 31) / 32;
-    const int EMt = E <= 1 ? 1 : E <= 2 ? 2 : E <= 4 ? 4 : 8;
-    int NWR = g_tune_rb > 0 ? g_tune_rb : 8;
-    NWR = std::max(kMinRowsR1, std::min(NWR, std::min(16, H)));
-    if (H < kMinRowsR1) NWR = kMinRowsR1;
-    while (NWR > kMinRowsR1 && pass_r1_smem(NWR, E) > (size_t)kMaxSmem) --NWR;
-    const size_t smem = pass_r1_smem(NWR, E);
-    if (smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
-    PassR1Args a;
-    memset(&a, 0, sizeof a);
-    a.C = C;
-    for (int k = 0; k < 4; ++k) a.M[k] = reinterpret_cast<int *>(ws + L.msg[k]);
-    a.labels = labels;
-    a.ll = reinterpret_cast<int2 *>(ws + L.ll);
-    a.status = reinterpret_cast<int *>(ws);
-    a.W = W;
-    a.H = H;
-    a.Q = g.Q;
-    a.E = E;
-    a.EMt = EMt;
-    a.lam = p->lambda;
-    a.capv = (int)cap_value(p);
-    a.kc = p->g <= 1 ? 0 : std::min(31, (p->g - 1 + E - 1) / E);
-    a.NWR = NWR;
-    a.nbands = (H + NWR - 1) / NWR;
-    a.grid = a.nbands;
-    a.spin_limit = 4000000;
-    // status, counters and the used hand-off records start from zero
-    int rc = cuda_status(cudaMemsetAsync(ws, 0, L.ll + (size_t)a.nbands * W * g.Q * 8, st));
-    if (rc) return rc;
-    for (int it = 0; it < p->iters; ++it) {
-        const bool last_it = (it == p->iters - 1);
-        for (int pass = 0; pass < 4; ++pass) {
-            const int slot = it * 4 + pass;
-            a.pass = pass;
-            a.band_counter = reinterpret_cast<unsigned *>(ws + L.counters) + slot;
-            a.read_c = (pass == 0) ? (it > 0) : 1;
-            a.read_d = (pass <= 1) ? (it > 0) : 1;
-            a.write_a = (pass == 3) ? !last_it : 1;
-            a.write_b = (pass == 1) ? 1 : (pass == 3 ? !last_it : 0);
-            a.final_ = (pass == 3 && last_it);
-            a.tag = slot + 1;
-            a.trace = (g_trace && (size_t)(slot + 1) * a.nbands * 32 <= g_trace_bytes)
-                          ? g_trace + (size_t)slot * a.nbands * 4
-                          : nullptr;
-            const bool prof = g_prof_events && 2 * slot + 1 < g_prof_n;
-            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot], st) != cudaSuccess) return EDP_ERR_CUDA;
-            if (launch_edp_pass_r1(a, 32 * NWR, smem, st)) return EDP_ERR_CUDA;
-            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
-                return EDP_ERR_CUDA;
-        }
-    }
-    return EDP_OK;
-}
+// Everything about one EDP problem that does not change from pass to pass:
+// which band body runs it, the launch shape and the argument blocks.
+struct SolvePlan {
+    bool r1;          // warp-per-row body (one label axis, Q <= 256)
+    int nbands;
+    int threads;
+    int em;
+    size_t smem;
+    SolveLayout L;
+    PassR1Args o;
+    PassArgs ga;
+};
 
-int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
-              unsigned char *ws, cudaStream_t st) {
-    if (g.R == 1 && g.Q <= 256 && !g_force_general) return run_solve_r1(C, W, H, g, p, labels, ws, st);
+int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
+               unsigned char *ws, SolvePlan *P) {
+    memset(P, 0, sizeof *P);
+    P->L = solve_layout(W, H, g.Q, p->iters);
+    const SolveLayout &L = P->L;
+    int *M[4];
+    for (int k = 0; k < 4; ++k) M[k] = reinterpret_cast<int *>(ws + L.msg[k]);
+    P->r1 = (g.R == 1 && g.Q <= 256 && !g_force_general);
+    if (P->r1) {
+        const int E = (g.Q + 31) / 32;
+        int NWR = g_tune_rb > 0 ? g_tune_rb : 8;
+        NWR = std::max(kMinRowsR1, std::min(NWR, std::min(16, H)));
+        while (NWR > kMinRowsR1 && pass_r1_smem(NWR, E) > (size_t)kMaxSmem) --NWR;
+        P->smem = pass_r1_smem(NWR, E);
+        if (P->smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
+        PassR1Args &a = P->o;
+        a.C = C;
+        for (int k = 0; k < 4; ++k) a.M[k] = M[k];
+        a.labels = labels;
+        a.ll = reinterpret_cast<int2 *>(ws + L.ll);
+        a.status = reinterpret_cast<int *>(ws);
+        a.W = W;
+        a.H = H;
+        a.Q = g.Q;
+        a.E = E;
+        a.EMt = E <= 1 ? 1 : E <= 2 ? 2 : E <= 4 ? 4 : 8;
+        a.lam = p->lambda;
+        a.capv = (int)cap_value(p);
+        a.kc = p->g <= 1 ? 0 : std::min(31, (p->g - 1 + E - 1) / E);
+        a.NWR = NWR;
+        a.nbands = (H + NWR - 1) / NWR;
+        a.grid = a.nbands;
+        a.spin_limit = 4000000;
+        P->nbands = a.nbands;
+        P->threads = 32 * NWR;
+        P->em = a.EMt;
+        return EDP_OK;
+    }
     DpConfig cfg;
     int rc = configure(g, H, false, W, 0, nullptr, &cfg);
     if (rc) return rc;
-    const SolveLayout L = solve_layout(W, H, g.Q, p->iters);
-    rc = cuda_status(cudaMemsetAsync(ws, 0, L.msg[0], st));
-    if (rc) return rc;
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    PassArgs a;
-    memset(&a, 0, sizeof a);
+    PassArgs &a = P->ga;
     a.C = C;
-    for (int k = 0; k < 4; ++k) a.M[k] = reinterpret_cast<int *>(ws + L.msg[k]);
+    for (int k = 0; k < 4; ++k) a.M[k] = M[k];
     a.labels = labels;
     a.status = reinterpret_cast<int *>(ws);
     a.W = W;
@@ -300,29 +282,70 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     a.mode = p->prior_mode;
     a.RB = cfg.RB;
     a.nbands = (H + cfg.RB - 1) / cfg.RB;
-    occ = edp_pass_occupancy(cfg.em, cfg.threads, cfg.smem);
-    a.grid = std::max(1, std::min(a.nbands, std::max(1, occ) * sms));
     a.spin_limit = 2000000;
+    P->nbands = a.nbands;
+    P->threads = cfg.threads;
+    P->em = cfg.em;
+    P->smem = cfg.smem;
+    return EDP_OK;
+}
+
+// Control words that must start from zero before the first pass: status,
+// progress and band counters, and the used hand-off records.
+size_t control_bytes(const SolvePlan &P, int W, int Q) {
+    return P.r1 ? P.L.ll + (size_t)P.nbands * W * Q * 8 : P.L.ll;
+}
+
+int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
+              unsigned char *ws, cudaStream_t st) {
+    SolvePlan P;
+    int rc = plan_solve(C, W, H, g, p, labels, ws, &P);
+    if (rc) return rc;
+    if ((rc = cuda_status(cudaMemsetAsync(ws, 0, control_bytes(P, W, g.Q), st)))) return rc;
+    int grid_g = 1;
+    if (!P.r1) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int occ = edp_pass_occupancy(P.em, P.threads, P.smem);
+        grid_g = std::max(1, std::min(P.nbands, std::max(1, occ) * sms));
+    }
     for (int it = 0; it < p->iters; ++it) {
-        const bool last_it = (it == p->iters - 1);
         for (int pass = 0; pass < 4; ++pass) {
             const int slot = it * 4 + pass;
-            a.pass = pass;
-            a.progress = reinterpret_cast<unsigned *>(ws + L.progress) + (size_t)slot * H;
-            a.band_counter = reinterpret_cast<unsigned *>(ws + L.counters) + slot;
-            // which old message arrays hold data yet (zero before first written)
-            a.read_c = (pass == 0) ? (it > 0) : 1;
-            a.read_d = (pass <= 1) ? (it > 0) : 1;
-            // which outputs a later pass reads (the others are overwritten first)
-            a.write_a = (pass == 3) ? !last_it : 1;
-            a.write_b = (pass == 1) ? 1 : (pass == 3 ? !last_it : 0);
-            a.final_ = (pass == 3 && last_it);
-            a.trace = (g_trace && (size_t)(slot + 1) * a.nbands * 32 <= g_trace_bytes)
-                          ? g_trace + (size_t)slot * a.nbands * 4
-                          : nullptr;
+            const PassFlags f = pass_flags(it, pass, p->iters);
+            unsigned long long *trace = (g_trace && (size_t)(slot + 1) * P.nbands * 32 <= g_trace_bytes)
+                                            ? g_trace + (size_t)slot * P.nbands * 4
+                                            : nullptr;
+            unsigned *counter = reinterpret_cast<unsigned *>(ws + P.L.counters) + slot;
             const bool prof = g_prof_events && 2 * slot + 1 < g_prof_n;
             if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot], st) != cudaSuccess) return EDP_ERR_CUDA;
-            if (launch_edp_pass(a, cfg.em, cfg.threads, cfg.smem, st)) return EDP_ERR_CUDA;
+            if (P.r1) {
+                PassR1Args a = P.o;
+                a.pass = pass;
+                a.read_c = f.read_c;
+                a.read_d = f.read_d;
+                a.write_a = f.write_a;
+                a.write_b = f.write_b;
+                a.final_ = f.final_;
+                a.tag = slot + 1;
+                a.band_counter = counter;
+                a.trace = trace;
+                if (launch_edp_pass_r1(a, P.threads, P.smem, st)) return EDP_ERR_CUDA;
+            } else {
+                PassArgs a = P.ga;
+                a.pass = pass;
+                a.read_c = f.read_c;
+                a.read_d = f.read_d;
+                a.write_a = f.write_a;
+                a.write_b = f.write_b;
+                a.final_ = f.final_;
+                a.progress = reinterpret_cast<unsigned *>(ws + P.L.progress) + (size_t)slot * H;
+                a.band_counter = counter;
+                a.grid = grid_g;
+                a.trace = trace;
+                if (launch_edp_pass(a, P.em, P.threads, P.smem, st)) return EDP_ERR_CUDA;
+            }
             if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
                 return EDP_ERR_CUDA;
         }
@@ -580,6 +603,394 @@ int edp_solve_images_host(const uint8_t *I0_host, const uint8_t *I1_host, const 
         (rc = cuda_status(cudaMemcpyAsync(energy4_host, energy, 4 * 8, cudaMemcpyDeviceToHost, st))))
         return rc;
     return cuda_status(cudaStreamSynchronize(st));
+}
+
+namespace {
+// batch workspace: control block (status | queue | done[kMaxBatch][4*iters])
+// followed by each resident problem's solve workspace and cost volume
+size_t batch_ctrl_bytes(int iters) { return align_up(kHeader + 256 + (size_t)kMaxBatch * 4 * iters * 4); }
+
+size_t problem_bytes(const edp_problem &pr, const Geometry &g) {
+    const int iters = std::max(1, pr.params.iters);
+    return align_up(solve_layout(pr.W, pr.H, g.Q, iters).end + (size_t)pr.W * pr.H * g.Q * 4);
+}
+
+int check_problem(const edp_problem &pr, Geometry *g) {
+    int rc = check_space(&pr.space, g);
+    if (rc) return rc;
+    if ((rc = check_prior(&pr.params))) return rc;
+    if ((rc = check_images(pr.I0, pr.I1, pr.I2, pr.W, pr.H, pr.pitch, &pr.space, &pr.params))) return rc;
+    if (!pr.labels || pr.params.iters < 1) return EDP_ERR_INVALID_ARG;
+    if (pr.params.l1 != 1) return EDP_ERR_UNSUPPORTED;
+    return check_range(pr.W, pr.H, *g, &pr.params);
+}
+
+int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, int iters, unsigned char *ws,
+             cudaStream_t st) {
+    const size_t ctrl = batch_ctrl_bytes(iters);
+    int *status = reinterpret_cast<int *>(ws);
+    ZeroBatch zb;
+    memset(&zb, 0, sizeof zb);
+    zb.ptr[zb.n] = ws;
+    zb.bytes[zb.n++] = ctrl;
+    CostBatch cb;
+    memset(&cb, 0, sizeof cb);
+    EnergyBatch eb;
+    memset(&eb, 0, sizeof eb);
+    static BatchArgs B;  // too large for the stack of some callers; filled and copied into the launch
+    memset(&B, 0, sizeof B);
+    B.n = n;
+    B.slots = 4 * iters;
+    B.queue = reinterpret_cast<unsigned *>(ws + kHeader);
+    B.done = reinterpret_cast<unsigned *>(ws + kHeader + 256);
+    B.status = status;
+    B.spin_limit = 4000000;
+    size_t off = ctrl;
+    long long max_entries = 0, max_pixels = 0;
+    int threads = 32, em = 8;
+    size_t smem = 0;
+    for (int k = 0; k < n; ++k) {
+        const edp_problem &pr = probs[first + k];
+        const Geometry &g = geo[first + k];
+        unsigned char *pws = ws + off;
+        const SolveLayout L = solve_layout(pr.W, pr.H, g.Q, iters);
+        int32_t *C = reinterpret_cast<int32_t *>(pws + L.end);
+        SolvePlan P;
+        int rc = plan_solve(C, pr.W, pr.H, g, &pr.params, pr.labels, pws, &P);
+        if (rc) return rc;
+        off += problem_bytes(pr, g);
+        BatchProblem &bp = B.p[k];
+        bp.r1 = P.r1;
+        bp.nbands = P.nbands;
+        bp.H = pr.H;
+        bp.iters = iters;
+        bp.progress = reinterpret_cast<unsigned *>(pws + L.progress);
+        bp.g = P.ga;
+        bp.o = P.o;
+        bp.g.status = status;
+        bp.o.status = status;
+        B.prefix[k + 1] = B.prefix[k] + P.nbands;
+        threads = std::max(threads, P.threads);
+        smem = std::max(smem, P.smem);
+        em = std::max(em, P.em);
+        zb.ptr[zb.n] = pws;
+        zb.bytes[zb.n++] = control_bytes(P, pr.W, g.Q);
+        CostArgs &c = cb.c[k];
+        c.I0 = pr.I0;
+        c.I1 = pr.I1;
+        c.I2 = pr.I2;
+        c.W = pr.W;
+        c.H = pr.H;
+        c.pitch = pr.pitch;
+        c.R = pr.space.R;
+        c.Q = g.Q;
+        c.Q0 = pr.space.Q[0];
+        c.Q1 = pr.space.Q[1];
+        c.Q2 = pr.space.Q[2];
+        for (int r = 0; r < 3; ++r) {
+            c.vmin[r] = pr.space.vmin[r];
+            c.step[r] = r < pr.space.R ? pr.space.step[r] : 1;
+        }
+        c.l2 = pr.params.l2;
+        c.cmax = pr.params.cmax;
+        c.mode = pr.params.cost_mode;
+        c.C = C;
+        EnergyArgs &e = eb.e[k];
+        e.C = C;
+        e.labels = pr.labels;
+        e.W = pr.W;
+        e.H = pr.H;
+        e.Q = g.Q;
+        e.R = pr.space.R;
+        e.Q0 = pr.space.Q[0];
+        e.Q1 = pr.space.Q[1];
+        e.lam = pr.params.lambda;
+        e.g = pr.params.g;
+        e.l1 = pr.params.l1;
+        e.mode = pr.params.prior_mode;
+        e.out4 = reinterpret_cast<long long *>(pr.energy4);
+        if (pr.energy4) {
+            zb.ptr[zb.n] = pr.energy4;
+            zb.bytes[zb.n++] = 4 * sizeof(int64_t);
+        }
+        max_entries = std::max(max_entries, (long long)pr.W * pr.H * g.Q);
+        max_pixels = std::max(max_pixels, (long long)pr.W * pr.H);
+    }
+    B.per_slot = B.prefix[n];
+    cb.n = n;
+    eb.n = n;
+    em = em <= 8 ? 8 : 16;
+    threads = std::min(kMaxThreads, (threads + 31) / 32 * 32);
+    if (launch_zero_batched(zb, st)) return EDP_ERR_CUDA;
+    if (launch_cost_batched(cb, max_entries, st)) return EDP_ERR_CUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = edp_batched_occupancy(em, threads, smem);
+    const int grid = std::max(1, std::min(B.slots * B.per_slot, std::max(1, occ) * sms));
+    if (launch_edp_batched(B, em, threads, smem, grid, st)) return EDP_ERR_CUDA;
+    if (launch_energy_batched(eb, max_pixels, st)) return EDP_ERR_CUDA;
+    return EDP_OK;
+}
+}  // namespace
+
+size_t edp_batch_workspace_size(const edp_problem *probs, int n) {
+    if (!probs || n < 1) return 0;
+    size_t total = 0;
+    int iters = 1;
+    for (int k = 0; k < n; ++k) {
+        Geometry g;
+        if (check_space(&probs[k].space, &g) || probs[k].W < 1 || probs[k].H < 1) return 0;
+        total += problem_bytes(probs[k], g);
+        iters = std::max(iters, probs[k].params.iters);
+    }
+    return batch_ctrl_bytes(iters) + total;
+}
+
+int edp_solve_batched(const edp_problem *probs, int n, void *ws, size_t ws_bytes, edp_stream_t stream) {
+    if (!probs || n < 1 || !ws) return EDP_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    Geometry geo_small[64];
+    Geometry *geo = geo_small;
+    if (n > 64) return EDP_ERR_UNSUPPORTED;  // larger batches: call again per 64 problems
+    for (int k = 0; k < n; ++k) {
+        int rc = check_problem(probs[k], &geo[k]);
+        if (rc) return rc;
+    }
+    int first = 0;
+    while (first < n) {
+        const int iters = probs[first].params.iters;
+        const size_t ctrl = batch_ctrl_bytes(iters);
+        size_t used = ctrl;
+        int cnt = 0;
+        while (first + cnt < n && cnt < kMaxBatch && probs[first + cnt].params.iters == iters) {
+            const size_t b = problem_bytes(probs[first + cnt], geo[first + cnt]);
+            if (used + b > ws_bytes) break;
+            used += b;
+            ++cnt;
+        }
+        if (cnt == 0) return EDP_ERR_WORKSPACE;
+        int rc = run_wave(probs, geo, first, cnt, iters, w, st);
+        if (rc) return rc;
+        first += cnt;
+    }
+    return EDP_OK;
+}
+
+namespace {
+struct WinLayout {
+    size_t counters, ll, msg[4], end;
+};
+WinLayout win_layout(int W, int H, int Qw, int iters) {
+    WinLayout L;
+    L.counters = kHeader;
+    L.ll = align_up(L.counters + 4 * (size_t)iters * 4);
+    size_t off = align_up(L.ll + (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * W * Qw * 8);
+    for (int k = 0; k < 4; ++k) {
+        L.msg[k] = off;
+        off = align_up(off + (size_t)W * H * Qw * 4);
+    }
+    L.end = off;
+    return L;
+}
+
+int check_window(const edp_label_space *space, const edp_params *params, int win, Geometry *g) {
+    int rc = check_space(space, g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if (space->R > 2 || params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    if (win < 1 || (win & 1) == 0 || win > 15) return EDP_ERR_UNSUPPORTED;
+    for (int r = 0; r < space->R; ++r)
+        if (space->Q[r] < win) return EDP_ERR_INVALID_ARG;
+    return EDP_OK;
+}
+}  // namespace
+
+size_t edp_workspace_size_windowed(int W, int H, const edp_label_space *space, const edp_params *params,
+                                   int win) {
+    Geometry g;
+    if (W < 1 || H < 1 || check_window(space, params, win, &g)) return 0;
+    const int Qw = space->R == 2 ? win * win : win;
+    return win_layout(W, H, Qw, std::max(1, params->iters)).end;
+}
+
+int edp_cost_window(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H, int pitch,
+                    const edp_label_space *space, const edp_params *params, const int32_t *centre, int win,
+                    int32_t *Cw, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_window(space, params, win, &g);
+    if (rc) return rc;
+    if ((rc = check_images(I0, I1, I2, W, H, pitch, space, params))) return rc;
+    if (params->cost_mode == EDP_COST_PAIR_STEREO3) return EDP_ERR_UNSUPPORTED;
+    if (!centre || !Cw) return EDP_ERR_INVALID_ARG;
+    CostArgs a;
+    memset(&a, 0, sizeof a);
+    a.I0 = I0;
+    a.I1 = I1;
+    a.I2 = I2;
+    a.W = W;
+    a.H = H;
+    a.pitch = pitch;
+    a.R = space->R;
+    a.Q0 = space->Q[0];
+    a.Q1 = space->Q[1];
+    for (int r = 0; r < 3; ++r) {
+        a.vmin[r] = space->vmin[r];
+        a.step[r] = r < space->R ? space->step[r] : 1;
+    }
+    a.l2 = params->l2;
+    a.cmax = params->cmax;
+    a.mode = params->cost_mode;
+    a.C = Cw;
+    return launch_cost_window(a, centre, win, (cudaStream_t)stream) ? EDP_ERR_CUDA : EDP_OK;
+}
+
+int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W, int H,
+                       const edp_label_space *space, const edp_params *params, int32_t *labels, void *ws,
+                       size_t ws_bytes, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_window(space, params, win, &g);
+    if (rc) return rc;
+    if (!Cw || !centre || !labels || !ws || W < 1 || H < 1 || params->iters < 1) return EDP_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
+    if (ws_bytes < edp_workspace_size_windowed(W, H, space, params, win)) return EDP_ERR_WORKSPACE;
+    Geometry gw = g;
+    gw.R = space->R;
+    if ((rc = check_range(W, H, gw, params))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    const int Qw = space->R == 2 ? win * win : win;
+    const WinLayout L = win_layout(W, H, Qw, params->iters);
+    WinArgs a;
+    memset(&a, 0, sizeof a);
+    a.Cw = Cw;
+    for (int k = 0; k < 4; ++k) a.M[k] = reinterpret_cast<int *>(w + L.msg[k]);
+    a.labels = labels;
+    a.ll = reinterpret_cast<int2 *>(w + L.ll);
+    a.centre = centre;
+    a.status = reinterpret_cast<int *>(w);
+    a.W = W;
+    a.H = H;
+    a.Qw = Qw;
+    a.E = (Qw + 31) / 32;
+    a.EMt = a.E <= 1 ? 1 : a.E <= 2 ? 2 : a.E <= 4 ? 4 : 8;
+    a.n = win;
+    a.R = space->R;
+    a.Q0 = space->Q[0];
+    a.Q1 = space->Q[1];
+    a.lam = params->lambda;
+    a.capv = (int)cap_value(params);
+    a.mode = params->prior_mode;
+    int NWR = g_tune_rb > 0 ? g_tune_rb : 8;
+    NWR = std::max(kMinRowsR1, std::min(NWR, std::min(16, H)));
+    while (NWR > kMinRowsR1 && pass_win_smem(NWR, a.E) > (size_t)kMaxSmem) --NWR;
+    const size_t smem = pass_win_smem(NWR, a.E);
+    if (smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
+    a.NWR = NWR;
+    a.nbands = (H + NWR - 1) / NWR;
+    a.grid = a.nbands;
+    a.spin_limit = 4000000;
+    if ((rc = cuda_status(cudaMemsetAsync(w, 0, L.ll + (size_t)a.nbands * W * Qw * 8, st)))) return rc;
+    for (int it = 0; it < params->iters; ++it)
+        for (int pass = 0; pass < 4; ++pass) {
+            const int slot = it * 4 + pass;
+            const PassFlags f = pass_flags(it, pass, params->iters);
+            a.pass = pass;
+            a.read_c = f.read_c;
+            a.read_d = f.read_d;
+            a.write_a = f.write_a;
+            a.write_b = f.write_b;
+            a.final_ = f.final_;
+            a.tag = slot + 1;
+            a.band_counter = reinterpret_cast<unsigned *>(w + L.counters) + slot;
+            const bool prof = g_prof_events && 2 * slot + 1 < g_prof_n;
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot], st) != cudaSuccess) return EDP_ERR_CUDA;
+            if (launch_edp_pass_win(a, 32 * NWR, smem, st)) return EDP_ERR_CUDA;
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
+                return EDP_ERR_CUDA;
+        }
+    return EDP_OK;
+}
+
+int edp_wta(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, const edp_label_space *space,
+            const edp_params *params, int32_t *labels, int32_t *cost, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_images(I0, I1, nullptr, W, H, pitch, space, params))) return rc;
+    if (params->cost_mode != EDP_COST_PAIR || space->R > 2) return EDP_ERR_UNSUPPORTED;
+    if (!labels) return EDP_ERR_INVALID_ARG;
+    CostArgs a;
+    memset(&a, 0, sizeof a);
+    a.I0 = I0;
+    a.I1 = I1;
+    a.W = W;
+    a.H = H;
+    a.pitch = pitch;
+    a.R = space->R;
+    a.Q = g.Q;
+    a.Q0 = space->Q[0];
+    a.Q1 = space->Q[1];
+    for (int r = 0; r < 3; ++r) {
+        a.vmin[r] = space->vmin[r];
+        a.step[r] = r < space->R ? space->step[r] : 1;
+    }
+    a.l2 = params->l2;
+    a.cmax = params->cmax;
+    return wta_launch(a, labels, cost, (cudaStream_t)stream) ? EDP_ERR_CUDA : EDP_OK;
+}
+
+long long edp_net_param_count(void) { return net_param_count(); }
+
+size_t edp_net_workspace_size(int N, int H, int W) {
+    if (N < 1 || H < 1 || W < 1) return 0;
+    return net_workspace_bytes((long long)N * H * W);
+}
+
+int edp_net_forward(const float *params, const void *x, int N, int H, int W, float *out, void *ws, size_t ws_bytes,
+                    edp_stream_t stream) {
+    if (!params || !x || !out || !ws || N < 1 || H < 1 || W < 1) return EDP_ERR_INVALID_ARG;
+    if (ws_bytes < edp_net_workspace_size(N, H, W)) return EDP_ERR_WORKSPACE;
+    return net_forward(params, x, N, H, W, out, static_cast<unsigned char *>(ws), (cudaStream_t)stream)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
+}
+
+int edp_net_backward(const float *params, const float *out, const float *target, int N, int H, int W, float *grad,
+                     double *loss, void *ws, size_t ws_bytes, edp_stream_t stream) {
+    if (!params || !out || !target || !grad || !loss || !ws || N < 1 || H < 1 || W < 1) return EDP_ERR_INVALID_ARG;
+    if (ws_bytes < edp_net_workspace_size(N, H, W)) return EDP_ERR_WORKSPACE;
+    return net_backward(params, out, target, N, H, W, grad, loss, static_cast<unsigned char *>(ws),
+                        (cudaStream_t)stream)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
+}
+
+int edp_net_adam(float *params, const float *grad, float *m, float *v, float lr, float beta1, float beta2, float eps,
+                 int step, edp_stream_t stream) {
+    if (!params || !grad || !m || !v || step < 1) return EDP_ERR_INVALID_ARG;
+    return net_adam_step(params, grad, m, v, net_param_count(), lr, beta1, beta2, eps, step, (cudaStream_t)stream)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
+}
+
+int edp_net_features(const uint8_t *I0, const uint8_t *I1, const int32_t *wta_labels, const int32_t *wta_cost,
+                     int W, int H, const edp_label_space *space, float scale, float cmax, void *x,
+                     edp_stream_t stream) {
+    if (!I0 || !I1 || !wta_labels || !wta_cost || !x || !space || W < 1 || H < 1) return EDP_ERR_INVALID_ARG;
+    if (space->R != 2 || !(scale > 0.f) || !(cmax > 0.f)) return EDP_ERR_INVALID_ARG;
+    return net_features_launch(I0, I1, wta_labels, wta_cost, W, H, space->Q[0], space->Q[1], scale, cmax, x,
+                               (cudaStream_t)stream)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
+}
+
+int edp_net_centres(const float *out, int n, const edp_label_space *space, int32_t *centre, edp_stream_t stream) {
+    if (!out || !centre || !space || n < 1 || space->R != 2) return EDP_ERR_INVALID_ARG;
+    return net_centres_launch(out, n, space->Q[0], space->Q[1], centre, (cudaStream_t)stream) ? EDP_ERR_CUDA
+                                                                                                : EDP_OK;
 }
 
 int edp_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stream_t stream) {

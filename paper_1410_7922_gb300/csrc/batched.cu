@@ -1,0 +1,122 @@
+// batched.cu -- many independent EDP problems (uneven sizes and label
+// spaces) solved by one persistent launch.
+//
+// Work items are (scan pass, problem, row band), ordered pass-major.  Blocks
+// take items in that order from one global counter.  Every dependency of an
+// item is an earlier item:
+//   - the previous band of the same pass and problem (the band bodies wait
+//     for it row by row);
+//   - the previous pass of the same problem (a per-problem counter of
+//     finished bands, waited for with a bounded spin).
+// A block therefore only ever waits for an item that an already running
+// block owns.  Problems of different sizes fill the GPU together; the
+// heterogeneity lives in the per-problem descriptors, passed by value as the
+// kernel's parameter block (no host tables, so the launch can be captured in
+// a CUDA graph).
+#include "pass_gen.cuh"
+#include "pass_r1.cuh"
+
+namespace edp {
+
+static_assert(sizeof(BatchArgs) <= 32000, "batch descriptors must fit the kernel parameter space");
+
+template <int EM>
+__global__ void __launch_bounds__(kMaxThreads) edp_batched_kernel(const __grid_constant__ BatchArgs B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_abort = (*(volatile int *)B.status != 0);
+    __syncthreads();
+    if (s_abort) return;
+    const int total = B.slots * B.per_slot;
+    while (true) {
+        if (tid == 0) s_item = (int)atomicAdd(B.queue, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int slot = item / B.per_slot;
+        const int k = item - slot * B.per_slot;
+        int i = 0;
+        while (B.prefix[i + 1] <= k) ++i;
+        const int band = k - B.prefix[i];
+        const BatchProblem &P = B.p[i];
+        // the previous pass of this problem must be complete
+        if (slot > 0 && tid == 0) {
+            const unsigned need = (unsigned)P.nbands;
+            const long long got =
+                wait_progress(B.done + (size_t)i * B.slots + (slot - 1), need, B.spin_limit, B.status);
+            if (got < 0) {
+                atomicCAS(B.status, 0, EDP_ERR_TIMEOUT_CODE);
+                s_abort = 1;
+            }
+        }
+        __syncthreads();
+        if (s_abort) return;
+        const int it = slot / 4, pass = slot % 4;
+        const PassFlags f = pass_flags(it, pass, P.iters);
+        bool ok;
+        if (P.r1) {
+            PassR1Args a = P.o;
+            a.pass = pass;
+            a.read_c = f.read_c;
+            a.read_d = f.read_d;
+            a.write_a = f.write_a;
+            a.write_b = f.write_b;
+            a.final_ = f.final_;
+            a.tag = slot + 1;
+            ok = r1_band<EM>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+        } else {
+            PassArgs a = P.g;
+            a.pass = pass;
+            a.read_c = f.read_c;
+            a.read_d = f.read_d;
+            a.write_a = f.write_a;
+            a.write_b = f.write_b;
+            a.final_ = f.final_;
+            a.progress = P.progress + (size_t)slot * P.H;
+            ok = gen_band<EM>(a, band, smem_raw, &s_abort);
+        }
+        if (!ok) return;
+        // both bodies end with a block barrier: every write of this band is done
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(B.done + (size_t)i * B.slots + slot, 1u);
+        }
+    }
+}
+
+int edp_batched_occupancy(int em, int threads, size_t smem) {
+    int occ = 0;
+    if (em == 8) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(edp_batched_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edp_batched_kernel<8>, threads, smem);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(edp_batched_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edp_batched_kernel<16>, threads, smem);
+    }
+    return occ;
+}
+
+int launch_edp_batched(const BatchArgs &a, int em, int threads, size_t smem, int grid, cudaStream_t st) {
+    switch (em) {
+#define EDP_CASE(N)                                                                          \
+    case N: {                                                                                \
+        auto k = edp_batched_kernel<N>;                                                      \
+        if (smem > 48 * 1024)                                                                \
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k<<<grid, threads, smem, st>>>(a);                                                   \
+        break;                                                                               \
+    }
+        EDP_CASE(8)
+        EDP_CASE(16)
+#undef EDP_CASE
+    default:
+        return -1;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace edp

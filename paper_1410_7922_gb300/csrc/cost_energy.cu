@@ -17,7 +17,7 @@ __device__ __forceinline__ int cost_term(const uint8_t *I, const uint8_t *I0, in
 
 // One thread per (pixel, 4 consecutive labels): the label dimension is the
 // fastest, so consecutive threads write consecutive 16-byte chunks.
-__global__ void cost_kernel(CostArgs A) {
+__device__ __forceinline__ void cost_body(const CostArgs &A) {
     const long long n = (long long)A.W * A.H * A.Q;
     const long long stride = (long long)gridDim.x * blockDim.x * 4;
     for (long long e0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; e0 < n; e0 += stride) {
@@ -53,6 +53,20 @@ __global__ void cost_kernel(CostArgs A) {
     }
 }
 
+__global__ void cost_kernel(CostArgs A) { cost_body(A); }
+
+// one launch for a wave of problems: blockIdx.y selects the problem
+__global__ void cost_batched_kernel(const __grid_constant__ CostBatch B) { cost_body(B.c[blockIdx.y]); }
+
+int launch_cost_batched(const CostBatch &a, long long max_entries, cudaStream_t st) {
+    const int threads = 256;
+    long long blocks = (max_entries + 4LL * threads - 1) / (4LL * threads);
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    if (blocks < 1) blocks = 1;
+    cost_batched_kernel<<<dim3((unsigned)blocks, a.n), threads, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
 int launch_cost(const CostArgs &a, cudaStream_t st) {
     const long long n = (long long)a.W * a.H * a.Q;
     const int threads = 256;
@@ -83,7 +97,7 @@ __device__ __forceinline__ long long prior_v(int a, int b, const EnergyArgs &A) 
     return v;
 }
 
-__global__ void energy_kernel(EnergyArgs A) {
+__device__ __forceinline__ void energy_body(const EnergyArgs &A) {
     long long e[3] = {0, 0, 0};
     const long long n = (long long)A.W * A.H;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -109,6 +123,40 @@ __global__ void energy_kernel(EnergyArgs A) {
         atomicAdd(reinterpret_cast<unsigned long long *>(A.out4 + threadIdx.x), (unsigned long long)s);
         atomicAdd(reinterpret_cast<unsigned long long *>(A.out4 + 3), (unsigned long long)s);
     }
+}
+
+__global__ void energy_kernel(EnergyArgs A) { energy_body(A); }
+
+__global__ void energy_batched_kernel(const __grid_constant__ EnergyBatch B) {
+    if (B.e[blockIdx.y].out4) energy_body(B.e[blockIdx.y]);
+}
+
+int launch_energy_batched(const EnergyBatch &a, long long max_pixels, cudaStream_t st) {
+    const int threads = 256;
+    long long blocks = (max_pixels + threads - 1) / threads;
+    if (blocks > 152LL * 2) blocks = 152LL * 2;
+    if (blocks < 1) blocks = 1;
+    energy_batched_kernel<<<dim3((unsigned)blocks, a.n), threads, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+// zero a list of device regions (control words, hand-off records, energy
+// accumulators of a wave) in one launch: blockIdx.y selects the region
+__global__ void zero_batched_kernel(const __grid_constant__ ZeroBatch Z) {
+    unsigned char *p = static_cast<unsigned char *>(Z.ptr[blockIdx.y]);
+    const size_t n = Z.bytes[blockIdx.y];
+    const size_t n16 = ((reinterpret_cast<uintptr_t>(p) & 15) == 0) ? n / 16 : 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+        reinterpret_cast<int4 *>(p)[i] = make_int4(0, 0, 0, 0);
+    for (size_t i = n16 * 16 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = 0;
+}
+
+int launch_zero_batched(const ZeroBatch &a, cudaStream_t st) {
+    if (a.n == 0) return 0;
+    zero_batched_kernel<<<dim3(64, a.n), 256, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 int launch_energy(const EnergyArgs &a, cudaStream_t st) {

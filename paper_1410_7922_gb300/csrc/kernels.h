@@ -10,6 +10,25 @@ namespace edp {
 
 constexpr int EDP_ERR_TIMEOUT_CODE = 5;  // == EDP_ERR_TIMEOUT of edp.h
 
+// Which message vectors a scan pass reads and writes (pass 0..3 = P1..P4 of
+// iteration it of iters).  An old vector is read only once some earlier pass
+// wrote it; a new vector is written only if a later pass reads it before it
+// is overwritten (P1's m_{+y} and P3's m_{-y} are overwritten by P2 / P4;
+// the last pass of the last iteration writes none).
+struct PassFlags {
+    int read_c, read_d, write_a, write_b, final_;
+};
+__host__ __device__ inline PassFlags pass_flags(int it, int pass, int iters) {
+    const bool last_it = (it == iters - 1);
+    PassFlags f;
+    f.read_c = (pass == 0) ? (it > 0) : 1;
+    f.read_d = (pass <= 1) ? (it > 0) : 1;
+    f.write_a = (pass == 3) ? !last_it : 1;
+    f.write_b = (pass == 1) ? 1 : (pass == 3 ? !last_it : 0);
+    f.final_ = (pass == 3 && last_it);
+    return f;
+}
+
 // one EDP scan pass
 struct PassArgs {
     const int *C;         // [H][W][Q]
@@ -55,6 +74,52 @@ struct PassR1Args {
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st);
 size_t pass_r1_smem(int NWR, int E);
 
+// one EDP scan pass on per-pixel label boxes (pass_win.cu)
+struct WinArgs {
+    const int *Cw;          // [H][W][Qw] cost of each pixel's box labels
+    int *M[4];              // messages, box coordinates of the receiving pixel
+    int *labels;            // [H][W] full-space label index
+    int2 *ll;               // [nbands][W][Qw] hand-off records
+    const int *centre;      // [H][W][R] proposed centres (label coordinates)
+    unsigned *band_counter;
+    int *status;
+    int W, H, Qw, E, EMt;
+    int n, R, Q0, Q1;       // box side, label axes, full-space sizes
+    int lam, capv, mode;
+    int pass, read_c, read_d, write_a, write_b, final_;
+    int NWR, nbands, grid, tag;
+    long long spin_limit;
+};
+int launch_edp_pass_win(const WinArgs &a, int threads, size_t smem, cudaStream_t st);
+size_t pass_win_smem(int NWR, int E);
+
+// batched solve: up to kMaxBatch problems of one wave, passed by value
+constexpr int kMaxBatch = 48;
+struct BatchProblem {
+    int r1;            // 1: warp-per-row band body, 0: general band body
+    int nbands;
+    int H;             // rows (progress arrays are [slot][H])
+    int iters;
+    unsigned *progress;  // general body: [4*iters][H]
+    PassArgs g;        // general body fields (pass / flags / progress set per item)
+    PassR1Args o;      // one-axis body fields
+};
+struct BatchArgs {
+    int n;
+    int slots;            // 4 * iters (shared by the wave)
+    int per_slot;         // sum of nbands over the wave
+    int prefix[kMaxBatch + 1];
+    unsigned *queue;      // work-item counter
+    unsigned *done;       // [n][slots] bands finished
+    int *status;
+    long long spin_limit;
+    BatchProblem p[kMaxBatch];
+};
+int launch_edp_batched(const BatchArgs &a, int em, int threads, size_t smem, int grid, cudaStream_t st);
+int edp_batched_occupancy(int em, int threads, size_t smem);
+
+
+
 // scanline DP
 struct ScanArgs {
     const int *C;
@@ -90,5 +155,37 @@ struct EnergyArgs {
     long long *out4;
 };
 int launch_energy(const EnergyArgs &a, cudaStream_t st);
+
+struct CostBatch {
+    int n;
+    CostArgs c[kMaxBatch];
+};
+struct EnergyBatch {
+    int n;
+    EnergyArgs e[kMaxBatch];
+};
+struct ZeroBatch {
+    int n;
+    void *ptr[2 * kMaxBatch + 1];
+    size_t bytes[2 * kMaxBatch + 1];
+};
+int launch_cost_batched(const CostBatch &a, long long max_entries, cudaStream_t st);
+int launch_energy_batched(const EnergyBatch &a, long long max_pixels, cudaStream_t st);
+int launch_zero_batched(const ZeroBatch &a, cudaStream_t st);
+int launch_cost_window(const CostArgs &a, const int *centre, int n, cudaStream_t st);
+
+// proposal network (net.cu)
+long long net_param_count();
+size_t net_workspace_bytes(long long npix);
+int net_forward(const float *params, const void *x, int N, int H, int W, float *out, unsigned char *ws,
+                cudaStream_t st);
+int net_backward(const float *params, const float *out, const float *target, int N, int H, int W, float *grad,
+                 double *loss, unsigned char *ws, cudaStream_t st);
+int net_adam_step(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2, float eps,
+                  int step, cudaStream_t st);
+int net_features_launch(const uint8_t *I0, const uint8_t *I1, const int *wta_q, const int *wta_cost, int W, int H,
+                        int Q0, int Q1, float scale, float cmax, void *out, cudaStream_t st);
+int net_centres_launch(const float *out, int n, int Q0, int Q1, int *centre, cudaStream_t st);
+int wta_launch(const CostArgs &a, int *labels, int *cost, cudaStream_t st);
 
 }  // namespace edp

@@ -40,6 +40,13 @@ class Params(ctypes.Structure):
                 ("cost_mode", ctypes.c_int32), ("iters", ctypes.c_int32)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("I0", ctypes.c_void_p), ("I1", ctypes.c_void_p), ("I2", ctypes.c_void_p),
+                ("W", ctypes.c_int32), ("H", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("space", LabelSpace), ("params", Params), ("labels", ctypes.c_void_p),
+                ("energy4", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -68,6 +75,19 @@ def load() -> ctypes.CDLL:
         "edp_solve_images": ([P, P, P, I, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_solve_images_host": ([P, P, P, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_get_device_status": ([P, SZ, ctypes.POINTER(I), P], I),
+        "edp_batch_workspace_size": ([ctypes.POINTER(Problem), I], SZ),
+        "edp_workspace_size_windowed": ([I, I, LS, PR, I], SZ),
+        "edp_cost_window": ([P, P, P, I, I, I, LS, PR, P, I, P, P], I),
+        "edp_solve_windowed": ([P, P, I, I, I, LS, PR, P, P, SZ, P], I),
+        "edp_wta": ([P, P, I, I, I, LS, PR, P, P, P], I),
+        "edp_net_param_count": ([], ctypes.c_longlong),
+        "edp_net_workspace_size": ([I, I, I], SZ),
+        "edp_net_forward": ([P, P, I, I, I, P, P, SZ, P], I),
+        "edp_net_backward": ([P, P, P, I, I, I, P, P, P, SZ, P], I),
+        "edp_net_adam": ([P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P], I),
+        "edp_net_features": ([P, P, P, P, I, I, LS, ctypes.c_float, ctypes.c_float, P, P], I),
+        "edp_net_centres": ([P, I, LS, P, P], I),
+        "edp_solve_batched": ([ctypes.POINTER(Problem), I, P, SZ, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -81,7 +101,10 @@ def exported_symbols() -> list[str]:
     return ["edp_version", "edp_status_string", "edp_workspace_size", "edp_set_tuning", "edp_set_profile_events",
             "edp_set_trace",
             "edp_cost_volume", "edp_scanline_dp", "edp_solve", "edp_energy", "edp_solve_images",
-            "edp_solve_images_host", "edp_get_device_status"]
+            "edp_solve_images_host", "edp_get_device_status", "edp_batch_workspace_size",
+            "edp_solve_batched", "edp_workspace_size_windowed", "edp_cost_window", "edp_solve_windowed",
+            "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_forward", "edp_net_backward",
+            "edp_net_adam", "edp_net_features", "edp_net_centres"]
 
 
 def status_string(code: int) -> str:
@@ -305,3 +328,163 @@ def get_device_status(ws, stream=None) -> int:
     rc = load().edp_get_device_status(_dev(ws, torch.uint8, "ws"), ws.numel(), ctypes.byref(st), _stream(stream))
     _check(rc, "get_device_status")
     return int(st.value)
+
+
+def make_problems(items) -> ctypes.Array:
+    """Problem descriptors from dicts with device tensors I0, I1, I2 (or
+    None), labels, energy4 (or None) and space / prior / l2 / cmax /
+    cost_mode / iters.  Keep the returned array alive while it is in use."""
+    arr = (Problem * len(items))()
+    for k, it in enumerate(items):
+        H, W = it["I0"].shape
+        pr = arr[k]
+        pr.I0 = _dev(it["I0"], torch.uint8, "I0")
+        pr.I1 = _dev(it["I1"], torch.uint8, "I1")
+        pr.I2 = _dev(it.get("I2"), torch.uint8, "I2")
+        pr.W, pr.H, pr.pitch = W, H, it["I0"].stride(0)
+        pr.space = label_space(it["space"])
+        pr.params = params(it["prior"], l2=it.get("l2", 1), cmax=it.get("cmax", 20),
+                           cost_mode=it.get("cost_mode", "pair"), iters=it.get("iters", 1))
+        pr.labels = _dev(it["labels"], torch.int32, "labels")
+        pr.energy4 = _dev(it.get("energy4"), torch.int64, "energy4")
+    return arr
+
+
+def batch_workspace_size(problems: ctypes.Array) -> int:
+    n = load().edp_batch_workspace_size(problems, len(problems))
+    if n == 0:
+        raise EdpError(ERR_INVALID_ARG, "batch_workspace_size")
+    return int(n)
+
+
+def solve_batched(problems: ctypes.Array, ws, stream=None) -> None:
+    """edp_solve_batched over descriptors from make_problems."""
+    rc = load().edp_solve_batched(problems, len(problems), _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(rc, "solve_batched")
+
+
+def cost_window(I0, I1, I2, space: dict, l2: int, cmax: int, centre, win: int, cost_mode: str = "pair",
+                out=None, stream=None):
+    """edp_cost_window: box costs int32 [H][W][win^R] around int32 centres [H][W][R]."""
+    H, W = I0.shape
+    R = int(space["R"])
+    if out is None:
+        out = torch.empty((H, W, win ** R), dtype=torch.int32, device=I0.device)
+    ls = label_space(space)
+    pr = params({"lam": 0, "g": 1}, l2=l2, cmax=cmax, cost_mode=cost_mode)
+    rc = load().edp_cost_window(_dev(I0, torch.uint8, "I0"), _dev(I1, torch.uint8, "I1"),
+                                _dev(I2, torch.uint8, "I2"), W, H, I0.stride(0), ctypes.byref(ls),
+                                ctypes.byref(pr), _dev(centre, torch.int32, "centre"), int(win),
+                                _dev(out, torch.int32, "Cw"), _stream(stream))
+    _check(rc, "cost_window")
+    return out
+
+
+def workspace_windowed(W: int, H: int, space: dict, prior: dict, win: int, iters: int = 1, device="cuda"):
+    ls, pr = label_space(space), params(prior, iters=iters)
+    n = load().edp_workspace_size_windowed(int(W), int(H), ctypes.byref(ls), ctypes.byref(pr), int(win))
+    if n == 0:
+        raise EdpError(ERR_INVALID_ARG, "workspace_size_windowed")
+    return torch.empty(int(n), dtype=torch.uint8, device=device)
+
+
+def solve_windowed(Cw, centre, win: int, space: dict, prior: dict, iters: int = 1, ws=None, labels=None,
+                   stream=None):
+    """edp_solve_windowed: full-space labels int32 [H][W]."""
+    H, W, _ = Cw.shape
+    if ws is None:
+        ws = workspace_windowed(W, H, space, prior, win, iters, device=Cw.device)
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=Cw.device)
+    ls, pr = label_space(space), params(prior, iters=iters)
+    rc = load().edp_solve_windowed(_dev(Cw, torch.int32, "Cw"), _dev(centre, torch.int32, "centre"), int(win), W, H,
+                                   ctypes.byref(ls), ctypes.byref(pr), _dev(labels, torch.int32, "labels"),
+                                   _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(rc, "solve_windowed")
+    return labels
+
+
+def wta(I0, I1, space: dict, l2: int, cmax: int, stream=None):
+    """edp_wta: (labels int32 [H][W], cost int32 [H][W]) over the full label space."""
+    H, W = I0.shape
+    lab = torch.empty((H, W), dtype=torch.int32, device=I0.device)
+    cost = torch.empty((H, W), dtype=torch.int32, device=I0.device)
+    ls = label_space(space)
+    pr = params({"lam": 0, "g": 1}, l2=l2, cmax=cmax)
+    rc = load().edp_wta(_dev(I0, torch.uint8, "I0"), _dev(I1, torch.uint8, "I1"), W, H, I0.stride(0),
+                        ctypes.byref(ls), ctypes.byref(pr), _dev(lab, torch.int32, "labels"),
+                        _dev(cost, torch.int32, "cost"), _stream(stream))
+    _check(rc, "wta")
+    return lab, cost
+
+
+def net_param_count() -> int:
+    return int(load().edp_net_param_count())
+
+
+def net_workspace(N: int, H: int, W: int, device="cuda"):
+    n = load().edp_net_workspace_size(int(N), int(H), int(W))
+    if n == 0:
+        raise EdpError(ERR_INVALID_ARG, "net_workspace_size")
+    return torch.empty(int(n), dtype=torch.uint8, device=device)
+
+
+def net_forward(params_f32, x_bf16, ws, out=None, stream=None):
+    """edp_net_forward: x bf16 [N][H][W][5] -> float32 [N][H][W][2]."""
+    N, H, W, _ = x_bf16.shape
+    if out is None:
+        out = torch.empty((N, H, W, 2), dtype=torch.float32, device=x_bf16.device)
+    rc = load().edp_net_forward(_dev(params_f32, torch.float32, "params"), _dev(x_bf16, torch.bfloat16, "x"), N, H, W,
+                                _dev(out, torch.float32, "out"), _dev(ws, torch.uint8, "ws"), ws.numel(),
+                                _stream(stream))
+    _check(rc, "net_forward")
+    return out
+
+
+def net_backward(params_f32, out, target, ws, grad=None, loss=None, stream=None):
+    """edp_net_backward after net_forward: (grad float32 like params, loss float64 [1])."""
+    N, H, W, _ = out.shape
+    if grad is None:
+        grad = torch.empty_like(params_f32)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=out.device)
+    rc = load().edp_net_backward(_dev(params_f32, torch.float32, "params"), _dev(out, torch.float32, "out"),
+                                 _dev(target, torch.float32, "target"), N, H, W, _dev(grad, torch.float32, "grad"),
+                                 _dev(loss, torch.float64, "loss"), _dev(ws, torch.uint8, "ws"), ws.numel(),
+                                 _stream(stream))
+    _check(rc, "net_backward")
+    return grad, loss
+
+
+def net_adam(params_f32, grad, m, v, lr: float, step: int, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8,
+             stream=None) -> None:
+    rc = load().edp_net_adam(_dev(params_f32, torch.float32, "params"), _dev(grad, torch.float32, "grad"),
+                             _dev(m, torch.float32, "m"), _dev(v, torch.float32, "v"), float(lr), float(b1), float(b2),
+                             float(eps), int(step), _stream(stream))
+    _check(rc, "net_adam")
+
+
+def net_features(I0, I1, wta_labels, wta_cost, space: dict, scale: float, cmax: float, out=None, stream=None):
+    """edp_net_features: bf16 [H][W][5]."""
+    H, W = I0.shape
+    if out is None:
+        out = torch.empty((H, W, 5), dtype=torch.bfloat16, device=I0.device)
+    ls = label_space(space)
+    rc = load().edp_net_features(_dev(I0, torch.uint8, "I0"), _dev(I1, torch.uint8, "I1"),
+                                 _dev(wta_labels, torch.int32, "wta_labels"), _dev(wta_cost, torch.int32, "wta_cost"),
+                                 W, H, ctypes.byref(ls), float(scale), float(cmax), _dev(out, torch.bfloat16, "x"),
+                                 _stream(stream))
+    _check(rc, "net_features")
+    return out
+
+
+def net_centres(out, space: dict, centre=None, stream=None):
+    """edp_net_centres: int32 [..][2] box centres from network outputs [..][2]."""
+    n = out.numel() // 2
+    if centre is None:
+        centre = torch.empty(out.shape[:-1] + (2,), dtype=torch.int32, device=out.device)
+    ls = label_space(space)
+    rc = load().edp_net_centres(_dev(out, torch.float32, "out"), n, ctypes.byref(ls),
+                                _dev(centre, torch.int32, "centre"), _stream(stream))
+    _check(rc, "net_centres")
+    return centre

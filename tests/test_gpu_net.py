@@ -1,0 +1,114 @@
+"""GPU proposal network against its CPU reference (oracle/net.py): forward
+outputs and parameter gradients within 1e-2 relative (bf16 storage on both
+sides, float32 vs float64 accumulation), features, centres, the
+winner-take-all kernel, and a short training run that lowers the loss."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import net as rnet
+from paper_1410_7922_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def flat_params(ps):
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in ps]).astype(np.float32)
+
+
+def unflat(v):
+    out, o = [], 0
+    for ci, co in zip(rnet.CHANNELS[:-1], rnet.CHANNELS[1:]):
+        w = v[o:o + co * ci * 9].reshape(co, ci, 3, 3).astype(np.float64)
+        o += co * ci * 9
+        b = v[o:o + co].astype(np.float64)
+        o += co
+        out.append((w, b))
+    return out
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.fixture
+def setup(edp_lib):
+    rng = np.random.default_rng(5)
+    ps = rnet.init_params(11)
+    ps = [(w, rng.normal(0, 0.05, size=b.shape)) for w, b in ps]
+    P = flat_params(ps)
+    assert P.size == edp_lib.net_param_count()
+    N, H, W = 2, 21, 35
+    x = rnet.bf16(rng.uniform(-1, 1, size=(N, 5, H, W)))
+    tgt = rng.normal(0, 3, size=(N, 2, H, W)).astype(np.float32)
+    return ps, P, x, tgt
+
+
+def test_net_forward_parity(edp_lib, setup):
+    ps, P, x, tgt = setup
+    N, _, H, W = x.shape
+    want = rnet.forward(x, unflat(P))                       # [N][2][H][W]
+    xg = torch.from_numpy(x.transpose(0, 2, 3, 1).astype(np.float32)).to(torch.bfloat16).cuda().contiguous()
+    Pg = torch.from_numpy(P).cuda()
+    ws = edp_lib.net_workspace(N, H, W)
+    out = edp_lib.net_forward(Pg, xg, ws).cpu().numpy().transpose(0, 3, 1, 2)
+    assert rel_err(out, want) < 1e-2
+    assert np.max(np.abs(out - want)) < 1e-2 * np.max(np.abs(want))
+
+
+def test_net_backward_parity(edp_lib, setup):
+    ps, P, x, tgt = setup
+    N, _, H, W = x.shape
+    loss_want, grads = rnet.backward(x, unflat(P), tgt.astype(np.float64))
+    xg = torch.from_numpy(x.transpose(0, 2, 3, 1).astype(np.float32)).to(torch.bfloat16).cuda().contiguous()
+    Pg = torch.from_numpy(P).cuda()
+    tg = torch.from_numpy(np.ascontiguousarray(tgt.transpose(0, 2, 3, 1))).cuda()
+    ws = edp_lib.net_workspace(N, H, W)
+    out = edp_lib.net_forward(Pg, xg, ws)
+    g, loss = edp_lib.net_backward(Pg, out, tg, ws)
+    assert abs(float(loss.item()) - loss_want) < 1e-2 * abs(loss_want)
+    gp = unflat(g.cpu().numpy())
+    for (gw, gb), (ww, wb) in zip(gp, grads):
+        assert rel_err(gw, ww) < 1e-2
+        assert rel_err(gb, wb) < 1e-2
+
+
+def test_wta_and_features(edp_lib):
+    w = synth.workload_motion_640x480(W=48, H=40)
+    space = w["space"]
+    C = oracle.cost_volume(w["I0"], w["I1"], None, space, w["l2"], w["cmax"])
+    I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
+    lab, cost = edp_lib.wta(I0, I1, space, w["l2"], w["cmax"])
+    assert np.array_equal(lab.cpu().numpy(), np.argmin(C, axis=2))
+    assert np.array_equal(cost.cpu().numpy(), np.min(C, axis=2))
+    x = edp_lib.net_features(I0, I1, lab, cost, space, 16.0, float(w["cmax"])).float().cpu().numpy()
+    q = np.argmin(C, axis=2)
+    Q0, Q1 = space["Q"][0], space["Q"][1]
+    feats = rnet.features(w["I0"].astype(np.float64), w["I1"].astype(np.float64),
+                          np.stack([q % Q0 - (Q0 - 1) / 2, q // Q0 - (Q1 - 1) / 2], -1), np.min(C, axis=2), 16.0,
+                          float(w["cmax"]))
+    # same float32 inputs on both sides; allow one bf16 step where a float32/float64 quotient straddles a tie
+    assert np.allclose(x.transpose(2, 0, 1), rnet.bf16(feats), rtol=8e-3, atol=1e-7)
+    out = torch.tensor([[[0.4, -0.6], [31.7, -40.0]]], dtype=torch.float32, device="cuda")
+    c = edp_lib.net_centres(out, space).cpu().numpy()
+    assert c.tolist() == [[[32, 31], [64, 0]]]
+
+
+def test_net_training_lowers_loss(edp_lib):
+    rng = np.random.default_rng(9)
+    N, H, W = 4, 32, 32
+    x = torch.from_numpy(rng.uniform(-1, 1, size=(N, H, W, 5)).astype(np.float32)).to(torch.bfloat16).cuda()
+    # target: a smooth function of the inputs the network can fit
+    xf = x.float()
+    tgt = torch.stack([3 * xf[..., 2] + xf[..., 0], -2 * xf[..., 3]], dim=-1).contiguous()
+    P = torch.from_numpy(flat_params(rnet.init_params(2))).cuda()
+    m, v = torch.zeros_like(P), torch.zeros_like(P)
+    ws = edp_lib.net_workspace(N, H, W)
+    losses = []
+    for step in range(1, 61):
+        out = edp_lib.net_forward(P, x, ws)
+        g, loss = edp_lib.net_backward(P, out, tgt, ws)
+        edp_lib.net_adam(P, g, m, v, 3e-3, step)
+        losses.append(float(loss.item()))
+    assert losses[-1] < 0.5 * losses[0]

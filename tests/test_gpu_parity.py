@@ -273,3 +273,103 @@ def test_range_and_argument_errors(edp_lib):
     with pytest.raises(edp_lib.EdpError) as ei:
         edp_lib.solve(C, sp((8,)), {"lam": 1, "g": 2}, ws=ws)
     assert ei.value.code == edp_lib.ERR_WORKSPACE
+
+
+# --------------------------------------------------------------------------
+# batched persistent solve
+# --------------------------------------------------------------------------
+
+def _batch_items(edp_lib, scale=0.12, n=9, iters=1):
+    items = []
+    for w in synth.workload_batch(n_pairs=n, scale=scale):
+        H, W = w["I0"].shape
+        it = dict(w)
+        it["I0"], it["I1"] = dev(w["I0"]), dev(w["I1"])
+        it["I2"] = dev(w["I2"]) if w["I2"] is not None else None
+        it["labels"] = torch.empty((H, W), dtype=torch.int32, device="cuda")
+        it["energy4"] = torch.empty(4, dtype=torch.int64, device="cuda")
+        it["iters"] = iters
+        it["_w"] = w
+        items.append(it)
+    return items
+
+
+def _oracle_problem(w, iters):
+    C = oracle.cost_volume(w["I0"], w["I1"], w["I2"], w["space"], w["l2"], w["cmax"], w["cost_mode"])
+    lab = oracle.edp(C, w["space"], w["prior"], iters=iters, tier=1)
+    return lab, oracle.energy(C, lab, w["space"], w["prior"])
+
+
+@pytest.mark.parametrize("iters", [1, 2])
+def test_batched_matches_oracle(edp_lib, iters):
+    items = _batch_items(edp_lib, iters=iters)
+    probs = edp_lib.make_problems(items)
+    ws = torch.empty(edp_lib.batch_workspace_size(probs), dtype=torch.uint8, device="cuda")
+    edp_lib.solve_batched(probs, ws)
+    torch.cuda.synchronize()
+    assert edp_lib.get_device_status(ws) == 0
+    for it in items:
+        lab, e = _oracle_problem(it["_w"], iters)
+        assert np.array_equal(host(it["labels"]), lab), it["name"]
+        assert tuple(int(v) for v in host(it["energy4"])) == e, it["name"]
+
+
+def test_batched_waves_and_replay(edp_lib):
+    """A workspace too small for all problems runs them in waves; a second
+    call on the same workspace gives the same result."""
+    items = _batch_items(edp_lib, n=6)
+    probs = edp_lib.make_problems(items)
+    full = edp_lib.batch_workspace_size(probs)
+    big = max(edp_lib.batch_workspace_size(edp_lib.make_problems([it])) for it in items)
+    ws = torch.empty(max(big, full // 3), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        for it in items:
+            it["labels"].fill_(-1)
+        edp_lib.solve_batched(probs, ws)
+        torch.cuda.synchronize()
+        for it in items:
+            lab, e = _oracle_problem(it["_w"], 1)
+            assert np.array_equal(host(it["labels"]), lab), it["name"]
+            assert tuple(int(v) for v in host(it["energy4"])) == e
+
+
+# --------------------------------------------------------------------------
+# windowed EDP (per-pixel label boxes)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("Q,win,mode", [((13, 13), 5, "per_axis"), ((13, 13), 5, "joint"), ((11, 9), 9, "per_axis"),
+                                        ((20,), 7, "joint"), ((9, 9), 9, "joint"), ((17, 17), 15, "per_axis")])
+@pytest.mark.parametrize("iters", [1, 2])
+def test_windowed_matches_oracle(edp_lib, Q, win, mode, iters):
+    rng = np.random.default_rng(sum(Q) * 10 + win + iters)
+    H, W = 15, 21
+    R = len(Q)
+    space = sp(Q, [-(q // 2) for q in Q], [1] * R)
+    I0 = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+    I1 = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+    # centres: a smooth field plus jumps, some outside the valid range (clamped)
+    centre = np.stack([rng.integers(-2, q + 2, size=(H, W)) for q in Q], axis=-1).astype(np.int32)
+    prior = {"lam": int(rng.integers(2, 9)), "g": 3, "l1": 1, "mode": mode}
+    Cw = oracle.cost_window(I0, I1, None, space, 1, 30, centre, win)
+    gCw = edp_lib.cost_window(dev(I0), dev(I1), None, space, 1, 30, dev(centre), win)
+    assert np.array_equal(host(gCw), Cw)
+    want = oracle.edp_windowed(Cw, centre, space, prior, win, iters=iters)
+    got = edp_lib.solve_windowed(gCw, dev(centre), win, space, prior, iters=iters)
+    assert np.array_equal(host(got), want)
+
+
+def test_windowed_full_box_equals_full_edp(edp_lib):
+    rng = np.random.default_rng(77)
+    Q = (9, 9)
+    space = sp(Q, (-4, -4), (1, 1))
+    H, W = 23, 29
+    I0 = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+    I1 = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+    prior = {"lam": 6, "g": 3, "l1": 1, "mode": "per_axis"}
+    centre = np.full((H, W, 2), 4, np.int32)
+    C = edp_lib.cost_volume(dev(I0), dev(I1), None, space, 1, 25)
+    full = host(edp_lib.solve(C, space, prior, iters=2))
+    Cw = edp_lib.cost_window(dev(I0), dev(I1), None, space, 1, 25, dev(centre), 9)
+    assert np.array_equal(host(Cw), host(C))
+    win = host(edp_lib.solve_windowed(Cw, dev(centre), 9, space, prior, iters=2))
+    assert np.array_equal(win, full)
