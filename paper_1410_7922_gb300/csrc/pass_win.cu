@@ -226,6 +226,23 @@ __global__ void __launch_bounds__(kMaxThreads) edp_pass_win_kernel(WinArgs A) {
                 const bool has_a = (s + 1 < W);
                 if (has_a) box_lo(A, rowp + xn, la0, la1);
                 if (has_next) box_lo(A, rowpn + x, lb0, lb1);
+                // Old messages no pass has written yet come from sums that are
+                // still zero: M(0) between the two boxes, lambda times the
+                // (truncated) distance from each label to the source box.
+                const int xc = incx ? x + 1 : x - 1;
+                const int yd = incy ? y + 1 : y - 1;
+                const bool c_m0 = !A.read_c && xc >= 0 && xc < W;
+                const bool d_m0 = !A.read_d && yd >= 0 && yd < H;
+                int lc0 = 0, lc1 = 0, ld0 = 0, ld1 = 0;
+                if (c_m0) box_lo(A, rowp + xc, lc0, lc1);
+                if (d_m0) box_lo(A, (size_t)yd * W + x, ld0, ld1);
+                auto m0 = [&](int q, int s0, int s1) {
+                    const int a0 = lo0 + q % n, a1 = lo1 + q / n;
+                    const int d0 = max(0, max(s0 - a0, a0 - (s0 + n - 1)));
+                    const int d1 = A.R == 2 ? max(0, max(s1 - a1, a1 - (s1 + n - 1))) : 0;
+                    if (per_axis) return min(A.lam * d0, A.capv) + min(A.lam * d1, A.capv);
+                    return min(A.lam * (d0 + d1), A.capv);
+                };
                 // ---- sums (Eq. DP_2D_base) in this pixel's box ----
                 int mina = kBig, minb = kBig;
                 int so_v = kBig, so_q = 0x7fffffff;
@@ -233,7 +250,9 @@ __global__ void __launch_bounds__(kMaxThreads) edp_pass_win_kernel(WinArgs A) {
                 for (int i = 0; i < EM; ++i) {
                     const int q = q0 + i;
                     if (i < E && q < Q) {
-                        const int Cv = src[q], mc = src[Qp + q], md = src[2 * Qp + q];
+                        const int Cv = src[q];
+                        const int mc = c_m0 ? m0(q, lc0, lc1) : src[Qp + q];
+                        const int md = d_m0 ? m0(q, ld0, ld1) : src[2 * Qp + q];
                         const int ha = floor_half(Cv + ma[i] + mb[i] + md - mc);
                         const int hb = floor_half(Cv + ma[i] + mb[i] + mc - md);
                         Hs[q] = ha;

@@ -244,11 +244,13 @@ def _stereo_partner(I0: np.ndarray, seed: int, dmax: int) -> np.ndarray:
     return _to_u8(rng, _sample_rows(I0.astype(np.float64), np.arange(W)[None, :] + d))
 
 
-def workload_motion_640x480(pair: int = 0, W: int = 640, H: int = 480) -> dict:
-    """640x480 motion with the full 65x65 label space ([-32, 32]^2)."""
-    I0, I1, f = motion_layers(seed_for(5, pair), W, H, 32)
-    return {"name": f"motion_{W}x{H}_Q65x65", "I0": I0, "I1": I1, "I2": None, "gt": f,
-            "space": space_motion(65), "prior": {"lam": 15, "g": 3, "l1": 1, "mode": "per_axis"},
+def workload_motion_640x480(pair: int = 0, W: int = 640, H: int = 480, vmax: int = 32) -> dict:
+    """640x480 motion with the full 65x65 label space ([-32, 32]^2); smaller
+    images / label spaces for tests through W, H, vmax."""
+    I0, I1, f = motion_layers(seed_for(5, pair), W, H, vmax)
+    Q = 2 * vmax + 1
+    return {"name": f"motion_{W}x{H}_Q{Q}x{Q}", "I0": I0, "I1": I1, "I2": None, "gt": f,
+            "space": space_motion(Q), "prior": {"lam": 15, "g": 3, "l1": 1, "mode": "per_axis"},
             "l2": 1, "cmax": 20, "cost_mode": "pair", "iters": 1}
 
 
