@@ -283,6 +283,27 @@ int edp_solve_batched(const edp_problem *probs, int n, void *ws, size_t ws_bytes
  * edp_solve_images / edp_scanline_dp.  Synchronises `stream`. */
 int edp_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stream_t stream);
 
+
+/* edp_solve without a workspace argument (the paper has no counterpart).
+ * For callers that cannot allocate device memory at all -- their device
+ * memory is entirely reserved up front by another allocator (a framework's
+ * fixed pool, an embedded or real-time loop with a fixed budget), or they
+ * must not call cudaMalloc because it may synchronise the device.  The
+ * caller still passes C and labels (as for edp_solve); the scratch is a
+ * static array of EDP_NOALLOC_SCRATCH_BYTES in the library's device memory,
+ * which every GPU that loads the library holds until the process exits.
+ * Problems whose edp_workspace_size(EDP_OP_SOLVE, ...) exceeds that size are
+ * rejected with EDP_ERR_WORKSPACE before anything is enqueued.  The first
+ * call on a device looks up the array's device address (once per device).
+ * Every call shares the one array and it keeps the previous call's contents:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and must be ordered by the caller.  The device status word is at the
+ * start of the array; this entry point allocates nothing, so there is no
+ * workspace pointer to pass to edp_get_device_status. */
+#define EDP_NOALLOC_SCRATCH_BYTES (64u << 20)
+int edp_solve_noalloc(const int32_t *C, int W, int H, const edp_label_space *space,
+                      const edp_params *params, int32_t *labels, edp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
         "edp_net_adam": ([P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P], I),
         "edp_net_features": ([P, P, P, P, I, I, LS, ctypes.c_float, ctypes.c_float, P, P], I),
         "edp_net_centres": ([P, I, LS, P, P], I),
+        "edp_solve_noalloc": ([P, I, I, LS, PR, P, P], I),
         "edp_solve_batched": ([ctypes.POINTER(Problem), I, P, SZ, P], I),
     }
     for name, (args, res) in sig.items():
@@ -104,7 +105,7 @@ def exported_symbols() -> list[str]:
             "edp_solve_images_host", "edp_get_device_status", "edp_batch_workspace_size",
             "edp_solve_batched", "edp_workspace_size_windowed", "edp_cost_window", "edp_solve_windowed",
             "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_forward", "edp_net_backward",
-            "edp_net_adam", "edp_net_features", "edp_net_centres"]
+            "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc"]
 
 
 def status_string(code: int) -> str:
