@@ -40,6 +40,9 @@ def parse_args():
     ap.add_argument("--impl", default="edp", choices=["edp", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--extra", default="", help="comma list of longer side measurements: batched,proposal")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="image scale of the batched workload")
+    ap.add_argument("--proposal-pairs", type=int, default=500, help="training pairs of the proposal network")
     return ap.parse_args()
 
 
@@ -101,7 +104,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("edp_pass.cu", "common.cuh"):
+    for f in ("pass_r1.cuh", "edp_pass_r1.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1410_7922_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -305,6 +308,101 @@ def time_solve_rows(edp, synth, torch):
     return rows
 
 
+def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, budget_gb: float = 120.0):
+    """64 heterogeneous pairs: per-pair edp_solve_images launches against one
+    edp_solve_batched call (persistent kernel) and its CUDA-graph replay."""
+    from paper_1410_7922_gb300 import autotune
+    ws_list = synth.workload_batch(n_pairs=n_pairs, scale=scale)
+    items = []
+    updates = 0
+    for w in ws_list:
+        H, W = w["I0"].shape
+        it = {"I0": torch.from_numpy(w["I0"]).cuda(), "I1": torch.from_numpy(w["I1"]).cuda(),
+              "I2": torch.from_numpy(w["I2"]).cuda() if w["I2"] is not None else None,
+              "space": w["space"], "prior": w["prior"], "l2": w["l2"], "cmax": w["cmax"],
+              "cost_mode": w["cost_mode"], "iters": 1,
+              "labels": torch.empty((H, W), dtype=torch.int32, device="cuda"),
+              "energy4": torch.empty(4, dtype=torch.int64, device="cuda")}
+        items.append(it)
+        updates += W * H * edp.n_labels(w["space"]) * 9
+    probs = edp.make_problems(items)
+    full = edp.batch_workspace_size(probs)
+    biggest = max(edp.batch_workspace_size(edp.make_problems([it])) for it in items)
+    wsb = torch.empty(int(max(biggest, min(full, budget_gb * 1e9))), dtype=torch.uint8, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            s, e = ev(), ev()
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            best = s.elapsed_time(e) if best is None else min(best, s.elapsed_time(e))
+        return best
+
+    # per-pair: one edp_solve_images per problem, one workspace sized for the largest
+    ws1 = torch.empty(max(edp.workspace_size(edp.OP_SOLVE_IMAGES, it["I0"].shape[1], it["I0"].shape[0],
+                                             it["space"], it["prior"]) for it in items), dtype=torch.uint8,
+                      device="cuda")
+    per_labels = []
+
+    def per_pair():
+        for it in items:
+            edp.solve_images(it["I0"], it["I1"], it["I2"], it["space"], it["prior"], it["l2"], it["cmax"],
+                             it["cost_mode"], 1, ws=ws1, labels=it["labels"], energy4=it["energy4"])
+
+    ms_per = timed(per_pair, reps=1)
+    per_labels = [it["labels"].clone() for it in items]
+    tuned = autotune.tune(lambda: edp.solve_batched(probs, wsb), rows=(0, 4, 8), lane_labels=(0, 5), reps=1)
+    ms_batched = timed(lambda: edp.solve_batched(probs, wsb))
+    same = all(torch.equal(a, it["labels"]) for a, it in zip(per_labels, items))
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        edp.solve_batched(probs, wsb, stream=st)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            edp.solve_batched(probs, wsb, stream=st)
+    torch.cuda.current_stream().wait_stream(st)
+    ms_graph = timed(lambda: g.replay())
+    same_graph = all(torch.equal(a, it["labels"]) for a, it in zip(per_labels, items))
+    edp.set_tuning(0, 0, False)
+    return {"pairs": n_pairs, "scale": scale, "workspace_gb": wsb.numel() / 1e9,
+            "all_resident_gb": full / 1e9, "updates_per_step": updates,
+            "ms_per_pair_launches": ms_per, "ms_batched": ms_batched, "ms_batched_graph": ms_graph,
+            "speedup_batched": ms_per / ms_batched, "speedup_graph": ms_per / ms_graph,
+            "updates_per_s_batched": updates / (ms_graph * 1e-3), "labels_identical": bool(same and same_graph),
+            "autotune": {"rows": tuned[0], "labels_per_lane": tuned[1], "table": tuned[3]}}
+
+
+def measure_proposal(edp, torch, train_pairs: int = 500, train_W: int = 160, train_H: int = 120, epochs: int = 20,
+                     eval_pairs=(1000, 1001, 1002, 1003), W: int = 640, H: int = 480, win: int = 9):
+    """Learned proposal + 9x9 windowed EDP against full-label EDP (65x65
+    labels) on held-out 640x480 pairs; the network is trained here, by the
+    project's kernels, on full-label EDP labelings of smaller pairs."""
+    from paper_1410_7922_gb300 import proposal
+    t0 = time.perf_counter()
+    x, t = proposal.build_training_set(train_pairs, train_W, train_H, first_pair=0)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P, losses = proposal.train(x, t, epochs=epochs, batch=8, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    rows = proposal.evaluate(P, list(eval_pairs), W, H, win=win, reps=2)
+    return {"train_pairs": train_pairs, "train_size": [train_W, train_H], "epochs": epochs,
+            "loss_first": losses[0], "loss_last": losses[-1], "s_training_data": t_data, "s_training": t_train,
+            "eval": rows,
+            "mean_gap_net": sum(r["gap_net"] for r in rows) / len(rows),
+            "mean_gap_wta": sum(r["gap_wta"] for r in rows) / len(rows),
+            "mean_speedup_net": sum(r["ms_full"] / r["ms_net"] for r in rows) / len(rows)}
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -387,7 +485,7 @@ def run_gpu(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     traffic = profiled_traffic(WORKLOAD)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": "edp_pass_kernel",
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": "edp_pass_r1_kernel",
                 "bytes_per_launch_avg": nbytes / npass, "launch_ms_avg": sum(pass_ms) / args.steps / npass,
                 "pass_ms": [p / args.steps for p in pass_ms]}
 
@@ -415,6 +513,13 @@ def run_gpu(args, world, rank, local):
     rows = None
     if not args.no_rows and rank == 0:
         rows = time_solve_rows(edp, synth, torch)
+    extra = {}
+    if rank == 0:
+        for name in [e for e in args.extra.split(",") if e]:
+            if name == "batched":
+                extra["batched"] = measure_batched(edp, synth, torch, scale=args.batch_scale)
+            elif name == "proposal":
+                extra["proposal"] = measure_proposal(edp, torch, train_pairs=args.proposal_pairs)
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_oracle_sample(w, j)
@@ -430,6 +535,8 @@ def run_gpu(args, world, rank, local):
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
                 "wall_s_timed_region": wall, "remeasured": remeasured, "rows": rows,
                 "energy_per_pixel": float(energy4[3].item()) / (W * H)}
+        if extra:
+            line["extra"] = extra
         print(json.dumps(line), flush=True)
 
 

@@ -15,23 +15,46 @@ __device__ __forceinline__ int cost_term(const uint8_t *I, const uint8_t *I0, in
     return l2 == 1 ? a : a * a;
 }
 
-// One thread per (pixel, 4 consecutive labels): the label dimension is the
-// fastest, so consecutive threads write consecutive 16-byte chunks.
+// One block-row of threads per pixel tile: blockIdx.x walks pixels, the
+// threads of a block cover that pixel's labels (consecutive threads write
+// consecutive labels, so the stores coalesce).  All index arithmetic is
+// 32-bit; the label coordinates come from a per-label table in shared memory.
 __device__ __forceinline__ void cost_body(const CostArgs &A) {
-    const long long n = (long long)A.W * A.H * A.Q;
-    const long long stride = (long long)gridDim.x * blockDim.x * 4;
-    for (long long e0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; e0 < n; e0 += stride) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const long long e = e0 + u;
-            if (e >= n) break;
-            const long long pix = e / A.Q;
-            const int q = (int)(e - pix * A.Q);
-            const int x = (int)(pix % A.W), y = (int)(pix / A.W);
+    __shared__ int s_o0[1024], s_o1[1024], s_o2[1024];
+    const int npix = A.W * A.H;
+    const int Q = A.Q;
+    // labels are processed in chunks of up to 1024 (one offset table each)
+    for (int qb = 0; qb < Q; qb += 1024) {
+        const int qn = min(1024, Q - qb);
+        __syncthreads();
+        for (int t = threadIdx.x; t < qn; t += blockDim.x) {
+            const int q = qb + t;
             const int q0 = q % A.Q0, q1 = (q / A.Q0) % A.Q1, q2 = q / (A.Q0 * A.Q1);
-            const int o0 = A.vmin[0] + A.step[0] * q0;
-            const int o1 = A.R >= 2 ? A.vmin[1] + A.step[1] * q1 : 0;
-            const int o2 = A.R >= 3 ? A.vmin[2] + A.step[2] * q2 : 0;
+            s_o0[t] = A.vmin[0] + A.step[0] * q0;
+            s_o1[t] = A.R >= 2 ? A.vmin[1] + A.step[1] * q1 : 0;
+            s_o2[t] = A.R >= 3 ? A.vmin[2] + A.step[2] * q2 : 0;
+        }
+        __syncthreads();
+        // element e = pix * qn + t, walked with a fixed stride: (pix, t) are
+        // advanced incrementally, no division in the loop
+        const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        const int sp = (int)(stride / qn), st = (int)(stride % qn);
+        int pix = (int)(e0 / qn), t = (int)(e0 % qn);
+        int y = pix / A.W, x = pix - y * A.W;
+        const int sy = sp / A.W, sx = sp - sy * A.W;
+        for (; pix < npix; pix += sp, t += st, x += sx, y += sy) {
+            if (t >= qn) {
+                t -= qn;
+                ++pix;
+                ++x;
+            }
+            if (x >= A.W) {
+                x -= A.W;
+                ++y;
+            }
+            if (pix >= npix) break;
+            const int o0 = s_o0[t], o1 = s_o1[t], o2 = s_o2[t];
             int c;
             bool oob1, oob2;
             if (A.mode == 0) {  // pair
@@ -48,7 +71,7 @@ __device__ __forceinline__ void cost_body(const CostArgs &A) {
                 c2 = oob2 ? A.cmax : min(c2, A.cmax);
                 c = min(c1, c2);
             }
-            A.C[e] = c;
+            A.C[(size_t)pix * Q + qb + t] = c;
         }
     }
 }
@@ -60,7 +83,7 @@ __global__ void cost_batched_kernel(const __grid_constant__ CostBatch B) { cost_
 
 int launch_cost_batched(const CostBatch &a, long long max_entries, cudaStream_t st) {
     const int threads = 256;
-    long long blocks = (max_entries + 4LL * threads - 1) / (4LL * threads);
+    long long blocks = (max_entries + threads - 1) / threads;
     if (blocks > 152LL * 8) blocks = 152LL * 8;
     if (blocks < 1) blocks = 1;
     cost_batched_kernel<<<dim3((unsigned)blocks, a.n), threads, 0, st>>>(a);
@@ -70,8 +93,8 @@ int launch_cost_batched(const CostBatch &a, long long max_entries, cudaStream_t 
 int launch_cost(const CostArgs &a, cudaStream_t st) {
     const long long n = (long long)a.W * a.H * a.Q;
     const int threads = 256;
-    long long blocks = (n + 4LL * threads - 1) / (4LL * threads);
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    long long blocks = (n + threads - 1) / threads;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
     if (blocks < 1) blocks = 1;
     cost_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
