@@ -216,10 +216,12 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
                        size_t ws_bytes, edp_stream_t stream);
 
 /* Winner-take-all over the full label space, straight from the images (no
- * cost volume): labels[x] = lowest-index argmin_q C(x, q) of Eq. Cost_value,
- * cost[x] = that minimum (cost may be NULL).  R = 1 or 2, EDP_COST_PAIR. */
+ * cost volume): labels[x] = lowest-index argmin_q of Eq. Cost_value summed
+ * over the (2 radius + 1)^2 pixels around x (edge pixels repeated; radius 0
+ * is the plain cost, radius <= 15), cost[x] = that minimum (may be NULL).
+ * R = 1 or 2, EDP_COST_PAIR. */
 int edp_wta(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, const edp_label_space *space,
-            const edp_params *params, int32_t *labels, int32_t *cost, edp_stream_t stream);
+            const edp_params *params, int radius, int32_t *labels, int32_t *cost, edp_stream_t stream);
 
 /* Learned proposal network (not in the paper): six 3x3 convolutions, channels
  * 5 -> 32 -> 32 -> 32 -> 32 -> 32 -> 2, ReLU between layers, predicting the

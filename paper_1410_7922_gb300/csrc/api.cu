@@ -251,7 +251,18 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         a.H = H;
         a.Q = g.Q;
         a.E = E;
-        a.EMt = E <= 1 ? 1 : E <= 2 ? 2 : E <= 4 ? 4 : 8;
+        a.EMt = E;
+        // widest prefetch copy that divides E and Q and keeps 4*vw-byte alignment
+        a.vw = 1;
+        for (int v : {4, 2}) {
+            const uintptr_t al = 4 * v;
+            bool ok = E % v == 0 && g.Q % v == 0 && reinterpret_cast<uintptr_t>(C) % al == 0;
+            for (int k = 0; k < 4; ++k) ok = ok && reinterpret_cast<uintptr_t>(M[k]) % al == 0;
+            if (ok) {
+                a.vw = v;
+                break;
+            }
+        }
         a.lam = p->lambda;
         a.capv = (int)cap_value(p);
         a.kc = p->g <= 1 ? 0 : std::min(31, (p->g - 1 + E - 1) / E);
@@ -915,13 +926,13 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
 }
 
 int edp_wta(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, const edp_label_space *space,
-            const edp_params *params, int32_t *labels, int32_t *cost, edp_stream_t stream) {
+            const edp_params *params, int radius, int32_t *labels, int32_t *cost, edp_stream_t stream) {
     Geometry g;
     int rc = check_space(space, &g);
     if (rc) return rc;
     if ((rc = check_images(I0, I1, nullptr, W, H, pitch, space, params))) return rc;
     if (params->cost_mode != EDP_COST_PAIR || space->R > 2) return EDP_ERR_UNSUPPORTED;
-    if (!labels) return EDP_ERR_INVALID_ARG;
+    if (!labels || radius < 0 || radius > 15) return EDP_ERR_INVALID_ARG;
     CostArgs a;
     memset(&a, 0, sizeof a);
     a.I0 = I0;
@@ -939,7 +950,7 @@ int edp_wta(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, const
     }
     a.l2 = params->l2;
     a.cmax = params->cmax;
-    return wta_launch(a, labels, cost, (cudaStream_t)stream) ? EDP_ERR_CUDA : EDP_OK;
+    return wta_launch(a, radius, labels, cost, (cudaStream_t)stream) ? EDP_ERR_CUDA : EDP_OK;
 }
 
 long long edp_net_param_count(void) { return net_param_count(); }

@@ -65,7 +65,9 @@ __global__ void __launch_bounds__(kMaxThreads) edp_batched_kernel(const __grid_c
             a.write_b = f.write_b;
             a.final_ = f.final_;
             a.tag = slot + 1;
-            ok = r1_band<EM>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+            ok = r1_dispatch(a.E, [&](auto e) {
+                return r1_band<decltype(e)::value>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+            });
         } else {
             PassArgs a = P.g;
             a.pass = pass;

@@ -4,7 +4,6 @@
 
 namespace edp {
 
-template <int EM>
 __global__ void __launch_bounds__(kMaxThreads) edp_pass_r1_kernel(PassR1Args A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
@@ -17,7 +16,8 @@ __global__ void __launch_bounds__(kMaxThreads) edp_pass_r1_kernel(PassR1Args A) 
         __syncthreads();
         const int band = s_band;
         if (band >= A.nbands) break;
-        if (!r1_band<EM>(A, band, smem_i, &s_abort)) return;
+        const bool ok = r1_dispatch(A.E, [&](auto e) { return r1_band<decltype(e)::value>(A, band, smem_i, &s_abort); });
+        if (!ok) return;
     }
 }
 
@@ -27,23 +27,9 @@ size_t pass_r1_smem(int NWR, int E) {
 }
 
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st) {
-    switch (a.EMt) {
-#define EDP_CASE(N)                                                                          \
-    case N: {                                                                                \
-        auto k = edp_pass_r1_kernel<N>;                                                      \
-        if (smem > 48 * 1024)                                                                \
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k<<<a.grid, threads, smem, st>>>(a);                                                 \
-        break;                                                                               \
-    }
-        EDP_CASE(1)
-        EDP_CASE(2)
-        EDP_CASE(4)
-        EDP_CASE(8)
-#undef EDP_CASE
-    default:
-        return -1;
-    }
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(edp_pass_r1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    edp_pass_r1_kernel<<<a.grid, threads, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

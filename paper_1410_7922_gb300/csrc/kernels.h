@@ -63,7 +63,8 @@ struct PassR1Args {
     int2 *ll;               // [nbands][W][Q] {value, tag} hand-off records between blocks
     unsigned *band_counter;
     int *status;
-    int W, H, Q, E, EMt;    // E labels per lane (EMt: template bound)
+    int W, H, Q, E, EMt;    // E labels per lane
+    int vw;                 // ints per prefetch copy (1, 2, 4): divides E and Q, aligned
     int lam, capv, kc;      // kc: lanes of carry in the truncated sweeps
     int pass, read_c, read_d, write_a, write_b, final_;
     int NWR;                // rows (warps) per block
@@ -186,6 +187,6 @@ int net_adam_step(float *p, const float *g, float *m, float *v, long long n, flo
 int net_features_launch(const uint8_t *I0, const uint8_t *I1, const int *wta_q, const int *wta_cost, int W, int H,
                         int Q0, int Q1, float scale, float cmax, void *out, cudaStream_t st);
 int net_centres_launch(const float *out, int n, int Q0, int Q1, int *centre, cudaStream_t st);
-int wta_launch(const CostArgs &a, int *labels, int *cost, cudaStream_t st);
+int wta_launch(const CostArgs &a, int radius, int *labels, int *cost, cudaStream_t st);
 
 }  // namespace edp

@@ -220,25 +220,33 @@ __global__ void net_centres(const float *out, int n, int Q0, int Q1, int *centre
 }
 
 // Winner-take-all over the full label space straight from the images (no
-// cost volume): lowest-index minimum of Eq. Cost_value per pixel, one warp
-// per pixel.
-__global__ void wta_kernel(CostArgs A, int *labels, int *cost) {
+// cost volume): lowest-index minimum of Eq. Cost_value per pixel, summed over
+// a (2 radius + 1)^2 window of pixels around it (radius 0: the plain cost),
+// one warp per pixel.
+__global__ void wta_kernel(CostArgs A, int radius, int *labels, int *cost) {
     const int lane = threadIdx.x & 31;
     const long long npix = (long long)A.W * A.H;
     for (long long pix = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; pix < npix;
          pix += (long long)gridDim.x * blockDim.x / 32) {
         const int x = (int)(pix % A.W), y = (int)(pix / A.W);
-        const int i0 = A.I0[(size_t)y * A.pitch + x];
         int best = 0x7fffffff, bq = 0x7fffffff;
         for (int q = lane; q < A.Q; q += 32) {
             const int q0 = q % A.Q0, q1 = (q / A.Q0) % A.Q1;
             const int o0 = A.vmin[0] + A.step[0] * q0;
             const int o1 = A.R >= 2 ? A.vmin[1] + A.step[1] * q1 : 0;
-            const int xs = x + o0, ys = y + o1;
-            int c = A.cmax;
-            if (xs >= 0 && xs < A.W && ys >= 0 && ys < A.H) {
-                const int d = abs((int)A.I1[(size_t)ys * A.pitch + xs] - i0);
-                c = min(A.l2 == 1 ? d : d * d, A.cmax);
+            int c = 0;
+            for (int dy = -radius; dy <= radius; ++dy) {
+                const int yy = min(max(y + dy, 0), A.H - 1);
+                for (int dx = -radius; dx <= radius; ++dx) {
+                    const int xx = min(max(x + dx, 0), A.W - 1);
+                    const int xs = xx + o0, ys = yy + o1;
+                    int cc = A.cmax;
+                    if (xs >= 0 && xs < A.W && ys >= 0 && ys < A.H) {
+                        const int d = abs((int)A.I1[(size_t)ys * A.pitch + xs] - (int)A.I0[(size_t)yy * A.pitch + xx]);
+                        cc = min(A.l2 == 1 ? d : d * d, A.cmax);
+                    }
+                    c += cc;
+                }
             }
             if (c < best) {
                 best = c;
@@ -387,8 +395,8 @@ int net_centres_launch(const float *out, int n, int Q0, int Q1, int *centre, cud
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-int wta_launch(const CostArgs &a, int *labels, int *cost, cudaStream_t st) {
-    wta_kernel<<<152 * 16, 256, 0, st>>>(a, labels, cost);
+int wta_launch(const CostArgs &a, int radius, int *labels, int *cost, cudaStream_t st) {
+    wta_kernel<<<152 * 16, 256, 0, st>>>(a, radius, labels, cost);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -1,23 +1,28 @@
 // pass_r1.cuh -- one row band of an EDP scan pass for one label axis (Q <= 256).
 //
-// Same arithmetic as edp_pass.cu (Sec. 4.2, Eq. DP_2D_base with the data
+// Same arithmetic as pass_gen.cuh (Sec. 4.2, Eq. DP_2D_base with the data
 // term, messages M(floor(S_k / 2)) stored at the receiving pixel), with a
-// schedule built for latency: one warp owns one image row and keeps the
-// message into its next pixel (m_a) in registers; lane j holds the E labels
-// j*E .. j*E+E-1 of the row's current pixel.
+// schedule built for the latency of the pass's wavefront: one warp owns one
+// image row and keeps the message into its next pixel (m_a) in registers;
+// lane j holds the E labels j*E .. j*E+E-1 of the row's current pixel.
 //
-//  - m_b from the previous row: through a shared-memory mailbox ring inside
-//    the block (per-row produced / consumed counters, bounded spins), and
-//    through a "value + tag" 8-byte record per label in global memory
-//    between blocks: the consumer polls the records themselves until every
-//    tag equals this pass's tag, so no memory fence sits on the path.
-//  - C, m_c, m_d (read-only in the pass) are prefetched kPf columns ahead
-//    with cp.async into a per-warp shared-memory ring.
-//  - M of the truncated linear prior: per-lane forward/backward sweeps
+// Per column the only work that waits for the row above is: two adds, the
+// halving, the min search M and the hand-off of m_b.  Everything else -- the
+// prefetch of C, m_c, m_d (cp.async, kPf columns ahead, vector copies), their
+// loads and partial sums -- is done before the wait.
+//
+//  - m_b from the row above: a shared-memory mailbox ring inside the block
+//    (release / acquire counters, bounded spins), and between blocks a
+//    "value + tag" 8-byte record per label in global memory that the
+//    consumer polls until every tag equals this pass's tag (no fence on the
+//    path).  Global message stores are issued after the hand-off.
+//  - M of the truncated linear prior: per-lane forward / backward sweeps
 //    (Eq. L_dec3, Eq. L_dec5), carries from the lanes within distance < g
-//    (farther labels cost at least the clip value), the minimum by
+//    (farther labels cost at least the clip value), the vector minimum by
 //    redux.sync, then the clip of Eq. derivation1.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -25,61 +30,157 @@ namespace edp {
 
 namespace {
 constexpr int kPf = 7;   // prefetch distance in columns (ring of kPf + 1)
-constexpr int kMb = 4;   // mailbox ring depth between rows of a block
+constexpr int kMb = 8;   // mailbox ring depth between rows of a block
+constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ int redux_min(int v) { return __reduce_min_sync(0xffffffffu, v); }
+__device__ __forceinline__ int redux_min(int v) { return __reduce_min_sync(kFull, v); }
 
-// In-place truncated L1 distance transform of one row vector held as
-// v[0..E) per lane over a full warp; carries from `kc` lanes on each side.
-template <int EM>
-__device__ __forceinline__ void dt_trunc(int (&v)[EM], int E, int lane, int lam, int kc) {
-    int f[EM], b[EM];
-    f[0] = v[0];
-#pragma unroll
-    for (int i = 1; i < EM; ++i)
-        if (i < E) f[i] = min(v[i], f[i - 1] + lam);
-#pragma unroll
-    for (int i = EM - 1; i >= 0; --i)
-        if (i < E) b[i] = (i == E - 1) ? v[i] : min(v[i], b[i + 1] + lam);
-    int F = f[0], B = b[0];
-#pragma unroll
-    for (int i = 0; i < EM; ++i)
-        if (i == E - 1) F = f[i];
-    int cf = kBig, cb = kBig;
-    for (int d = 1; d <= kc; ++d) {
-        const int tf = __shfl_up_sync(0xffffffffu, F, d);
-        const int tb = __shfl_down_sync(0xffffffffu, B, d);
-        const int gap = lam * ((d - 1) * E + 1);
-        if (lane >= d) cf = min(cf, tf + gap);
-        if (lane + d < 32) cb = min(cb, tb + gap);
-    }
-#pragma unroll
-    for (int i = 0; i < EM; ++i)
-        if (i < E) v[i] = min(min(f[i], cf + lam * i), min(b[i], cb + lam * (E - 1 - i)));
+__device__ __forceinline__ int ld_acq_shared(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
 }
-
-__device__ __forceinline__ int ld_volatile_shared(const int *p) {
-    return *reinterpret_cast<const volatile int *>(p);
+__device__ __forceinline__ void st_rel_shared(int *p, int v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
-__device__ __forceinline__ void st_volatile_shared(int *p, int v) { *reinterpret_cast<volatile int *>(p) = v; }
-
-__device__ __forceinline__ int2 ld_ll(const int2 *p) {
+__device__ __forceinline__ int2 ld_rec(const int2 *p) {
     int2 r;
     asm volatile("ld.relaxed.gpu.global.v2.s32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p) : "memory");
     return r;
 }
-__device__ __forceinline__ void st_ll(int2 *p, int v, int tag) {
+__device__ __forceinline__ void st_rec(int2 *p, int v, int tag) {
     asm volatile("st.relaxed.gpu.global.v2.s32 [%0], {%1, %2};" ::"l"(p), "r"(v), "r"(tag) : "memory");
+}
+__device__ __forceinline__ void cp_async_bytes(int *dst, const int *src, int bytes, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? bytes : 0;
+    if (bytes == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+
+// Truncated L1 distance transform of two row vectors a, b (E labels per
+// lane), carries from kc <= 4 lanes on each side (full lane scan otherwise).
+template <int E>
+__device__ __forceinline__ void dt_pair(int (&a)[E], int (&b)[E], int lane, int lam, int kc) {
+    int fa[E], ba[E], fb[E], bb[E];
+    fa[0] = a[0];
+    fb[0] = b[0];
+#pragma unroll
+    for (int i = 1; i < E; ++i) {
+        fa[i] = min(a[i], fa[i - 1] + lam);
+        fb[i] = min(b[i], fb[i - 1] + lam);
+    }
+    ba[E - 1] = a[E - 1];
+    bb[E - 1] = b[E - 1];
+#pragma unroll
+    for (int i = E - 2; i >= 0; --i) {
+        ba[i] = min(a[i], ba[i + 1] + lam);
+        bb[i] = min(b[i], bb[i + 1] + lam);
+    }
+    int cfa = kBig, cba = kBig, cfb = kBig, cbb = kBig;
+    if (kc <= 4) {
+#pragma unroll
+        for (int d = 1; d <= 4; ++d) {
+            if (d > kc) break;
+            const int t0 = __shfl_up_sync(kFull, fa[E - 1], d);
+            const int t1 = __shfl_up_sync(kFull, fb[E - 1], d);
+            const int t2 = __shfl_down_sync(kFull, ba[0], d);
+            const int t3 = __shfl_down_sync(kFull, bb[0], d);
+            const int gap = lam * ((d - 1) * E + 1);
+            if (lane >= d) {
+                cfa = min(cfa, t0 + gap);
+                cfb = min(cfb, t1 + gap);
+            }
+            if (lane + d < 32) {
+                cba = min(cba, t2 + gap);
+                cbb = min(cbb, t3 + gap);
+            }
+        }
+    } else {
+        // min-plus prefix / suffix scans over all lanes
+        int pa = fa[E - 1] - lam * E * lane, pb = fb[E - 1] - lam * E * lane;
+        int sa = ba[0] + lam * E * lane, sb = bb[0] + lam * E * lane;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t0 = __shfl_up_sync(kFull, pa, d), t1 = __shfl_up_sync(kFull, pb, d);
+            const int t2 = __shfl_down_sync(kFull, sa, d), t3 = __shfl_down_sync(kFull, sb, d);
+            if (lane >= d) {
+                pa = min(pa, t0);
+                pb = min(pb, t1);
+            }
+            if (lane + d < 32) {
+                sa = min(sa, t2);
+                sb = min(sb, t3);
+            }
+        }
+        const int xa = __shfl_up_sync(kFull, pa, 1), xb = __shfl_up_sync(kFull, pb, 1);
+        const int ya = __shfl_down_sync(kFull, sa, 1), yb = __shfl_down_sync(kFull, sb, 1);
+        if (lane > 0) {
+            cfa = xa + lam * (E * (lane - 1) + 1);
+            cfb = xb + lam * (E * (lane - 1) + 1);
+        }
+        if (lane < 31) {
+            cba = ya - lam * (lane * E + E - 1);
+            cbb = yb - lam * (lane * E + E - 1);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        a[i] = min(min(fa[i], cfa + lam * i), min(ba[i], cba + lam * (E - 1 - i)));
+        b[i] = min(min(fb[i], cfb + lam * i), min(bb[i], cbb + lam * (E - 1 - i)));
+    }
+}
+
+// vector shared-memory load / store of a lane's E consecutive ints
+template <int E>
+__device__ __forceinline__ void lds_vec(const int *p, int (&v)[E]) {
+    if constexpr (E % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < E; i += 4) {
+            const int4 t = *reinterpret_cast<const int4 *>(p + i);
+            v[i] = t.x;
+            v[i + 1] = t.y;
+            v[i + 2] = t.z;
+            v[i + 3] = t.w;
+        }
+    } else if constexpr (E % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < E; i += 2) {
+            const int2 t = *reinterpret_cast<const int2 *>(p + i);
+            v[i] = t.x;
+            v[i + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = p[i];
+    }
+}
+template <int E>
+__device__ __forceinline__ void sts_vec(int *p, const int (&v)[E]) {
+    if constexpr (E % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < E; i += 4) *reinterpret_cast<int4 *>(p + i) = make_int4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    } else if constexpr (E % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < E; i += 2) *reinterpret_cast<int2 *>(p + i) = make_int2(v[i], v[i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) p[i] = v[i];
+    }
 }
 }  // namespace
 
 // One row band (NWR rows, one warp each) of one scan pass.  Every thread of
 // the block calls it with the same band; returns false when the pass was
 // aborted (a wait timed out).
-template <int EM>
+template <int E>
 __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int *smem_i, volatile int *s_abort) {
-    const int Q = A.Q, E = A.E, W = A.W, H = A.H, NWR = A.NWR;
-    const int Qp = 32 * E;  // padded vector length in shared memory
+    const int Q = A.Q, W = A.W, H = A.H, NWR = A.NWR;
+    constexpr int Qp = 32 * E;  // padded vector length in shared memory
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int *ring = smem_i + (size_t)w * (kPf + 1) * 3 * Qp;  // [kPf+1][3][Qp] per warp
     int *mbox = smem_i + (size_t)NWR * (kPf + 1) * 3 * Qp;  // [NWR][kMb][Qp]
@@ -104,85 +205,96 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
         const int y_next = incy ? y + 1 : y - 1;
         const bool last_in_band = (w == NWR - 1);
         const bool d_ok = A.read_d && (incy ? y + 1 < H : y - 1 >= 0);
-        const size_t row0 = (size_t)y * W * Q;
-        const size_t rown = (size_t)(has_next ? y_next : y) * W * Q;
-        const int2 *ll_in = A.ll + (size_t)(band - 1) * W * Q;   // previous band's last row
-        int2 *ll_out = A.ll + (size_t)band * W * Q;
         const int q0 = lane * E;
+        const bool lane_on = q0 < Q;
+        const int vw = A.vw;          // ints per cp.async (1, 2 or 4)
+        // pixel pointers advance by +/-Q per column
+        const long long dq = incx ? Q : -Q;
+        const size_t row0 = (size_t)y * W * Q, rown = (size_t)(has_next ? y_next : y) * W * Q;
+        const size_t x0 = incx ? 0 : (size_t)(W - 1) * Q;
+        const int *pC = A.C + row0 + x0 + q0;
+        const int *pc = Mc + row0 + x0 + q0;
+        const int *pd = Md + row0 + x0 + q0;
+        int *pa_out = Ma + row0 + x0 + q0;   // message into the column, written one column ahead
+        int *pb_out = Mb + rown + x0 + q0;
+        const int2 *ll_in = A.ll + (size_t)(band - 1) * W * Q + q0;  // previous band's last row
+        int2 *ll_out = A.ll + (size_t)band * W * Q + q0;
+        const int mb_src = (w - 1) * kMb;
 
         auto prefetch = [&](int s) {
-            if (s < W) {
+            if (s < W && lane_on) {
+                const long long off = (long long)s * dq;
                 const int x = incx ? s : W - 1 - s;
                 const bool c_ok = A.read_c && (incx ? x + 1 < W : x - 1 >= 0);
-                const size_t pix = row0 + (size_t)x * Q;
-                int *dst = ring + (s % (kPf + 1)) * 3 * Qp;
+                int *dst = ring + (s % (kPf + 1)) * 3 * Qp + q0;
 #pragma unroll
-                for (int i = 0; i < EM; ++i) {
-                    const int q = q0 + i;
-                    if (i < E && q < Q) {
-                        cp_async4(dst + q, A.C + pix + q, true);
-                        cp_async4(dst + Qp + q, Mc + pix + q, c_ok);
-                        cp_async4(dst + 2 * Qp + q, Md + pix + q, d_ok);
-                    }
+                for (int i = 0; i < E; i += 1) {
+                    // vw divides both E and Q: a vw-chunk is wholly inside or outside the vector
+                    if (i % vw || q0 + i >= Q) continue;
+                    cp_async_bytes(dst + i, pC + off + i, 4 * vw, true);
+                    cp_async_bytes(dst + Qp + i, pc + off + i, 4 * vw, c_ok);
+                    cp_async_bytes(dst + 2 * Qp + i, pd + off + i, 4 * vw, d_ok);
                 }
             }
             cp_async_commit();
         };
         for (int s = 0; s < kPf; ++s) prefetch(s);
 
-        int ma[EM];
+        int ma[E];
 #pragma unroll
-        for (int i = 0; i < EM; ++i) ma[i] = 0;
-        long long spins = 0;
+        for (int i = 0; i < E; ++i) ma[i] = 0;
         for (int s = 0; s < W; ++s) {
-            const int x = incx ? s : W - 1 - s;
             prefetch(s + kPf);
             cp_async_wait_n<kPf>();
-            const int *src = ring + (s % (kPf + 1)) * 3 * Qp;
-            // ---- m_b from the previous row ----
-            int mb[EM];
+            // ---- work that does not wait for the row above ----
+            const int *src = ring + (s % (kPf + 1)) * 3 * Qp + q0;
+            int cv[E], mc[E], md[E], pa[E], pb[E], po[E];
+            lds_vec<E>(src, cv);
+            lds_vec<E>(src + Qp, mc);
+            lds_vec<E>(src + 2 * Qp, md);
 #pragma unroll
-            for (int i = 0; i < EM; ++i) mb[i] = 0;
+            for (int i = 0; i < E; ++i) {
+                pa[i] = cv[i] + ma[i] + md[i] - mc[i];
+                pb[i] = cv[i] + ma[i] + mc[i] - md[i];
+                po[i] = cv[i] + ma[i] + mc[i] + md[i];
+            }
+            // ---- m_b from the row above ----
+            int mb[E];
+#pragma unroll
+            for (int i = 0; i < E; ++i) mb[i] = 0;
             if (r > 0) {
+                long long spins = 0;
                 if (w > 0) {
-                    if (lane == 0) {
-                        spins = 0;
-                        while (ld_volatile_shared(produced + w - 1) < s + 1) {
-                            if (++spins > A.spin_limit || (*s_abort)) {
+                    while (true) {
+                        const bool ok = ld_acq_shared(produced + w - 1) >= s + 1;
+                        if (__all_sync(kFull, ok)) break;
+                        if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0)) {
+                            if (lane == 0) {
                                 atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
                                 *s_abort = 1;
-                                break;
                             }
+                            break;
                         }
                     }
+                    lds_vec<E>(mbox + (mb_src + s % kMb) * Qp + q0, mb);
                     __syncwarp();
-                    __threadfence_block();
-                    const int *mbx = mbox + ((w - 1) * kMb + s % kMb) * Qp;
-#pragma unroll
-                    for (int i = 0; i < EM; ++i)
-                        if (i < E) mb[i] = ld_volatile_shared(mbx + q0 + i);
-                    __syncwarp();
-                    if (lane == 0) st_volatile_shared(consumed + w, s + 1);
+                    if (lane == 0) st_rel_shared(consumed + w, s + 1);
                 } else {
                     const unsigned long long tw = A.trace ? global_ns() : 0;
                     const int2 *p = ll_in + (size_t)s * Q;
-                    bool ok = false;
-                    spins = 0;
                     while (true) {
-                        ok = true;
+                        bool ok = true;
 #pragma unroll
-                        for (int i = 0; i < EM; ++i) {
-                            const int q = q0 + i;
-                            if (i < E && q < Q) {
-                                const int2 t = ld_ll(p + q);
+                        for (int i = 0; i < E; ++i) {
+                            if (q0 + i < Q) {
+                                const int2 t = ld_rec(p + i);
                                 mb[i] = t.x;
                                 ok = ok && (t.y == A.tag);
                             }
                         }
-                        if (__all_sync(0xffffffffu, ok)) break;
-                        const bool bail = ++spins > A.spin_limit || (*s_abort) ||
-                                          *(volatile int *)A.status != 0;
-                        if (__any_sync(0xffffffffu, bail)) {
+                        if (__all_sync(kFull, ok)) break;
+                        if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0 ||
+                                                  *(volatile int *)A.status != 0)) {
                             if (lane == 0) {
                                 atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
                                 *s_abort = 1;
@@ -193,92 +305,86 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                     }
                     if (A.trace) t_wait += global_ns() - tw;
                 }
+                if (__any_sync(kFull, *s_abort != 0)) break;
             }
-            __syncwarp();
-            if (__any_sync(0xffffffffu, (*s_abort) != 0)) break;
-            // ---- sums (Eq. DP_2D_base) and halving ----
-            int ha[EM], hb[EM];
-            int lmin_a = kBig, lmin_b = kBig;
-            int so_v = kBig, so_q = 0x7fffffff;
+            // ---- sums (Eq. DP_2D_base), halving, min search M ----
+            int ha[E], hb[E];
+            int la = kBig, lb = kBig;
 #pragma unroll
-            for (int i = 0; i < EM; ++i) {
-                const int q = q0 + i;
-                if (i < E && q < Q) {
-                    const int Cv = src[q], mc = src[Qp + q], md = src[2 * Qp + q];
-                    const int sa = Cv + ma[i] + mb[i] + md - mc;
-                    const int sb = Cv + ma[i] + mb[i] + mc - md;
-                    ha[i] = floor_half(sa);
-                    hb[i] = floor_half(sb);
-                    lmin_a = min(lmin_a, ha[i]);
-                    lmin_b = min(lmin_b, hb[i]);
-                    if (A.final_) {
-                        const int so = Cv + ma[i] + mb[i] + mc + md;
-                        if (so < so_v) {
-                            so_v = so;
-                            so_q = q;
-                        }
-                    }
-                } else {
-                    ha[i] = kBig;
-                    hb[i] = kBig;
-                }
+            for (int i = 0; i < E; ++i) {
+                const bool on = q0 + i < Q;
+                ha[i] = on ? floor_half(pa[i] + mb[i]) : kBig;
+                hb[i] = on ? floor_half(pb[i] + mb[i]) : kBig;
+                la = min(la, ha[i]);
+                lb = min(lb, hb[i]);
             }
-            // ---- min search M (RMS sweeps + clip) ----
-            const int ga = redux_min(lmin_a), gb = redux_min(lmin_b);
-            dt_trunc<EM>(ha, E, lane, A.lam, A.kc);
-            dt_trunc<EM>(hb, E, lane, A.lam, A.kc);
+            const int ga = redux_min(la), gb = redux_min(lb);
+            dt_pair<E>(ha, hb, lane, A.lam, A.kc);
             const int clipa = ga + A.capv, clipb = gb + A.capv;
 #pragma unroll
-            for (int i = 0; i < EM; ++i) {
-                ma[i] = min(ha[i], clipa);
+            for (int i = 0; i < E; ++i) {
+                ha[i] = min(ha[i], clipa);
                 hb[i] = min(hb[i], clipb);
             }
-            if (A.final_) {
-                const int vbest = redux_min(so_v);
-                const int qbest = redux_min(so_v == vbest ? so_q : 0x7fffffff);
-                if (lane == 0) A.labels[(size_t)y * W + x] = qbest;
-            }
-            // ---- outputs ----
-            if (A.write_a && s + 1 < W) {
-                const int xn = incx ? x + 1 : x - 1;
-                int *dst = Ma + row0 + (size_t)xn * Q;
-#pragma unroll
-                for (int i = 0; i < EM; ++i)
-                    if (i < E && q0 + i < Q) dst[q0 + i] = ma[i];
-            }
+            // ---- hand-off of m_b to the row below, then the global stores ----
             if (has_next) {
-                if (A.write_b) {
-                    int *dst = Mb + rown + (size_t)x * Q;
-#pragma unroll
-                    for (int i = 0; i < EM; ++i)
-                        if (i < E && q0 + i < Q) dst[q0 + i] = hb[i];
-                }
                 if (!last_in_band) {
-                    if (lane == 0 && s >= kMb) {
-                        spins = 0;
-                        while (ld_volatile_shared(consumed + w + 1) < s - kMb + 1) {
-                            if (++spins > A.spin_limit || (*s_abort)) {
-                                atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
-                                *s_abort = 1;
+                    if (s >= kMb) {
+                        long long spins = 0;
+                        while (true) {
+                            const bool ok = ld_acq_shared(consumed + w + 1) >= s - kMb + 1;
+                            if (__all_sync(kFull, ok)) break;
+                            if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0)) {
+                                if (lane == 0) {
+                                    atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
+                                    *s_abort = 1;
+                                }
                                 break;
                             }
                         }
                     }
+                    sts_vec<E>(mbox + (w * kMb + s % kMb) * Qp + q0, hb);
                     __syncwarp();
-                    int *mbx = mbox + (w * kMb + s % kMb) * Qp;
-#pragma unroll
-                    for (int i = 0; i < EM; ++i)
-                        if (i < E) st_volatile_shared(mbx + q0 + i, hb[i]);
-                    __threadfence_block();
-                    __syncwarp();
-                    if (lane == 0) st_volatile_shared(produced + w, s + 1);
+                    if (lane == 0) st_rel_shared(produced + w, s + 1);
                 } else {
                     int2 *p = ll_out + (size_t)s * Q;
 #pragma unroll
-                    for (int i = 0; i < EM; ++i)
-                        if (i < E && q0 + i < Q) st_ll(p + q0 + i, hb[i], A.tag);
+                    for (int i = 0; i < E; ++i)
+                        if (q0 + i < Q) st_rec(p + i, hb[i], A.tag);
+                }
+                if (A.write_b) {
+                    int *p = pb_out + (long long)s * dq;
+#pragma unroll
+                    for (int i = 0; i < E; ++i)
+                        if (q0 + i < Q) p[i] = hb[i];
                 }
             }
+            if (A.write_a && s + 1 < W) {
+                int *p = pa_out + (long long)(s + 1) * dq;
+#pragma unroll
+                for (int i = 0; i < E; ++i)
+                    if (q0 + i < Q) p[i] = ha[i];
+            }
+            if (A.final_) {
+                // marginal S_Omega = C + all four messages, lowest-index argmin
+                int sv = kBig, sq = 0x7fffffff;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int v = po[i] + mb[i];
+                    if (q0 + i < Q && v < sv) {
+                        sv = v;
+                        sq = q0 + i;
+                    }
+                }
+                const int vbest = redux_min(sv);
+                const int qbest = redux_min(sv == vbest ? sq : 0x7fffffff);
+                if (lane == 0) {
+                    const int x = incx ? s : W - 1 - s;
+                    A.labels[(size_t)y * W + x] = qbest;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < E; ++i) ma[i] = ha[i];
         }
         cp_async_wait_0();
     }
@@ -290,6 +396,21 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
     }
     __syncthreads();
     return *s_abort == 0;
+}
+
+// dispatch on the labels per lane
+template <typename F>
+__device__ __forceinline__ bool r1_dispatch(int E, F &&f) {
+    switch (E) {
+    case 1: return f(std::integral_constant<int, 1>());
+    case 2: return f(std::integral_constant<int, 2>());
+    case 3: return f(std::integral_constant<int, 3>());
+    case 4: return f(std::integral_constant<int, 4>());
+    case 5: return f(std::integral_constant<int, 5>());
+    case 6: return f(std::integral_constant<int, 6>());
+    case 7: return f(std::integral_constant<int, 7>());
+    default: return f(std::integral_constant<int, 8>());
+    }
 }
 
 }  // namespace edp

@@ -79,7 +79,7 @@ def load() -> ctypes.CDLL:
         "edp_workspace_size_windowed": ([I, I, LS, PR, I], SZ),
         "edp_cost_window": ([P, P, P, I, I, I, LS, PR, P, I, P, P], I),
         "edp_solve_windowed": ([P, P, I, I, I, LS, PR, P, P, SZ, P], I),
-        "edp_wta": ([P, P, I, I, I, LS, PR, P, P, P], I),
+        "edp_wta": ([P, P, I, I, I, LS, PR, I, P, P, P], I),
         "edp_net_param_count": ([], ctypes.c_longlong),
         "edp_net_workspace_size": ([I, I, I], SZ),
         "edp_net_forward": ([P, P, I, I, I, P, P, SZ, P], I),
@@ -405,15 +405,16 @@ def solve_windowed(Cw, centre, win: int, space: dict, prior: dict, iters: int = 
     return labels
 
 
-def wta(I0, I1, space: dict, l2: int, cmax: int, stream=None):
-    """edp_wta: (labels int32 [H][W], cost int32 [H][W]) over the full label space."""
+def wta(I0, I1, space: dict, l2: int, cmax: int, radius: int = 0, stream=None):
+    """edp_wta: (labels int32 [H][W], cost int32 [H][W]) over the full label
+    space, costs summed over a (2 radius + 1)^2 pixel window."""
     H, W = I0.shape
     lab = torch.empty((H, W), dtype=torch.int32, device=I0.device)
     cost = torch.empty((H, W), dtype=torch.int32, device=I0.device)
     ls = label_space(space)
     pr = params({"lam": 0, "g": 1}, l2=l2, cmax=cmax)
     rc = load().edp_wta(_dev(I0, torch.uint8, "I0"), _dev(I1, torch.uint8, "I1"), W, H, I0.stride(0),
-                        ctypes.byref(ls), ctypes.byref(pr), _dev(lab, torch.int32, "labels"),
+                        ctypes.byref(ls), ctypes.byref(pr), int(radius), _dev(lab, torch.int32, "labels"),
                         _dev(cost, torch.int32, "cost"), _stream(stream))
     _check(rc, "wta")
     return lab, cost

@@ -24,6 +24,7 @@ import torch
 from . import edp, synth
 
 FLOW_SCALE = 16.0
+WTA_RADIUS = 3  # winner-take-all feature on costs summed over 7x7 pixels
 
 
 def pair(pair_id: int, W: int, H: int, vmax: int = 32) -> dict:
@@ -34,9 +35,10 @@ def to_device(w: dict) -> tuple[torch.Tensor, torch.Tensor]:
     return torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
 
 
-def features(I0, I1, w: dict) -> torch.Tensor:
-    lab, cost = edp.wta(I0, I1, w["space"], w["l2"], w["cmax"])
-    return edp.net_features(I0, I1, lab, cost, w["space"], FLOW_SCALE, float(w["cmax"]))
+def features(I0, I1, w: dict, radius: int = WTA_RADIUS) -> torch.Tensor:
+    lab, cost = edp.wta(I0, I1, w["space"], w["l2"], w["cmax"], radius=radius)
+    area = (2 * radius + 1) ** 2
+    return edp.net_features(I0, I1, lab, cost, w["space"], FLOW_SCALE, float(w["cmax"] * area))
 
 
 def targets(labels: torch.Tensor, space: dict) -> torch.Tensor:
@@ -123,9 +125,10 @@ def propose(P: torch.Tensor, I0, I1, w: dict) -> torch.Tensor:
     return edp.net_centres(out[0].contiguous(), w["space"])
 
 
-def wta_centres(I0, I1, w: dict) -> torch.Tensor:
-    """Centres straight from winner-take-all (the proposal without a network)."""
-    lab, _ = edp.wta(I0, I1, w["space"], w["l2"], w["cmax"])
+def wta_centres(I0, I1, w: dict, radius: int = WTA_RADIUS) -> torch.Tensor:
+    """Centres straight from (window-aggregated) winner-take-all: the
+    proposal without a network."""
+    lab, _ = edp.wta(I0, I1, w["space"], w["l2"], w["cmax"], radius=radius)
     Q0 = w["space"]["Q"][0]
     return torch.stack([lab % Q0, torch.div(lab, Q0, rounding_mode="floor")], dim=-1).int().contiguous()
 
@@ -133,6 +136,21 @@ def wta_centres(I0, I1, w: dict) -> torch.Tensor:
 def windowed_edp(I0, I1, w: dict, centre: torch.Tensor, win: int = 9, iters: int = 1, ws=None):
     Cw = edp.cost_window(I0, I1, None, w["space"], w["l2"], w["cmax"], centre, win)
     return edp.solve_windowed(Cw, centre, win, w["space"], w["prior"], iters=iters, ws=ws)
+
+
+def label_centres(labels: torch.Tensor, space: dict) -> torch.Tensor:
+    """Label coordinates of a labeling as box centres int32 [H][W][2]."""
+    Q0 = space["Q"][0]
+    return torch.stack([labels % Q0, torch.div(labels, Q0, rounding_mode="floor")], dim=-1).int().contiguous()
+
+
+def refine(I0, I1, w: dict, centre: torch.Tensor, rounds: int, win: int = 9, iters: int = 1, ws=None):
+    """Windowed EDP, then `rounds - 1` more windowed solves re-centred on the
+    previous result."""
+    lab = windowed_edp(I0, I1, w, centre, win, iters, ws)
+    for _ in range(rounds - 1):
+        lab = windowed_edp(I0, I1, w, label_centres(lab, w["space"]), win, iters, ws)
+    return lab
 
 
 def evaluate(P: torch.Tensor, pairs: list[int], W: int, H: int, win: int = 9, iters: int = 1, reps: int = 3,
