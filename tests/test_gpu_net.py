@@ -82,6 +82,14 @@ def test_wta_and_features(edp_lib):
     lab, cost = edp_lib.wta(I0, I1, space, w["l2"], w["cmax"])
     assert np.array_equal(lab.cpu().numpy(), np.argmin(C, axis=2))
     assert np.array_equal(cost.cpu().numpy(), np.min(C, axis=2))
+    # window-aggregated: costs summed over a 5x5 pixel window, edge pixels repeated
+    r = 2
+    Cp = np.pad(C.astype(np.int64), ((r, r), (r, r), (0, 0)), mode="edge")
+    Hh, Ww = C.shape[:2]
+    agg = sum(Cp[dy:dy + Hh, dx:dx + Ww] for dy in range(2 * r + 1) for dx in range(2 * r + 1))
+    lab2, cost2 = edp_lib.wta(I0, I1, space, w["l2"], w["cmax"], radius=r)
+    assert np.array_equal(lab2.cpu().numpy(), np.argmin(agg, axis=2))
+    assert np.array_equal(cost2.cpu().numpy(), np.min(agg, axis=2))
     x = edp_lib.net_features(I0, I1, lab, cost, space, 16.0, float(w["cmax"])).float().cpu().numpy()
     q = np.argmin(C, axis=2)
     Q0, Q1 = space["Q"][0], space["Q"][1]
