@@ -357,7 +357,7 @@ def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, bu
 
     ms_per = timed(per_pair, reps=1)
     per_labels = [it["labels"].clone() for it in items]
-    tuned = autotune.tune(lambda: edp.solve_batched(probs, wsb), rows=(0, 4, 8), lane_labels=(0, 5), reps=1)
+    tuned = autotune.tune(lambda: edp.solve_batched(probs, wsb), rows=(0,), warps=(0, 1, 2, 4), reps=1)
     ms_batched = timed(lambda: edp.solve_batched(probs, wsb))
     same = all(torch.equal(a, it["labels"]) for a, it in zip(per_labels, items))
     g = torch.cuda.CUDAGraph()
@@ -377,7 +377,7 @@ def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, bu
             "ms_per_pair_launches": ms_per, "ms_batched": ms_batched, "ms_batched_graph": ms_graph,
             "speedup_batched": ms_per / ms_batched, "speedup_graph": ms_per / ms_graph,
             "updates_per_s_batched": updates / (ms_graph * 1e-3), "labels_identical": bool(same and same_graph),
-            "autotune": {"rows": tuned[0], "labels_per_lane": tuned[1], "table": tuned[3]}}
+            "autotune": {"rows": tuned[0], "warps_per_row": tuned[1], "table": tuned[3]}}
 
 
 def measure_proposal(edp, torch, train_pairs: int = 500, train_W: int = 160, train_H: int = 120, epochs: int = 20,

@@ -112,13 +112,18 @@ const char *edp_status_string(int status);
 size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
                           const edp_params *params);
 
-/* Process-wide launch shape of the DP kernels: rows per block and target
- * labels per lane on one label line (0 = automatic, the default), and
- * general_kernel = 1 to run one-axis label spaces through the multi-axis
- * scan-pass kernel instead of the warp-per-row one.  Used by the autotuner
- * and the tests; results never depend on it.  Not thread-safe with
- * concurrent solves. */
-int edp_set_tuning(int rows_per_block, int labels_per_lane, int general_kernel);
+/* Process-wide launch shape of the DP kernels (0 = automatic, the default):
+ *   rows_per_block   rows of the image per block (scanline DP, both
+ *                    scan-pass kernels);
+ *   labels_per_lane  target labels per lane on one label line (scanline DP);
+ *   warps_per_row    warps that share one image row in the multi-axis
+ *                    scan-pass kernel (1..12);
+ *   general_kernel   1: one-axis label spaces also take the multi-axis
+ *                    scan-pass kernel instead of the warp-per-row one.
+ * Used by the autotuner and the tests; results never depend on it.  A shape
+ * the kernels cannot run makes the next solve return EDP_ERR_UNSUPPORTED.
+ * Not thread-safe with concurrent solves. */
+int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, int general_kernel);
 
 /* Per-pass timing hook: while set, edp_solve (and edp_solve_images) record
  * events[2*i] / events[2*i + 1] (cudaEvent_t handles created by the caller)

@@ -19,7 +19,8 @@ constexpr int kMaxSmem = 227 * 1024;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 int g_tune_rb = 0;       // rows per block override (0 = automatic)
-int g_tune_e = 0;        // labels per lane target override (0 = automatic)
+int g_tune_e = 0;        // labels per lane target override, scanline DP (0 = automatic)
+int g_tune_t = 0;        // warps per row override, multi-axis scan pass (0 = automatic)
 int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass kernel
 void *const *g_prof_events = nullptr;  // optional per-pass events (profiling hook)
 int g_prof_n = 0;
@@ -159,24 +160,37 @@ int configure(const Geometry &g, int H, bool scan, int W, int ptr_bytes, bool *p
 int ptr_bytes_for(int Q) { return Q <= 256 ? 1 : (Q <= 65536 ? 2 : 4); }
 
 // Workspace of edp_solve:
-//   header | progress [4*iters][H] | counters [4*iters] | hand-off records | M[4][N*Q]
-// The hand-off records ({value, tag} per label of the last row of each row
-// band, one-axis kernel) are sized for bands of kMinRowsR1 rows.
+//   header | consumed columns [4*iters][H] | band counters [4*iters] |
+//   hand-off records | M[4][N*Qm]
+// Messages are stored with the vector stride Qm = Q rounded up to a multiple
+// of 4 (16-byte aligned pixel vectors).  The hand-off records are sized for
+// both scan-pass kernels: {value, tag} per label of the last row of each row
+// band -- one-axis kernel: every column, bands of kMinRowsR1 rows; multi-axis
+// kernel: a ring of team_ring(W) columns, bands of one row or more.
 constexpr int kMinRowsR1 = 2;
+constexpr int kResidentMin = 128;  // resident blocks assumed when sizing the record ring
+int msg_stride(int Q) { return (Q + 3) / 4 * 4; }
+// columns of the record ring: the first of K resident bands may run
+// (K - 1) * ring columns ahead of the last, which must cover the row
+int team_ring(int W, int resident) { return std::max(8, (W + resident - 2) / std::max(1, resident - 1) + 2); }
 struct SolveLayout {
-    size_t progress, counters, ll, ll_bytes, msg[4], end;
+    size_t cons, counters, ll, ll_bytes, msg[4], end;
+    int Qm;
 };
-SolveLayout solve_layout(int W, int H, int Q, int iters) {
+SolveLayout solve_layout(int W, int H, int Q, int R, int iters) {
     SolveLayout L;
     const size_t npass = 4 * (size_t)iters;
-    L.progress = kHeader;
-    L.counters = align_up(L.progress + npass * H * 4);
+    L.Qm = msg_stride(Q);
+    L.cons = kHeader;
+    L.counters = align_up(L.cons + npass * H * 4);
     L.ll = align_up(L.counters + npass * 4);
-    L.ll_bytes = (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * W * Q * 8;
+    const size_t r1 = (R == 1 && Q <= 256) ? (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * W * Q * 8 : 0;
+    const size_t tm = (size_t)H * team_ring(W, kResidentMin) * L.Qm * 8;
+    L.ll_bytes = std::max(r1, tm);
     size_t off = align_up(L.ll + L.ll_bytes);
     for (int k = 0; k < 4; ++k) {
         L.msg[k] = off;
-        off = align_up(off + (size_t)W * H * Q * 4);
+        off = align_up(off + (size_t)W * H * L.Qm * 4);
     }
     L.end = off;
     return L;
@@ -186,9 +200,9 @@ struct ImagesLayout {
     SolveLayout s;
     size_t C, img[3], labels, energy, end;
 };
-ImagesLayout images_layout(int W, int H, int Q, int iters) {
+ImagesLayout images_layout(int W, int H, int Q, int R, int iters) {
     ImagesLayout L;
-    L.s = solve_layout(W, H, Q, iters);
+    L.s = solve_layout(W, H, Q, R, iters);
     L.C = L.s.end;
     size_t off = align_up(L.C + (size_t)W * H * Q * 4);
     for (int k = 0; k < 3; ++k) {
@@ -213,32 +227,77 @@ int check_range(int W, int H, const Geometry &g, const edp_params *p) {
     return EDP_OK;
 }
 
+// Multi-axis kernel shape: warps per row (team), per-axis lane groups.
+// Cost model of one column step: every round of an axis runs the two
+// in-lane sweeps over E labels; lane groups add the carry exchange.
+struct TeamShape {
+    int T, em;
+    TeamAxis ax[3];
+    long cost;
+};
+bool team_shape(const Geometry &g, int T, int gpar, TeamShape *S) {
+    const int NL = 32 * T;
+    int stride = 1, maxE = 1;
+    S->T = T;
+    S->cost = (g.R > 1 && T > 1 ? 24L * g.R : 0) + 10L * T;  // barriers, per-warp overhead
+    for (int r = 0; r < g.R; ++r) {
+        const int L = g.Qr[r], nlines = g.Q / L;
+        long best = -1;
+        TeamAxis bx{};
+        for (int G = 1; G <= 32; G <<= 1) {
+            const int E = (L + G - 1) / G;
+            if (E > 33) continue;
+            if (G > 1 && (L + G / 2 - 1) / (G / 2) <= 1) break;  // more lanes than labels
+            const int rounds = (int)(((long)nlines * G + NL - 1) / NL);
+            const int kc = (G > 1 && gpar > 1) ? std::min(G - 1, (gpar - 1 + E - 1) / E) : 0;
+            int lg = 0;
+            while ((1 << lg) < G) ++lg;
+            const long c = (long)rounds * (5L * E + (G > 1 ? 4L * E + 10L * kc + 6L * lg : 0) + 12);
+            if (best < 0 || c < best) {
+                best = c;
+                bx = TeamAxis{L, G, E, nlines, stride, kc, rounds};
+            }
+        }
+        if (best < 0) return false;
+        S->ax[r] = bx;
+        S->cost += best;
+        maxE = std::max(maxE, bx.E);
+        stride *= L;
+    }
+    for (int r = g.R; r < 3; ++r) S->ax[r] = TeamAxis{1, 1, 1, g.Q, stride, 0, 0};
+    S->em = maxE <= 9 ? 9 : (maxE <= 17 ? 17 : 33);
+    return true;
+}
+
 // Everything about one EDP problem that does not change from pass to pass:
 // which band body runs it, the launch shape and the argument blocks.
+// max_threads / fixed_threads: block size limit, or the block size of a
+// batched launch (0 = free).
 struct SolvePlan {
     bool r1;          // warp-per-row body (one label axis, Q <= 256)
     int nbands;
     int threads;
     int em;
+    int laps;         // record ring laps per pass (multi-axis kernel)
     size_t smem;
     SolveLayout L;
     PassR1Args o;
-    PassArgs ga;
+    TeamArgs ta;
 };
 
 int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
-               unsigned char *ws, SolvePlan *P) {
+               unsigned char *ws, SolvePlan *P, int fixed_threads = 0) {
     memset(P, 0, sizeof *P);
-    P->L = solve_layout(W, H, g.Q, p->iters);
+    P->L = solve_layout(W, H, g.Q, g.R, p->iters);
     const SolveLayout &L = P->L;
     int *M[4];
     for (int k = 0; k < 4; ++k) M[k] = reinterpret_cast<int *>(ws + L.msg[k]);
     P->r1 = (g.R == 1 && g.Q <= 256 && !g_force_general);
     if (P->r1) {
         const int E = (g.Q + 31) / 32;
-        int NWR = g_tune_rb > 0 ? g_tune_rb : 8;
-        NWR = std::max(kMinRowsR1, std::min(NWR, std::min(16, H)));
-        while (NWR > kMinRowsR1 && pass_r1_smem(NWR, E) > (size_t)kMaxSmem) --NWR;
+        int NWR = fixed_threads ? fixed_threads / 32 : (g_tune_rb > 0 ? g_tune_rb : 8);
+        if (!fixed_threads) NWR = std::max(kMinRowsR1, std::min(NWR, std::min(16, H)));
+        while (!fixed_threads && NWR > kMinRowsR1 && pass_r1_smem(NWR, E) > (size_t)kMaxSmem) --NWR;
         P->smem = pass_r1_smem(NWR, E);
         if (P->smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
         PassR1Args &a = P->o;
@@ -250,6 +309,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         a.W = W;
         a.H = H;
         a.Q = g.Q;
+        a.Qm = L.Qm;
         a.E = E;
         a.EMt = E;
         // widest prefetch copy that divides E and Q and keeps 4*vw-byte alignment
@@ -275,36 +335,77 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         P->em = a.EMt;
         return EDP_OK;
     }
-    DpConfig cfg;
-    int rc = configure(g, H, false, W, 0, nullptr, &cfg);
-    if (rc) return rc;
-    PassArgs &a = P->ga;
+    // multi-axis (team) kernel
+    TeamShape S;
+    bool have = false;
+    const int tmax = fixed_threads ? std::min(12, fixed_threads / 32) : 12;
+    if (g_tune_t > 0) {
+        if (g_tune_t > tmax || !team_shape(g, g_tune_t, p->g, &S)) return EDP_ERR_UNSUPPORTED;
+        if (S.em > 17 && S.T > 8) return EDP_ERR_UNSUPPORTED;
+        have = true;
+    } else {
+        for (int T = 1; T <= tmax; ++T) {
+            if (g.R == 1 && T > 1) break;  // one line: one warp
+            TeamShape c;
+            if (!team_shape(g, T, p->g, &c)) continue;
+            if (c.em > 17 && T > 8) continue;  // built for <= 256 threads (<= 384 otherwise)
+            if (!have || c.cost * 10 < S.cost * 9) {
+                S = c;
+                have = true;
+            }
+        }
+    }
+    if (!have) return EDP_ERR_UNSUPPORTED;
+    const int T = S.T;
+    const int thr_cap = fixed_threads ? fixed_threads : (S.em > 17 ? 256 : 384);
+    int NT = 0, nbuf = 3, kmb = 4;
+    for (int attempt = 0; attempt < 2 && NT < 1; ++attempt) {
+        if (attempt == 1) nbuf = kmb = 2;
+        NT = std::min(thr_cap / (32 * T), 15);
+        while (NT > 0 && pass_team_smem(NT, L.Qm, g.R, nbuf, kmb) > (size_t)kMaxSmem) --NT;
+    }
+    if (NT < 1) return EDP_ERR_UNSUPPORTED;
+    if (!fixed_threads) {
+        int want = g_tune_rb > 0 ? g_tune_rb : 4;
+        while (g_tune_rb <= 0 && want > 1 && (H + want - 1) / want < 100) --want;
+        NT = std::max(1, std::min(NT, want));
+    }
+    NT = std::min(NT, H);
+    TeamArgs &a = P->ta;
     a.C = C;
     for (int k = 0; k < 4; ++k) a.M[k] = M[k];
     a.labels = labels;
+    a.ll = reinterpret_cast<int2 *>(ws + L.ll);
     a.status = reinterpret_cast<int *>(ws);
     a.W = W;
     a.H = H;
     a.Q = g.Q;
+    a.Qm = L.Qm;
     a.R = g.R;
-    for (int r = 0; r < 3; ++r) a.ax[r] = cfg.ax[r];
+    for (int r = 0; r < 3; ++r) a.ax[r] = S.ax[r];
     a.lam = p->lambda;
     a.capv = (int)cap_value(p);
     a.mode = p->prior_mode;
-    a.RB = cfg.RB;
-    a.nbands = (H + cfg.RB - 1) / cfg.RB;
-    a.spin_limit = 2000000;
+    a.T = T;
+    a.NT = NT;
+    a.nbuf = nbuf;
+    a.kmb = kmb;
+    a.ring = team_ring(W, kResidentMin);
+    a.em = S.em;
+    a.nbands = (H + NT - 1) / NT;
+    a.spin_limit = 4000000;
+    P->laps = (W + a.ring - 1) / a.ring;
     P->nbands = a.nbands;
-    P->threads = cfg.threads;
-    P->em = cfg.em;
-    P->smem = cfg.smem;
+    P->threads = fixed_threads ? fixed_threads : 32 * T * NT;
+    P->em = S.em;
+    P->smem = pass_team_smem(NT, L.Qm, g.R, nbuf, kmb);
     return EDP_OK;
 }
 
 // Control words that must start from zero before the first pass: status,
-// progress and band counters, and the used hand-off records.
+// consumed-column and band counters, and the used hand-off records.
 size_t control_bytes(const SolvePlan &P, int W, int Q) {
-    return P.r1 ? P.L.ll + (size_t)P.nbands * W * Q * 8 : P.L.ll;
+    return P.r1 ? P.L.ll + (size_t)P.nbands * W * Q * 8 : P.L.ll + (size_t)P.nbands * P.ta.ring * P.L.Qm * 8;
 }
 
 int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
@@ -313,13 +414,15 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     int rc = plan_solve(C, W, H, g, p, labels, ws, &P);
     if (rc) return rc;
     if ((rc = cuda_status(cudaMemsetAsync(ws, 0, control_bytes(P, W, g.Q), st)))) return rc;
-    int grid_g = 1;
+    int grid_t = 1;
     if (!P.r1) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int occ = edp_pass_occupancy(P.em, P.threads, P.smem);
-        grid_g = std::max(1, std::min(P.nbands, std::max(1, occ) * sms));
+        const int occ = std::max(1, edp_pass_team_occupancy(P.em, P.threads, P.smem));
+        grid_t = std::min(P.nbands, occ * sms);
+        // a smaller resident set than the ring was sized for could stall the back-pressure
+        if (grid_t < P.nbands && team_ring(W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
     }
     for (int it = 0; it < p->iters; ++it) {
         for (int pass = 0; pass < 4; ++pass) {
@@ -344,18 +447,19 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
                 a.trace = trace;
                 if (launch_edp_pass_r1(a, P.threads, P.smem, st)) return EDP_ERR_CUDA;
             } else {
-                PassArgs a = P.ga;
+                TeamArgs a = P.ta;
                 a.pass = pass;
                 a.read_c = f.read_c;
                 a.read_d = f.read_d;
                 a.write_a = f.write_a;
                 a.write_b = f.write_b;
                 a.final_ = f.final_;
-                a.progress = reinterpret_cast<unsigned *>(ws + P.L.progress) + (size_t)slot * H;
+                a.cons = reinterpret_cast<unsigned *>(ws + P.L.cons) + (size_t)slot * H;
+                a.tag0 = 1 + slot * P.laps;
                 a.band_counter = counter;
-                a.grid = grid_g;
+                a.grid = grid_t;
                 a.trace = trace;
-                if (launch_edp_pass(a, P.em, P.threads, P.smem, st)) return EDP_ERR_CUDA;
+                if (launch_edp_pass_team(a, P.threads, P.smem, st)) return EDP_ERR_CUDA;
             }
             if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
                 return EDP_ERR_CUDA;
@@ -452,11 +556,13 @@ const char *edp_status_string(int status) {
     }
 }
 
-int edp_set_tuning(int rows_per_block, int labels_per_lane, int general_kernel) {
+int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, int general_kernel) {
     if (rows_per_block < 0 || labels_per_lane < 0 || labels_per_lane > kEM) return EDP_ERR_INVALID_ARG;
+    if (warps_per_row < 0 || warps_per_row > 12) return EDP_ERR_INVALID_ARG;
     if (general_kernel != 0 && general_kernel != 1) return EDP_ERR_INVALID_ARG;
     g_tune_rb = rows_per_block;
     g_tune_e = labels_per_lane;
+    g_tune_t = warps_per_row;
     g_force_general = general_kernel;
     return EDP_OK;
 }
@@ -483,9 +589,9 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space, co
     case EDP_OP_SCANLINE_DP:
         return align_up(kHeader + (size_t)W * H * g.Q * ptr_bytes_for(g.Q));
     case EDP_OP_SOLVE:
-        return solve_layout(W, H, g.Q, iters).end;
+        return solve_layout(W, H, g.Q, g.R, iters).end;
     case EDP_OP_SOLVE_IMAGES:
-        return images_layout(W, H, g.Q, iters).end;
+        return images_layout(W, H, g.Q, g.R, iters).end;
     default:
         return 0;
     }
@@ -580,7 +686,7 @@ int edp_solve_images(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, in
     if ((rc = check_range(W, H, g, params))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *w = static_cast<unsigned char *>(ws);
-    const ImagesLayout L = images_layout(W, H, g.Q, params->iters);
+    const ImagesLayout L = images_layout(W, H, g.Q, g.R, params->iters);
     int32_t *C = reinterpret_cast<int32_t *>(w + L.C);
     if ((rc = run_cost(I0, I1, I2, W, H, pitch, space, params, g.Q, C, st))) return rc;
     if ((rc = run_solve(C, W, H, g, params, labels, w, st))) return rc;
@@ -598,7 +704,7 @@ int edp_solve_images_host(const uint8_t *I0_host, const uint8_t *I1_host, const 
     if (ws_bytes < edp_workspace_size(EDP_OP_SOLVE_IMAGES, W, H, space, params)) return EDP_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *w = static_cast<unsigned char *>(ws);
-    const ImagesLayout L = images_layout(W, H, g.Q, std::max(1, params->iters));
+    const ImagesLayout L = images_layout(W, H, g.Q, g.R, std::max(1, params->iters));
     const size_t npix = (size_t)W * H;
     const uint8_t *hin[3] = {I0_host, I1_host, I2_host};
     for (int k = 0; k < 3; ++k)
@@ -623,7 +729,7 @@ size_t batch_ctrl_bytes(int iters) { return align_up(kHeader + 256 + (size_t)kMa
 
 size_t problem_bytes(const edp_problem &pr, const Geometry &g) {
     const int iters = std::max(1, pr.params.iters);
-    return align_up(solve_layout(pr.W, pr.H, g.Q, iters).end + (size_t)pr.W * pr.H * g.Q * 4);
+    return align_up(solve_layout(pr.W, pr.H, g.Q, g.R, iters).end + (size_t)pr.W * pr.H * g.Q * 4);
 }
 
 int check_problem(const edp_problem &pr, Geometry *g) {
@@ -658,32 +764,49 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     B.spin_limit = 4000000;
     size_t off = ctrl;
     long long max_entries = 0, max_pixels = 0;
-    int threads = 32, em = 8;
+    // one block shape for the wave: 8 warps (one-axis bands of 8 rows, or
+    // teams of the multi-axis body)
+    const int threads = 256;
+    int em = 9;
     size_t smem = 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static SolvePlan plans[kMaxBatch];
     for (int k = 0; k < n; ++k) {
         const edp_problem &pr = probs[first + k];
         const Geometry &g = geo[first + k];
         unsigned char *pws = ws + off;
-        const SolveLayout L = solve_layout(pr.W, pr.H, g.Q, iters);
+        const SolveLayout L = solve_layout(pr.W, pr.H, g.Q, g.R, iters);
         int32_t *C = reinterpret_cast<int32_t *>(pws + L.end);
-        SolvePlan P;
-        int rc = plan_solve(C, pr.W, pr.H, g, &pr.params, pr.labels, pws, &P);
+        int rc = plan_solve(C, pr.W, pr.H, g, &pr.params, pr.labels, pws, &plans[k], threads);
         if (rc) return rc;
         off += problem_bytes(pr, g);
+        if (!plans[k].r1) em = std::max(em, plans[k].em);
+        smem = std::max(smem, plans[k].smem);
+    }
+    const int occ = std::max(1, edp_batched_occupancy(em, threads, smem));
+    off = ctrl;
+    for (int k = 0; k < n; ++k) {
+        const edp_problem &pr = probs[first + k];
+        const Geometry &g = geo[first + k];
+        unsigned char *pws = ws + off;
+        const SolveLayout L = solve_layout(pr.W, pr.H, g.Q, g.R, iters);
+        int32_t *C = reinterpret_cast<int32_t *>(pws + L.end);
+        const SolvePlan &P = plans[k];
+        off += problem_bytes(pr, g);
+        if (!P.r1 && team_ring(pr.W, occ * sms) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
         BatchProblem &bp = B.p[k];
         bp.r1 = P.r1;
         bp.nbands = P.nbands;
-        bp.H = pr.H;
         bp.iters = iters;
-        bp.progress = reinterpret_cast<unsigned *>(pws + L.progress);
-        bp.g = P.ga;
+        bp.laps = P.laps;
+        bp.cons = reinterpret_cast<unsigned *>(pws + L.cons);
+        bp.t = P.ta;
         bp.o = P.o;
-        bp.g.status = status;
+        bp.t.status = status;
         bp.o.status = status;
         B.prefix[k + 1] = B.prefix[k] + P.nbands;
-        threads = std::max(threads, P.threads);
-        smem = std::max(smem, P.smem);
-        em = std::max(em, P.em);
         zb.ptr[zb.n] = pws;
         zb.bytes[zb.n++] = control_bytes(P, pr.W, g.Q);
         CostArgs &c = cb.c[k];
@@ -730,15 +853,9 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     B.per_slot = B.prefix[n];
     cb.n = n;
     eb.n = n;
-    em = em <= 8 ? 8 : 16;
-    threads = std::min(kMaxThreads, (threads + 31) / 32 * 32);
     if (launch_zero_batched(zb, st)) return EDP_ERR_CUDA;
     if (launch_cost_batched(cb, max_entries, st)) return EDP_ERR_CUDA;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int occ = edp_batched_occupancy(em, threads, smem);
-    const int grid = std::max(1, std::min(B.slots * B.per_slot, std::max(1, occ) * sms));
+    const int grid = std::max(1, std::min(B.slots * B.per_slot, occ * sms));
     if (launch_edp_batched(B, em, threads, smem, grid, st)) return EDP_ERR_CUDA;
     if (launch_energy_batched(eb, max_pixels, st)) return EDP_ERR_CUDA;
     return EDP_OK;

@@ -13,15 +13,15 @@
 // heterogeneity lives in the per-problem descriptors, passed by value as the
 // kernel's parameter block (no host tables, so the launch can be captured in
 // a CUDA graph).
-#include "pass_gen.cuh"
 #include "pass_r1.cuh"
+#include "pass_team.cuh"
 
 namespace edp {
 
 static_assert(sizeof(BatchArgs) <= 32000, "batch descriptors must fit the kernel parameter space");
 
 template <int EM>
-__global__ void __launch_bounds__(kMaxThreads) edp_batched_kernel(const __grid_constant__ BatchArgs B) {
+__global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ volatile int s_abort;
@@ -69,15 +69,16 @@ __global__ void __launch_bounds__(kMaxThreads) edp_batched_kernel(const __grid_c
                 return r1_band<decltype(e)::value>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
             });
         } else {
-            PassArgs a = P.g;
+            TeamArgs a = P.t;
             a.pass = pass;
             a.read_c = f.read_c;
             a.read_d = f.read_d;
             a.write_a = f.write_a;
             a.write_b = f.write_b;
             a.final_ = f.final_;
-            a.progress = P.progress + (size_t)slot * P.H;
-            ok = gen_band<EM>(a, band, smem_raw, &s_abort);
+            a.cons = P.cons + (size_t)slot * P.nbands;
+            a.tag0 = 1 + slot * P.laps;
+            ok = team_band<EM>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
         }
         if (!ok) return;
         // both bodies end with a block barrier: every write of this band is done
@@ -88,37 +89,27 @@ __global__ void __launch_bounds__(kMaxThreads) edp_batched_kernel(const __grid_c
     }
 }
 
+template <int EM>
+static void *batched_kernel() {
+    return reinterpret_cast<void *>(edp_batched_kernel<EM>);
+}
+static void *batched_kernel_for(int em) {
+    return em == 9 ? batched_kernel<9>() : (em == 17 ? batched_kernel<17>() : batched_kernel<33>());
+}
+
 int edp_batched_occupancy(int em, int threads, size_t smem) {
+    void *k = batched_kernel_for(em);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    if (em == 8) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(edp_batched_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edp_batched_kernel<8>, threads, smem);
-    } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(edp_batched_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edp_batched_kernel<16>, threads, smem);
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
     return occ;
 }
 
 int launch_edp_batched(const BatchArgs &a, int em, int threads, size_t smem, int grid, cudaStream_t st) {
-    switch (em) {
-#define EDP_CASE(N)                                                                          \
-    case N: {                                                                                \
-        auto k = edp_batched_kernel<N>;                                                      \
-        if (smem > 48 * 1024)                                                                \
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k<<<grid, threads, smem, st>>>(a);                                                   \
-        break;                                                                               \
-    }
-        EDP_CASE(8)
-        EDP_CASE(16)
-#undef EDP_CASE
-    default:
-        return -1;
-    }
-    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    void *k = batched_kernel_for(em);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void *args[] = {const_cast<BatchArgs *>(&a)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, st) == cudaSuccess ? 0 : -2;
 }
 
 }  // namespace edp

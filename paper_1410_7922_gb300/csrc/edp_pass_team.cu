@@ -1,0 +1,52 @@
+// edp_pass_team.cu -- the single-problem multi-axis scan-pass kernel; the
+// band body is in pass_team.cuh.
+#include "pass_team.cuh"
+
+namespace edp {
+
+template <int EM>
+__global__ void __launch_bounds__(EM > 17 ? 256 : 384) edp_pass_team_kernel(TeamArgs A) {
+    extern __shared__ __align__(16) int smem_i[];
+    __shared__ int s_band;
+    __shared__ volatile int s_abort;
+    if (threadIdx.x == 0) s_abort = (*(volatile int *)A.status != 0);
+    __syncthreads();
+    if (s_abort) return;
+    while (true) {
+        if (threadIdx.x == 0) s_band = atomicAdd(A.band_counter, 1);
+        __syncthreads();
+        const int band = s_band;
+        if (band >= A.nbands) break;
+        if (!team_band<EM>(A, band, smem_i, &s_abort)) return;
+    }
+}
+
+size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb) {
+    return (size_t)NT * team::team_ints(Qm, R, nbuf, kmb) * 4;
+}
+
+template <int EM>
+static void *team_kernel() {
+    return reinterpret_cast<void *>(edp_pass_team_kernel<EM>);
+}
+static void *team_kernel_for(int em) {
+    return em == 9 ? team_kernel<9>() : (em == 17 ? team_kernel<17>() : team_kernel<33>());
+}
+
+int edp_pass_team_occupancy(int em, int threads, size_t smem) {
+    void *k = team_kernel_for(em);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
+    return occ;
+}
+
+int launch_edp_pass_team(const TeamArgs &a, int threads, size_t smem, cudaStream_t st) {
+    void *k = team_kernel_for(a.em);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void *args[] = {const_cast<TeamArgs *>(&a)};
+    if (cudaLaunchKernel(k, dim3(a.grid), dim3(threads), args, smem, st) != cudaSuccess) return -2;
+    return 0;
+}
+
+}  // namespace edp

@@ -29,31 +29,39 @@ __host__ __device__ inline PassFlags pass_flags(int it, int pass, int iters) {
     return f;
 }
 
-// one EDP scan pass
-struct PassArgs {
-    const int *C;         // [H][W][Q]
-    int *M[4];            // messages into each pixel from +x, -x, +y, -y
-    int *labels;          // [H][W], written by the final pass
-    unsigned *progress;   // [H] columns published per pass-order row
+// one EDP scan pass, any label axes, one team of T warps per row (pass_team.cuh)
+struct TeamAxis {
+    int L;        // labels on the axis (line length)
+    int G;        // lanes per line segment group (power of two <= 32)
+    int E;        // labels per lane, ceil(L / G)
+    int nlines;   // Q / L
+    int stride;   // distance of axis neighbours in the linear label index
+    int kc;       // lanes of carry in the truncated sweeps
+    int rounds;   // line groups per lane, ceil(nlines * G / (32 T))
+};
+struct TeamArgs {
+    const int *C;           // [H][W][Q]
+    int *M[4];              // [H][W][Qm] messages into each pixel from +x, -x, +y, -y
+    int *labels;            // [H][W], written by the final pass
+    int2 *ll;               // [nbands][ring][Qm] {value, tag} records between bands
+    unsigned *cons;         // [nbands] columns of each band's records consumed
     unsigned *band_counter;
     int *status;
-    int W, H, Q, R;
-    AxisCfg ax[3];
-    int lam;              // lambda
-    int capv;             // lambda * g^l1 (clip addend)
-    int mode;             // 0 joint, 1 per axis
-    int pass;             // 0..3 = P1..P4
-    int read_c, read_d;   // 0: the old message array is known to be zero
-    int write_a, write_b; // 0: the outputs are never read again
-    int final_;           // marginal + argmin in this pass
-    int RB;               // rows per band
-    int nbands;
-    int grid;
+    int W, H, Q, Qm, R;     // Qm: message stride, Q rounded up to a multiple of 4
+    TeamAxis ax[3];
+    int lam, capv, mode;    // mode 0 joint, 1 per axis truncation
+    int pass, read_c, read_d, write_a, write_b, final_;
+    int T, NT;              // warps per team (one row), teams per block
+    int nbuf, kmb, ring;    // staging buffers, mailbox slots, record ring columns
+    int tag0;               // tag of the first ring lap of this pass
+    int em;                 // labels-per-lane bound of the instantiation
+    int nbands, grid;
     long long spin_limit;
-    unsigned long long *trace;  // optional: per band {start ns, end ns, wait ns, sm id}
+    unsigned long long *trace;  // optional: per band {start ns, end ns, 0, sm id}
 };
-int launch_edp_pass(const PassArgs &a, int em, int threads, size_t smem, cudaStream_t st);
-int edp_pass_occupancy(int em, int threads, size_t smem);
+int launch_edp_pass_team(const TeamArgs &a, int threads, size_t smem, cudaStream_t st);
+int edp_pass_team_occupancy(int em, int threads, size_t smem);
+size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb);
 
 // one EDP scan pass, one label axis, one warp per row (edp_pass_r1.cu)
 struct PassR1Args {
@@ -63,7 +71,7 @@ struct PassR1Args {
     int2 *ll;               // [nbands][W][Q] {value, tag} hand-off records between blocks
     unsigned *band_counter;
     int *status;
-    int W, H, Q, E, EMt;    // E labels per lane
+    int W, H, Q, Qm, E, EMt; // Qm: message stride; E labels per lane
     int vw;                 // ints per prefetch copy (1, 2, 4): divides E and Q, aligned
     int lam, capv, kc;      // kc: lanes of carry in the truncated sweeps
     int pass, read_c, read_d, write_a, write_b, final_;
@@ -97,12 +105,12 @@ size_t pass_win_smem(int NWR, int E);
 // batched solve: up to kMaxBatch problems of one wave, passed by value
 constexpr int kMaxBatch = 48;
 struct BatchProblem {
-    int r1;            // 1: warp-per-row band body, 0: general band body
+    int r1;            // 1: warp-per-row band body, 0: team band body
     int nbands;
-    int H;             // rows (progress arrays are [slot][H])
     int iters;
-    unsigned *progress;  // general body: [4*iters][H]
-    PassArgs g;        // general body fields (pass / flags / progress set per item)
+    int laps;          // record ring laps per pass (team body)
+    unsigned *cons;    // team body: [4*iters][nbands] consumed columns
+    TeamArgs t;        // team body fields (pass / flags / tags set per item)
     PassR1Args o;      // one-axis body fields
 };
 struct BatchArgs {

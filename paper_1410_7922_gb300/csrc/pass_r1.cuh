@@ -208,22 +208,23 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
         const int q0 = lane * E;
         const bool lane_on = q0 < Q;
         const int vw = A.vw;          // ints per cp.async (1, 2 or 4)
-        // pixel pointers advance by +/-Q per column
-        const long long dq = incx ? Q : -Q;
-        const size_t row0 = (size_t)y * W * Q, rown = (size_t)(has_next ? y_next : y) * W * Q;
-        const size_t x0 = incx ? 0 : (size_t)(W - 1) * Q;
-        const int *pC = A.C + row0 + x0 + q0;
-        const int *pc = Mc + row0 + x0 + q0;
-        const int *pd = Md + row0 + x0 + q0;
-        int *pa_out = Ma + row0 + x0 + q0;   // message into the column, written one column ahead
-        int *pb_out = Mb + rown + x0 + q0;
+        // pixel pointers advance by +/-Q (cost) and +/-Qm (messages) per column
+        const int Qm = A.Qm;
+        const long long dq = incx ? Q : -Q, dqm = incx ? Qm : -Qm;
+        const int *pC = A.C + ((size_t)y * W + (incx ? 0 : W - 1)) * Q + q0;
+        const size_t m0 = ((size_t)y * W + (incx ? 0 : W - 1)) * Qm + q0;
+        const size_t mn = ((size_t)(has_next ? y_next : y) * W + (incx ? 0 : W - 1)) * Qm + q0;
+        const int *pc = Mc + m0;
+        const int *pd = Md + m0;
+        int *pa_out = Ma + m0;   // message into the column, written one column ahead
+        int *pb_out = Mb + mn;
         const int2 *ll_in = A.ll + (size_t)(band - 1) * W * Q + q0;  // previous band's last row
         int2 *ll_out = A.ll + (size_t)band * W * Q + q0;
         const int mb_src = (w - 1) * kMb;
 
         auto prefetch = [&](int s) {
             if (s < W && lane_on) {
-                const long long off = (long long)s * dq;
+                const long long off = (long long)s * dq, offm = (long long)s * dqm;
                 const int x = incx ? s : W - 1 - s;
                 const bool c_ok = A.read_c && (incx ? x + 1 < W : x - 1 >= 0);
                 int *dst = ring + (s % (kPf + 1)) * 3 * Qp + q0;
@@ -232,8 +233,8 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                     // vw divides both E and Q: a vw-chunk is wholly inside or outside the vector
                     if (i % vw || q0 + i >= Q) continue;
                     cp_async_bytes(dst + i, pC + off + i, 4 * vw, true);
-                    cp_async_bytes(dst + Qp + i, pc + off + i, 4 * vw, c_ok);
-                    cp_async_bytes(dst + 2 * Qp + i, pd + off + i, 4 * vw, d_ok);
+                    cp_async_bytes(dst + Qp + i, pc + offm + i, 4 * vw, c_ok);
+                    cp_async_bytes(dst + 2 * Qp + i, pd + offm + i, 4 * vw, d_ok);
                 }
             }
             cp_async_commit();
@@ -353,14 +354,14 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                         if (q0 + i < Q) st_rec(p + i, hb[i], A.tag);
                 }
                 if (A.write_b) {
-                    int *p = pb_out + (long long)s * dq;
+                    int *p = pb_out + (long long)s * dqm;
 #pragma unroll
                     for (int i = 0; i < E; ++i)
                         if (q0 + i < Q) p[i] = hb[i];
                 }
             }
             if (A.write_a && s + 1 < W) {
-                int *p = pa_out + (long long)(s + 1) * dq;
+                int *p = pa_out + (long long)(s + 1) * dqm;
 #pragma unroll
                 for (int i = 0; i < E; ++i)
                     if (q0 + i < Q) p[i] = ha[i];

@@ -1,0 +1,545 @@
+// pass_team.cuh -- one row band of an EDP scan pass, any number of label axes.
+//
+// What is stored.  The paper keeps the four directional sums S_k.  Every use
+// of S_k is through the message  m_k(x) = M(floor(S_k(x_k) / 2))  into the
+// neighbour x of x_k (Eq. DP_2D_1, Eq. DP_2D_base), so the kernels store the
+// messages instead: M[k] at pixel x holds m_k(x), computed once by the pixel
+// x_k that produces S_k(x_k).  A pass p updates the sums a (x direction) and
+// b (y direction):
+//   P1: a = +x, b = +y   P2: a = -x, b = +y   P3: a = +x, b = -y   P4: a = -x, b = -y
+// with c = opposite(a), d = opposite(b) read from the previous passes, and
+//   S_a = C + m_a + m_b + m_d - m_c,    S_b = C + m_a + m_b + m_c - m_d
+// (Eq. DP_2D_base with the data term: all k except -k', minus m_{-k'}).  The
+// new messages M(floor(S_a / 2)) and M(floor(S_b / 2)) go to the next pixel
+// of the row and to the same column of the next row.  In the last pass the
+// marginal S_Omega = C + m_a + m_b + m_c + m_d and its lowest-index argmin
+// (Eq. DP_2D_1, Eq. DP_2D_2) are taken on the way.
+//
+// Schedule.  The recursion is in place (Sec. 4.2), so pixel (x, y) of a pass
+// needs (x -/+ 1, y) and (x, y -/+ 1) of the same pass: a wavefront.  One
+// team of T warps owns one image row and walks it column by column; a block
+// holds NT teams (NT consecutive rows, a "band").  Per column a team:
+//   1. prefetches C, m_c, m_d of a later column into shared memory
+//      (cp.async, 16-byte copies, nbuf - 1 columns ahead);
+//   2. gets m_b: from the team above through a shared-memory mailbox
+//      (release / acquire flags), or, for the first row of a band, from a
+//      ring of "value + tag" records in global memory written by the last
+//      row of the previous band (polled until every tag matches; no fence);
+//   3. phase 0: sums, halving and the sweeps of label axis 0 -- lane groups
+//      own line segments of axis 0 in registers (Eq. L_dec3, Eq. L_dec5);
+//   4. phases 1..R-1: the same for axes 1, 2 after a transpose through
+//      shared memory (named barrier of the team);
+//   5. the clip of Eq. derivation1 (joint: vector minimum + lambda f(g);
+//      per-axis: line minimum + lambda f(g) after every axis), then the two
+//      messages go to the next column (shared memory + global M[a]) and to
+//      the next row (mailbox or record ring + global M[b]).
+// Between blocks the producer may run at most `ring` columns ahead of its
+// consumer (a consumed-column counter per band).  Every wait is a bounded
+// spin that sets the launch's status word on timeout.
+#pragma once
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace edp {
+namespace team {
+
+constexpr unsigned kAllLanes = 0xffffffffu;
+constexpr int kMaxT = 12;   // warps per team
+// per-team control words (ints): [0, 16) produced columns per warp, [16]
+// consumed columns, [24, 48) warp minima (a, b), [48, 72) warp argmin keys
+constexpr int kMisc = 96;
+
+__device__ __forceinline__ void sync(int tm, int T) {
+    if (T == 1) {
+        __syncwarp();
+        return;
+    }
+    asm volatile("barrier.sync %0, %1;" ::"r"(tm + 1), "r"(32 * T) : "memory");
+}
+// team barrier that also returns the OR of `pred` over the team
+__device__ __forceinline__ bool sync_or(int tm, int T, bool pred) {
+    if (T == 1) return __any_sync(kAllLanes, pred);
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((int)pred), "r"(tm + 1), "r"(32 * T)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ int ld_acq_cta(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel_cta(int *p, int v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int4 ld_rec2(const int2 *p) {
+    int4 r;
+    asm volatile("ld.relaxed.gpu.global.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p)
+                 : "memory");
+    return r;
+}
+__device__ __forceinline__ void st_record(int2 *p, int v, int tag) {
+    asm volatile("st.relaxed.gpu.global.v2.s32 [%0], {%1, %2};" ::"l"(p), "r"(v), "r"(tag) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cp16(int *dst, const int *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void wait_groups(int keep) {
+    switch (keep) {
+    case 0: cp_async_wait_0(); break;
+    case 1: cp_async_wait_n<1>(); break;
+    case 2: cp_async_wait_n<2>(); break;
+    default: cp_async_wait_n<3>(); break;
+    }
+}
+
+// Truncated-L1 distance transform (Eq. L_dec3, Eq. L_dec5) of two vectors a,
+// b along one label line, in place.  Lane j of a group of G lanes holds the
+// positions j*E .. j*E+E-1; positions past the line hold kBig.  Carries come
+// from the kc nearest lanes of the group on each side: a source farther than
+// g - 1 labels costs at least the clip value lambda f(g) applied afterwards,
+// so the clipped result is exact.  Returns the minima of a and b over the
+// line (of the input).
+template <int EM>
+__device__ __forceinline__ int2 seg_dt2(int (&a)[EM], int (&b)[EM], const int E, const int G, const int j,
+                                        const int lam, const int kc) {
+    int mina = kBig, minb = kBig;
+#pragma unroll
+    for (int i = 0; i < EM; ++i)
+        if (i < E) {
+            mina = min(mina, a[i]);
+            minb = min(minb, b[i]);
+        }
+    int cfa = kBig, cfb = kBig, cba = kBig, cbb = kBig;
+    if (G > 1) {
+        // value of the lane's own labels at its last position (forward) and
+        // at its first position (backward)
+        int Fa = kBig, Fb = kBig, Ba = kBig, Bb = kBig;
+#pragma unroll
+        for (int i = 0; i < EM; ++i)
+            if (i < E) {
+                Fa = min(Fa + lam, a[i]);
+                Fb = min(Fb + lam, b[i]);
+                Ba = min(Ba, a[i] + lam * i);
+                Bb = min(Bb, b[i] + lam * i);
+            }
+        const int kcl = min(kc, G - 1);
+        for (int d = 1; d <= kcl; ++d) {
+            const int t0 = __shfl_up_sync(kAllLanes, Fa, d, G), t1 = __shfl_up_sync(kAllLanes, Fb, d, G);
+            const int t2 = __shfl_down_sync(kAllLanes, Ba, d, G), t3 = __shfl_down_sync(kAllLanes, Bb, d, G);
+            const int gap = lam * ((d - 1) * E + 1);
+            if (j >= d) {
+                cfa = min(cfa, t0 + gap);
+                cfb = min(cfb, t1 + gap);
+            }
+            if (j + d < G) {
+                cba = min(cba, t2 + gap);
+                cbb = min(cbb, t3 + gap);
+            }
+        }
+        for (int d = G >> 1; d >= 1; d >>= 1) {
+            mina = min(mina, __shfl_xor_sync(kAllLanes, mina, d, G));
+            minb = min(minb, __shfl_xor_sync(kAllLanes, minb, d, G));
+        }
+    }
+    int fa[EM], fb[EM];
+    int ra = cfa, rb = cfb;
+#pragma unroll
+    for (int i = 0; i < EM; ++i)
+        if (i < E) {
+            ra = min(a[i], i == 0 ? ra : ra + lam);
+            rb = min(b[i], i == 0 ? rb : rb + lam);
+            fa[i] = ra;
+            fb[i] = rb;
+        }
+    int sa = cba, sb = cbb;
+    bool started = false;
+#pragma unroll
+    for (int i = EM - 1; i >= 0; --i)
+        if (i < E) {
+            sa = min(a[i], started ? sa + lam : sa);
+            sb = min(b[i], started ? sb + lam : sb);
+            started = true;
+            a[i] = min(fa[i], sa);
+            b[i] = min(fb[i], sb);
+        }
+    return make_int2(mina, minb);
+}
+
+// ints of shared memory of one team
+__host__ __device__ inline size_t team_ints(int Qm, int R, int nbuf, int kmb) {
+    const size_t Qs = (size_t)Qm + 4;
+    return (size_t)nbuf * 3 * Qs + (size_t)Qm * (1 + (R >= 2 ? 2 : 0) + kmb) + kMisc;
+}
+
+}  // namespace team
+
+// One row band of one scan pass.  Every thread of the block calls it with the
+// same band; returns false when the pass was aborted (a wait timed out).
+template <int EM>
+__device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int *smem, volatile int *s_abort) {
+    using namespace team;
+    const int Q = A.Q, Qm = A.Qm, W = A.W, H = A.H, T = A.T, NT = A.NT, R = A.R;
+    const int nbuf = A.nbuf, kmb = A.kmb, ring = A.ring;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tm = warp / T;
+    const int wt = warp - tm * T;
+    const int tl = wt * 32 + lane;
+    const int NL = 32 * T;
+    const size_t tints = team_ints(Qm, R, nbuf, kmb);
+    const int Qs = Qm + 4;
+    // regions of team i
+    auto stg_of = [&](int i) { return smem + (size_t)i * tints; };
+    auto ma_of = [&](int i) { return stg_of(i) + (size_t)nbuf * 3 * Qs; };
+    auto ta_of = [&](int i) { return ma_of(i) + Qm; };
+    auto mbox_of = [&](int i) { return ma_of(i) + Qm * (1 + (R >= 2 ? 2 : 0)); };
+    auto misc_of = [&](int i) { return mbox_of(i) + (size_t)kmb * Qm; };
+    for (int i = tid; i < NT * 32; i += blockDim.x) misc_of(i >> 5)[i & 31] = 0;
+    __syncthreads();
+    unsigned long long t_band0 = (A.trace && tid == 0) ? global_ns() : 0;
+
+    const int r = band * NT + tm;
+    if (tm < NT && r < H) {
+        const bool incx = (A.pass == 0 || A.pass == 2);
+        const bool incy = (A.pass < 2);
+        int *const Ma = incx ? A.M[0] : A.M[1];
+        int *const Mb = incy ? A.M[2] : A.M[3];
+        const int *const Mc = incx ? A.M[1] : A.M[0];
+        const int *const Md = incy ? A.M[3] : A.M[2];
+        const int y = incy ? r : H - 1 - r;
+        const bool has_next = r + 1 < H;
+        const int y_next = has_next ? (incy ? y + 1 : y - 1) : y;
+        const bool to_mbox = has_next && tm + 1 < NT;
+        const bool to_ring = has_next && tm + 1 == NT;
+        const bool from_mbox = r > 0 && tm > 0;
+        const bool from_ring = r > 0 && tm == 0;
+        const bool d_ok = A.read_d && (incy ? y + 1 < H : y - 1 >= 0);
+        const bool per_axis = (A.mode == 1);
+        int *const stg = stg_of(tm);
+        int *const maS = ma_of(tm);
+        int *const tA = ta_of(tm);
+        int *const tB = tA + Qm;
+        int *const mbox = mbox_of(tm);
+        int *const misc = misc_of(tm);
+        int *const produced = misc;
+        int *const wmin = misc + 24;
+        unsigned long long *const wkey = reinterpret_cast<unsigned long long *>(misc + 48);
+        int *const nx_mbox = to_mbox ? mbox_of(tm + 1) : nullptr;
+        const int *const nx_consumed = to_mbox ? misc_of(tm + 1) + 16 : nullptr;
+        const int *const pv_produced = from_mbox ? misc_of(tm - 1) : nullptr;
+        const int2 *const ll_in = from_ring ? A.ll + (size_t)(band - 1) * ring * Qm : nullptr;
+        int2 *const ll_out = to_ring ? A.ll + (size_t)band * ring * Qm : nullptr;
+        const size_t NQ = (size_t)W * H * Q;
+        // C is read in 16-byte chunks from the aligned-down base
+        const int cshift = (int)((reinterpret_cast<uintptr_t>(A.C) & 15) >> 2);
+        const int *const Cbase = A.C - cshift;
+
+        // lane -> line segments: on an axis with groups of G lanes, lane tl
+        // serves position jr = tl % G of line gi + k * gpt, gi = tl / G,
+        // gpt = 32 T / G (round k)
+        auto line_first = [&](const TeamAxis &X, int li) {
+            return X.stride == 1 ? li * X.L : (li % X.stride) + (li / X.stride) * X.stride * X.L;
+        };
+
+        auto prefetch = [&](int s) {
+            if (s < W) {
+                const int x = incx ? s : W - 1 - s;
+                const size_t pix = (size_t)y * W + x;
+                const bool c_ok = A.read_c && (incx ? x + 1 < W : x - 1 >= 0);
+                int *dst = stg + (size_t)(s % nbuf) * 3 * Qs;
+                const size_t e0 = pix * Q + cshift, e1 = e0 + Q, eend = NQ + cshift;
+                const size_t c0 = e0 >> 2, c1 = (e1 + 3) >> 2;
+                for (size_t c = c0 + tl; c < c1; c += NL) {
+                    const size_t rem = eend - 4 * c;
+                    cp16(dst + 4 * (c - c0), Cbase + 4 * c, rem >= 4 ? 16 : (int)rem * 4);
+                }
+                const int *sc = Mc + pix * Qm, *sd = Md + pix * Qm;
+                for (int c = tl; c < Qm / 4; c += NL) {
+                    cp16(dst + Qs + 4 * c, sc + 4 * c, c_ok ? 16 : 0);
+                    cp16(dst + 2 * Qs + 4 * c, sd + 4 * c, d_ok ? 16 : 0);
+                }
+            }
+            cp_async_commit();
+        };
+        for (int s = 0; s < nbuf - 1; ++s) prefetch(s);
+
+        unsigned cons_seen = 0;     // consumer progress seen by this producer (lane tl == 0)
+        int mb_cons_seen = 0;       // same, for the mailbox consumer
+        for (int s = 0; s < W; ++s) {
+            prefetch(s + nbuf - 1);
+            wait_groups(nbuf - 1);
+            bool bad = false;
+            // ---- m_b of this column from the row above ----
+            if (from_mbox) {
+                if (wt == 0) {
+                    long long spins = 0;
+                    while (true) {
+                        const bool ok = lane >= T || ld_acq_cta(pv_produced + lane) >= s + 1;
+                        if (__all_sync(kAllLanes, ok)) break;
+                        if (++spins > A.spin_limit || *s_abort) {
+                            bad = true;
+                            break;
+                        }
+                    }
+                }
+            } else if (from_ring) {
+                const int2 *p = ll_in + (size_t)(s % ring) * Qm;
+                const int tag = A.tag0 + s / ring;
+                int *dst = mbox + (s % kmb) * Qm;
+                for (int q = 2 * tl; q < Q; q += 2 * NL) {
+                    long long spins = 0;
+                    int4 v;
+                    while (true) {
+                        v = ld_rec2(p + q);
+                        if (v.y == tag && (q + 1 >= Q || v.w == tag)) break;
+                        if (++spins > A.spin_limit ||
+                            ((spins & 63) == 0 && (*s_abort || *(volatile int *)A.status != 0))) {
+                            bad = true;
+                            break;
+                        }
+                    }
+                    if (bad) break;
+                    dst[q] = v.x;
+                    if (q + 1 < Q) dst[q + 1] = v.z;
+                }
+            }
+            // producer side: room in the consumer's mailbox / record ring
+            if (tl == 0 && has_next) {
+                long long spins = 0;
+                if (to_mbox) {
+                    const int need = s - kmb + 1;
+                    while (mb_cons_seen < need) {
+                        mb_cons_seen = ld_acq_cta(nx_consumed);
+                        if (mb_cons_seen >= need) break;
+                        if (++spins > A.spin_limit || *s_abort) {
+                            bad = true;
+                            break;
+                        }
+                    }
+                } else {
+                    const int need = s - ring + 1;
+                    while ((int)cons_seen < need) {
+                        cons_seen = ld_relaxed_gpu(A.cons + band);
+                        if ((int)cons_seen >= need) break;
+                        if (++spins > A.spin_limit || *s_abort ||
+                            ((spins & 63) == 0 && *(volatile int *)A.status != 0)) {
+                            bad = true;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+            }
+            if (bad) {
+                atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
+                *s_abort = 1;
+            }
+            if (sync_or(tm, T, bad || *s_abort)) break;  // barrier 1
+
+            // ---- phase 0: sums, halving, axis-0 sweeps ----
+            const int *sb = stg + (size_t)(s % nbuf) * 3 * Qs;
+            const int *sC = sb + (int)((((size_t)y * W + (incx ? s : W - 1 - s)) * Q + cshift) & 3);
+            const int *sc = sb + Qs, *sd = sb + 2 * Qs;
+            const int *mbv = (r > 0) ? mbox + (s % kmb) * Qm : nullptr;
+            const bool has_ma = s > 0;
+            int ja = kBig, jb = kBig;                 // joint minima of the halved sums
+            unsigned long long key = ~0ull;           // final pass: (S_Omega, q) minimum
+            const int x = incx ? s : W - 1 - s;
+            const int xn = incx ? x + 1 : x - 1;
+            const bool a_out = A.write_a && s + 1 < W;
+            const int tag_out = A.tag0 + s / ring;
+            auto emit = [&](int q, int oa, int ob) {
+                maS[q] = oa;
+                if (a_out) Ma[((size_t)y * W + xn) * Qm + q] = oa;
+                if (has_next) {
+                    if (to_mbox)
+                        nx_mbox[(s % kmb) * Qm + q] = ob;
+                    else
+                        st_record(ll_out + (size_t)(s % ring) * Qm + q, ob, tag_out);
+                    if (A.write_b) Mb[((size_t)y_next * W + x) * Qm + q] = ob;
+                }
+            };
+            {
+                const TeamAxis X = A.ax[0];
+                const int lg = __ffs(X.G) - 1;
+                const int jr = tl & (X.G - 1), gi = tl >> lg, gpt = NL >> lg;
+#pragma unroll 1
+                for (int k = 0; k < X.rounds; ++k) {
+                    int ha[EM], hb[EM];
+                    const int li = gi + k * gpt;
+                    const bool gv = li < X.nlines;
+                    const int p0 = jr * X.E;
+                    const int qb = (gv ? line_first(X, li) : 0) + p0;
+#pragma unroll
+                    for (int i = 0; i < EM; ++i) {
+                        ha[i] = kBig;
+                        hb[i] = kBig;
+                        if (gv && i < X.E && p0 + i < X.L) {
+                            const int q = qb + i;
+                            const int c = sc[q], d = sd[q];
+                            int t = sC[q];
+                            if (has_ma) t += maS[q];
+                            if (mbv) t += mbv[q];
+                            ha[i] = floor_half(t + d - c);
+                            hb[i] = floor_half(t + c - d);
+                            if (A.final_) {
+                                const int so = t + c + d;
+                                key = min(key, ((unsigned long long)((unsigned)so ^ 0x80000000u) << 32) | (unsigned)q);
+                            }
+                        }
+                    }
+                    const int2 lm = seg_dt2<EM>(ha, hb, X.E, X.G, jr, A.lam, X.kc);
+                    if (gv) {
+                        ja = min(ja, lm.x);
+                        jb = min(jb, lm.y);
+                    }
+                    if (R == 1 || per_axis) {
+                        const int ca = lm.x + A.capv, cb = lm.y + A.capv;
+#pragma unroll
+                        for (int i = 0; i < EM; ++i) {
+                            ha[i] = min(ha[i], ca);
+                            hb[i] = min(hb[i], cb);
+                        }
+                    }
+                    if (gv) {
+#pragma unroll
+                        for (int i = 0; i < EM; ++i) {
+                            if (i < X.E && p0 + i < X.L) {
+                                const int q = qb + i;
+                                if (R == 1) {
+                                    emit(q, ha[i], hb[i]);
+                                } else {
+                                    tA[q] = ha[i];
+                                    tB[q] = hb[i];
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            // warp partial minima and argmin keys
+            ja = __reduce_min_sync(kAllLanes, ja);
+            jb = __reduce_min_sync(kAllLanes, jb);
+            if (A.final_) {
+                const unsigned hi = __reduce_min_sync(kAllLanes, (unsigned)(key >> 32));
+                const unsigned lo = __reduce_min_sync(kAllLanes, (unsigned)(key >> 32) == hi ? (unsigned)key : 0xffffffffu);
+                key = ((unsigned long long)hi << 32) | lo;
+            }
+            if (lane == 0) {
+                wmin[2 * wt] = ja;
+                wmin[2 * wt + 1] = jb;
+                if (A.final_) wkey[wt] = key;
+            }
+            if (sync_or(tm, T, *s_abort != 0)) break;  // barrier 2
+            // every lane of the team is done with this column's m_b
+            if (tl == 0) {
+                if (from_mbox) st_rel_cta(misc + 16, s + 1);
+                // the consumer's record loads above have returned (their values
+                // went through shared memory and a barrier) before this store
+                if (from_ring && ((s & 3) == 3 || s + 1 == W)) st_relaxed_gpu(A.cons + band - 1, (unsigned)(s + 1));
+                if (A.final_) {
+                    unsigned long long best = wkey[0];
+                    for (int w = 1; w < T; ++w) best = min(best, wkey[w]);
+                    A.labels[(size_t)y * W + x] = (int)(best & 0xffffffffu);
+                }
+            }
+            // ---- phases 1 .. R-1: sweeps of the other axes, clip, emit ----
+            if (R >= 2) {
+                int ga = kBig, gb = kBig;
+                if (!per_axis) {
+                    for (int w = 0; w < T; ++w) {
+                        ga = min(ga, wmin[2 * w]);
+                        gb = min(gb, wmin[2 * w + 1]);
+                    }
+                }
+#pragma unroll 1
+                for (int ax = 1; ax < R; ++ax) {
+                    if (ax == 2) sync(tm, T);
+                    const TeamAxis X = A.ax[ax];
+                    const bool last = (ax == R - 1);
+                    const int lg = __ffs(X.G) - 1;
+                    const int jr = tl & (X.G - 1), gi = tl >> lg, gpt = NL >> lg;
+#pragma unroll 1
+                    for (int k = 0; k < X.rounds; ++k) {
+                        int va[EM], vb[EM];
+                        const int li = gi + k * gpt;
+                        const bool gv = li < X.nlines;
+                        const int p0 = jr * X.E;
+                        const int qb = (gv ? line_first(X, li) : 0) + p0 * X.stride;
+#pragma unroll
+                        for (int i = 0; i < EM; ++i) {
+                            va[i] = kBig;
+                            vb[i] = kBig;
+                            if (gv && i < X.E && p0 + i < X.L) {
+                                va[i] = tA[qb + i * X.stride];
+                                vb[i] = tB[qb + i * X.stride];
+                            }
+                        }
+                        const int2 lm = seg_dt2<EM>(va, vb, X.E, X.G, jr, A.lam, X.kc);
+                        const int ca = (per_axis ? lm.x : ga) + A.capv;
+                        const int cb = (per_axis ? lm.y : gb) + A.capv;
+                        if (gv) {
+#pragma unroll
+                            for (int i = 0; i < EM; ++i) {
+                                if (i < X.E && p0 + i < X.L) {
+                                    const int q = qb + i * X.stride;
+                                    if (last) {
+                                        emit(q, min(va[i], ca), min(vb[i], cb));
+                                    } else {
+                                        tA[q] = per_axis ? min(va[i], ca) : va[i];
+                                        tB[q] = per_axis ? min(vb[i], cb) : vb[i];
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            if (to_mbox) {
+                __syncwarp();
+                if (lane == 0) st_rel_cta(produced + wt, s + 1);
+            }
+        }
+        cp_async_wait_0();
+    }
+    if (A.trace && tid == 0) {
+        A.trace[band * 4 + 0] = t_band0;
+        A.trace[band * 4 + 1] = global_ns();
+        A.trace[band * 4 + 2] = 0;
+        A.trace[band * 4 + 3] = sm_id();
+    }
+    __syncthreads();
+    return *s_abort == 0;
+}
+
+// dispatch on the labels-per-lane bound
+template <typename F>
+__device__ __forceinline__ bool team_dispatch(int em, F &&f) {
+    switch (em) {
+    case 9: return f(std::integral_constant<int, 9>());
+    case 17: return f(std::integral_constant<int, 17>());
+    default: return f(std::integral_constant<int, 33>());
+    }
+}
+
+}  // namespace edp

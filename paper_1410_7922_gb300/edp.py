@@ -65,7 +65,7 @@ def load() -> ctypes.CDLL:
         "edp_version": ([], I),
         "edp_status_string": ([I], ctypes.c_char_p),
         "edp_workspace_size": ([I, I, I, LS, PR], SZ),
-        "edp_set_tuning": ([I, I, I], I),
+        "edp_set_tuning": ([I, I, I, I], I),
         "edp_set_profile_events": ([P, I], I),
         "edp_set_trace": ([P, SZ], I),
         "edp_cost_volume": ([P, P, P, I, I, I, LS, PR, P, P], I),
@@ -171,9 +171,11 @@ def version() -> int:
     return load().edp_version()
 
 
-def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0, general_kernel: bool = False) -> None:
-    _check(load().edp_set_tuning(int(rows_per_block), int(labels_per_lane), int(bool(general_kernel))),
-           "set_tuning")
+def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0, general_kernel: bool = False,
+               warps_per_row: int = 0) -> None:
+    """Launch shape of the DP kernels (0 = automatic); results never depend on it."""
+    _check(load().edp_set_tuning(int(rows_per_block), int(labels_per_lane), int(warps_per_row),
+                                 int(bool(general_kernel))), "set_tuning")
 
 
 _prof_keep = None

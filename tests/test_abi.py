@@ -58,5 +58,6 @@ def test_host_validation_without_gpu(lib):
     b = edp.workspace_size(edp.OP_SOLVE, 64, 48, space, prior, 6)
     assert a >= 4 * 64 * 48 * 16 * 4 and b > a
     assert edp.status_string(edp.ERR_TIMEOUT) == "EDP_ERR_TIMEOUT"
-    assert lib.edp_set_tuning(-1, 0, 0) == edp.ERR_INVALID_ARG
-    assert lib.edp_set_tuning(0, 0, 2) == edp.ERR_INVALID_ARG
+    assert lib.edp_set_tuning(-1, 0, 0, 0) == edp.ERR_INVALID_ARG
+    assert lib.edp_set_tuning(0, 0, 0, 2) == edp.ERR_INVALID_ARG
+    assert lib.edp_set_tuning(0, 0, 13, 0) == edp.ERR_INVALID_ARG

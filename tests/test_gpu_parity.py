@@ -182,17 +182,21 @@ def test_edp_one_axis_rows_per_block(edp_lib, rows):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("rb,e", [(1, 1), (2, 2), (3, 4), (6, 3), (16, 8), (1, 16)])
-def test_edp_launch_shapes(edp_lib, rb, e):
-    """Results never depend on the launch shape (rows per block, labels per lane)."""
-    rng = np.random.default_rng(rb * 31 + e)
-    for Q, mode in (((24,), "joint"), ((7, 6), "per_axis"), ((7, 6), "joint")):
-        C = rng.integers(0, 21, size=(21, 19, int(np.prod(Q)))).astype(np.int32)
+@pytest.mark.parametrize("rb,t", [(1, 1), (2, 2), (3, 4), (6, 3), (4, 8), (1, 12), (15, 1)])
+def test_edp_launch_shapes(edp_lib, rb, t):
+    """Results never depend on the launch shape of the multi-axis kernel
+    (rows per block, warps per row)."""
+    rng = np.random.default_rng(rb * 31 + t)
+    for Q, mode in (((24,), "joint"), ((7, 6), "per_axis"), ((7, 6), "joint"), ((33, 33), "joint"),
+                    ((5, 4, 3), "per_axis")):
+        n = int(np.prod(Q))
+        H, W = (7, 11) if n > 500 else (21, 19)
+        C = rng.integers(0, 21, size=(H, W, n)).astype(np.int32)
         prior = {"lam": 6, "g": 3, "l1": 1, "mode": mode}
         want = oracle.edp(C, sp(Q), prior, iters=2, tier=1)
-        edp_lib.set_tuning(rb, e, True)
+        edp_lib.set_tuning(rb, 0, True, warps_per_row=t)
         got = host(edp_lib.solve(dev(C), sp(Q), prior, iters=2))
-        assert np.array_equal(got, want), (Q, mode, rb, e)
+        assert np.array_equal(got, want), (Q, mode, rb, t)
 
 
 def test_edp_stereo_450x375_full_size(edp_lib):
