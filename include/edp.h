@@ -98,7 +98,8 @@ typedef struct {
 enum {
     EDP_OP_SCANLINE_DP = 1,
     EDP_OP_SOLVE = 2,
-    EDP_OP_SOLVE_IMAGES = 3 /* edp_solve_images and edp_solve_images_host */
+    EDP_OP_SOLVE_IMAGES = 3, /* edp_solve_images and edp_solve_images_host */
+    EDP_OP_COARSE = 4        /* edp_coarse_labels */
 };
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -119,7 +120,9 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
  *   warps_per_row    warps that share one image row in the multi-axis
  *                    scan-pass kernel (1..12);
  *   general_kernel   1: one-axis label spaces also take the multi-axis
- *                    scan-pass kernel instead of the warp-per-row one.
+ *                    scan-pass kernel instead of the warp-per-row one;
+ *                    2: in addition, multi-axis spaces take its lane-group
+ *                    form instead of the whole-line form.
  * Used by the autotuner and the tests; results never depend on it.  A shape
  * the kernels cannot run makes the next solve return EDP_ERR_UNSUPPORTED.
  * Not thread-safe with concurrent solves. */
@@ -257,6 +260,41 @@ int edp_net_features(const uint8_t *I0, const uint8_t *I1, const int32_t *wta_la
 /* Box centres (int32 [n][2], label coordinates) from network outputs:
  * round to the nearest label, clamp into the space. */
 int edp_net_centres(const float *out, int n, const edp_label_space *space, int32_t *centre, edp_stream_t stream);
+
+/* Coarse-level labeling for the proposal (no counterpart in the paper; an
+ * input of the proposal network).  Two-axis spaces with step +1 only
+ * (EDP_ERR_UNSUPPORTED otherwise).  I0, I1: device uint8 [H][pitch].  Both
+ * images are halved (2x2 averages rounded half up, (W+1)/2 x (H+1)/2), full
+ * EDP (Algorithm 1, params->iters iterations, the given prior and cost) runs
+ * there on the label space with halved offsets (ceil(vmin/2) ..
+ * floor(vmax/2) per axis), and each full-resolution pixel (x, y) gets the
+ * label of coarse pixel (x/2, y/2) with its offsets doubled and clamped into
+ * `space`.  labels: device int32 [H][W] (linear label index of `space`).
+ * ws: edp_workspace_size(EDP_OP_COARSE, ...) bytes, 256-byte aligned; the
+ * coarse solve's status word is the workspace's first int at offset 256.
+ * Errors as edp_solve_images. */
+int edp_coarse_labels(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, const edp_label_space *space,
+                      const edp_params *params, int32_t *labels, void *ws, size_t ws_bytes, edp_stream_t stream);
+
+/* Network input (bf16 [H][W][5]) from a labeling of a two-axis space with
+ * step +1: I0/255, I1/255, the label's coordinates minus (Q_r - 1)/2,
+ * divided by `scale`, and its data cost (Eq. Cost_value with params->l2,
+ * params->cmax) / cmax.  Images uint8 [H][pitch], labels int32 [H][W]. */
+int edp_net_features_labels(const uint8_t *I0, const uint8_t *I1, const int32_t *labels, int W, int H, int pitch,
+                            const edp_label_space *space, const edp_params *params, float scale, void *x,
+                            edp_stream_t stream);
+
+/* Box centres (int32 [n][2]) as a correction of a base labeling: the base
+ * label's coordinates plus the rounded network output (label units), clamped
+ * into the space.  out: float [n][2]; base: int32 [n]. */
+int edp_net_centres_residual(const float *out, const int32_t *base, int n, const edp_label_space *space,
+                             int32_t *centre, edp_stream_t stream);
+
+/* Training targets (float [n][2], label units) of a labeling: its label
+ * coordinates minus those of `base` (int32 [n]), or minus (Q_r - 1)/2 when
+ * base is NULL. */
+int edp_net_targets(const int32_t *labels, const int32_t *base, int n, const edp_label_space *space, float *target,
+                    edp_stream_t stream);
 
 /* One problem of a batch: a device image pair (or triple) in, labels and
  * energy out.  Images are uint8 [H][pitch]. */

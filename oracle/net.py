@@ -148,3 +148,91 @@ def features(I0: np.ndarray, I1: np.ndarray, wta_flow: np.ndarray, wta_cost: np.
     displacement (/flow_scale, 2 channels) and its cost (/cost_scale)."""
     return np.stack([I0 / 255.0, I1 / 255.0, wta_flow[..., 0] / flow_scale, wta_flow[..., 1] / flow_scale,
                      wta_cost / cost_scale]).astype(np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Coarse-level proposal inputs (not in the paper either): the image pyramid
+# step, the coarse-to-fine label map, the network input built from a
+# labeling, and the residual centre / target conventions.
+# ---------------------------------------------------------------------------
+
+def pyr_down2(I: np.ndarray) -> np.ndarray:
+    """2x2 box average, rounded half up; odd sizes repeat the last row/column.
+    Output shape ((H+1)//2, (W+1)//2), uint8."""
+    H, W = I.shape
+    Hc, Wc = (H + 1) // 2, (W + 1) // 2
+    out = np.zeros((Hc, Wc), dtype=np.uint8)
+    for yc in range(Hc):
+        for xc in range(Wc):
+            ys = (min(2 * yc, H - 1), min(2 * yc + 1, H - 1))
+            xs = (min(2 * xc, W - 1), min(2 * xc + 1, W - 1))
+            total = sum(int(I[y, x]) for y in ys for x in xs)
+            out[yc, xc] = (total + 2) // 4
+    return out
+
+
+def halved_space(vmin: tuple[int, int], Q: tuple[int, int]) -> tuple[tuple[int, int], tuple[int, int]]:
+    """Offsets o in [vmin, vmin + Q - 1] per axis -> the coarse axis holding
+    the integers in [ceil(vmin / 2), floor((vmin + Q - 1) / 2)]: (vmin_c, Q_c)."""
+    vc, qc = [], []
+    for v, q in zip(vmin, Q):
+        lo = -((-v) // 2)          # ceil(v / 2)
+        hi = (v + q - 1) // 2      # floor
+        vc.append(lo)
+        qc.append(max(1, hi - lo + 1))
+    return tuple(vc), tuple(qc)
+
+
+def labels_up2(lc: np.ndarray, vmin_c, Qc, vmin, Q, H: int, W: int) -> np.ndarray:
+    """Coarse labels (linear index, axis 0 fastest) -> full resolution: pixel
+    (x, y) takes coarse pixel (x//2, y//2), offsets doubled, clamped."""
+    Hc, Wc = lc.shape
+    out = np.zeros((H, W), dtype=np.int64)
+    for y in range(H):
+        for x in range(W):
+            q = int(lc[min(y // 2, Hc - 1), min(x // 2, Wc - 1)])
+            o = (2 * (vmin_c[0] + q % Qc[0]), 2 * (vmin_c[1] + q // Qc[0]))
+            q0 = min(max(o[0] - vmin[0], 0), Q[0] - 1)
+            q1 = min(max(o[1] - vmin[1], 0), Q[1] - 1)
+            out[y, x] = q0 + Q[0] * q1
+    return out
+
+
+def features_from_labels(I0, I1, labels, vmin, Q, l2: int, cmax: int, scale: float) -> np.ndarray:
+    """Network input [5][H][W] from a labeling: both frames / 255, the label
+    coordinates minus (Q_r - 1)/2, / scale, and the label's data cost
+    min(|I1(x + o) - I0(x)|^l2, cmax) / cmax (out of the image: cmax)."""
+    H, W = I0.shape
+    f = np.zeros((5, H, W))
+    for y in range(H):
+        for x in range(W):
+            q = int(labels[y, x])
+            q0, q1 = q % Q[0], q // Q[0]
+            xs, ys = x + vmin[0] + q0, y + vmin[1] + q1
+            c = cmax
+            if 0 <= xs < W and 0 <= ys < H:
+                d = abs(int(I1[ys, xs]) - int(I0[y, x]))
+                c = min(d if l2 == 1 else d * d, cmax)
+            f[:, y, x] = (I0[y, x] / 255.0, I1[y, x] / 255.0, (q0 - 0.5 * (Q[0] - 1)) / scale,
+                          (q1 - 0.5 * (Q[1] - 1)) / scale, c / cmax)
+    return f
+
+
+def targets(labels: np.ndarray, Q, base: np.ndarray | None = None) -> np.ndarray:
+    """[..][2] label coordinates minus the base labeling's (or minus the
+    space's middle without one)."""
+    q0, q1 = labels % Q[0], labels // Q[0]
+    if base is None:
+        b0, b1 = 0.5 * (Q[0] - 1), 0.5 * (Q[1] - 1)
+    else:
+        b0, b1 = base % Q[0], base // Q[0]
+    return np.stack([q0 - b0, q1 - b1], axis=-1).astype(np.float64)
+
+
+def centres_residual(out: np.ndarray, base: np.ndarray, Q) -> np.ndarray:
+    """[..][2] int centres: base coordinates + out rounded half away from
+    zero, clamped into the space."""
+    r = np.where(out >= 0, np.floor(out + 0.5), -np.floor(-out + 0.5)).astype(np.int64)
+    c0 = np.clip(base % Q[0] + r[..., 0], 0, Q[0] - 1)
+    c1 = np.clip(base // Q[0] + r[..., 1], 0, Q[1] - 1)
+    return np.stack([c0, c1], axis=-1)

@@ -22,6 +22,7 @@ int g_tune_rb = 0;       // rows per block override (0 = automatic)
 int g_tune_e = 0;        // labels per lane target override, scanline DP (0 = automatic)
 int g_tune_t = 0;        // warps per row override, multi-axis scan pass (0 = automatic)
 int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass kernel
+int g_generic_team = 0;  // 1: multi-axis problems take the generic team body (tests)
 void *const *g_prof_events = nullptr;  // optional per-pass events (profiling hook)
 int g_prof_n = 0;
 unsigned long long *g_trace = nullptr;  // optional per-band trace buffer (device)
@@ -335,33 +336,58 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         P->em = a.EMt;
         return EDP_OK;
     }
-    // multi-axis (team) kernel
+    // multi-axis (team) kernel.  Lean form: two or more axes whose lines hold
+    // 9, 17 or 33 labels, Tv warps per message vector, lanes owning whole lines.
     TeamShape S;
-    bool have = false;
-    const int tmax = fixed_threads ? std::min(12, fixed_threads / 32) : 12;
-    if (g_tune_t > 0) {
-        if (g_tune_t > tmax || !team_shape(g, g_tune_t, p->g, &S)) return EDP_ERR_UNSUPPORTED;
-        if (S.em > 17 && S.T > 8) return EDP_ERR_UNSUPPORTED;
-        have = true;
+    bool lean = g.R >= 2 && !g_generic_team;
+    int LM = 0, Tv = 0;
+    for (int r = 0; r < g.R; ++r) {
+        LM = std::max(LM, g.Qr[r]);
+        lean = lean && (g.Qr[r] == 9 || g.Qr[r] == 17 || g.Qr[r] == 33);
+    }
+    const int tmax = fixed_threads ? std::min(12, fixed_threads / 32) : (lean ? 8 : 12);
+    if (lean) {
+        LM = LM <= 9 ? 9 : (LM <= 17 ? 17 : 33);
+        int maxlines = 1;
+        for (int r = 0; r < g.R; ++r) maxlines = std::max(maxlines, g.Q / g.Qr[r]);
+        Tv = g_tune_t > 0 ? std::max(1, g_tune_t / 2) : std::min((maxlines + 31) / 32, 4);
+        if (2 * Tv > tmax) Tv = tmax / 2;
+        if (Tv < 1) return EDP_ERR_UNSUPPORTED;
+        S.T = 2 * Tv;
+        S.em = LM;
+        int stride = 1;
+        for (int r = 0; r < 3; ++r) {
+            const int L = r < g.R ? g.Qr[r] : 1;
+            S.ax[r] = TeamAxis{L, 1, L, g.Q / L, stride, 0, 1};
+            stride *= L;
+        }
     } else {
-        for (int T = 1; T <= tmax; ++T) {
-            if (g.R == 1 && T > 1) break;  // one line: one warp
-            TeamShape c;
-            if (!team_shape(g, T, p->g, &c)) continue;
-            if (c.em > 17 && T > 8) continue;  // built for <= 256 threads (<= 384 otherwise)
-            if (!have || c.cost * 10 < S.cost * 9) {
-                S = c;
-                have = true;
+        bool have = false;
+        if (g_tune_t > 0) {
+            if (g_tune_t > tmax || !team_shape(g, g_tune_t, p->g, &S)) return EDP_ERR_UNSUPPORTED;
+            if (S.em > 17 && S.T > 8) return EDP_ERR_UNSUPPORTED;
+            have = true;
+        } else {
+            for (int T = 1; T <= tmax; ++T) {
+                if (g.R == 1 && T > 1) break;  // one line: one warp
+                TeamShape c;
+                if (!team_shape(g, T, p->g, &c)) continue;
+                if (c.em > 17 && T > 8) continue;  // built for <= 256 threads (<= 384 otherwise)
+                if (!have || c.cost * 10 < S.cost * 9) {
+                    S = c;
+                    have = true;
+                }
             }
         }
+        if (!have) return EDP_ERR_UNSUPPORTED;
     }
-    if (!have) return EDP_ERR_UNSUPPORTED;
     const int T = S.T;
-    const int thr_cap = fixed_threads ? fixed_threads : (S.em > 17 ? 256 : 384);
+    const int thr_cap = fixed_threads ? fixed_threads : (lean || S.em > 17 ? 256 : 384);
     int NT = 0, nbuf = 3, kmb = 4;
-    for (int attempt = 0; attempt < 2 && NT < 1; ++attempt) {
+    for (int attempt = 0; attempt < 3 && NT < 1; ++attempt) {
         if (attempt == 1) nbuf = kmb = 2;
-        NT = std::min(thr_cap / (32 * T), 15);
+        if (attempt == 2) kmb = 1;  // one team per block: the slot of the copied-in records only
+        NT = std::min(thr_cap / (32 * T), attempt == 2 ? 1 : 15);
         while (NT > 0 && pass_team_smem(NT, L.Qm, g.R, nbuf, kmb) > (size_t)kMaxSmem) --NT;
     }
     if (NT < 1) return EDP_ERR_UNSUPPORTED;
@@ -371,6 +397,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         NT = std::max(1, std::min(NT, want));
     }
     NT = std::min(NT, H);
+    if (kmb == 1 && NT > 1) return EDP_ERR_UNSUPPORTED;
     TeamArgs &a = P->ta;
     a.C = C;
     for (int k = 0; k < 4; ++k) a.M[k] = M[k];
@@ -392,6 +419,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
     a.kmb = kmb;
     a.ring = team_ring(W, kResidentMin);
     a.em = S.em;
+    a.lean = lean;
     a.nbands = (H + NT - 1) / NT;
     a.spin_limit = 4000000;
     P->laps = (W + a.ring - 1) / a.ring;
@@ -419,7 +447,7 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int occ = std::max(1, edp_pass_team_occupancy(P.em, P.threads, P.smem));
+        const int occ = std::max(1, edp_pass_team_occupancy(P.em, P.ta.lean, P.threads, P.smem));
         grid_t = std::min(P.nbands, occ * sms);
         // a smaller resident set than the ring was sized for could stall the back-pressure
         if (grid_t < P.nbands && team_ring(W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
@@ -559,11 +587,12 @@ const char *edp_status_string(int status) {
 int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, int general_kernel) {
     if (rows_per_block < 0 || labels_per_lane < 0 || labels_per_lane > kEM) return EDP_ERR_INVALID_ARG;
     if (warps_per_row < 0 || warps_per_row > 12) return EDP_ERR_INVALID_ARG;
-    if (general_kernel != 0 && general_kernel != 1) return EDP_ERR_INVALID_ARG;
+    if (general_kernel < 0 || general_kernel > 2) return EDP_ERR_INVALID_ARG;
     g_tune_rb = rows_per_block;
     g_tune_e = labels_per_lane;
     g_tune_t = warps_per_row;
-    g_force_general = general_kernel;
+    g_force_general = general_kernel >= 1;
+    g_generic_team = general_kernel == 2;
     return EDP_OK;
 }
 
@@ -581,6 +610,45 @@ int edp_set_trace(void *device_buffer, size_t bytes) {
     return EDP_OK;
 }
 
+namespace {
+// Coarse level of the proposal (two-axis motion spaces): the images halved
+// (2x2 averages), the label space with halved offsets.
+struct CoarseGeometry {
+    int Wc, Hc;
+    edp_label_space sc;
+};
+int coarse_geometry(int W, int H, const edp_label_space *s, CoarseGeometry *c) {
+    if (!s || s->R != 2 || s->step[0] != 1 || s->step[1] != 1 || s->Q[2] != 1) return EDP_ERR_UNSUPPORTED;
+    c->Wc = (W + 1) / 2;
+    c->Hc = (H + 1) / 2;
+    memset(&c->sc, 0, sizeof c->sc);
+    c->sc.R = 2;
+    for (int r = 0; r < 2; ++r) {
+        const int lo = s->vmin[r], hi = s->vmin[r] + s->Q[r] - 1;
+        const int clo = lo >= 0 ? (lo + 1) / 2 : -((-lo) / 2);  // ceil(lo / 2)
+        const int chi = hi >= 0 ? hi / 2 : -((-hi + 1) / 2);     // floor(hi / 2)
+        c->sc.vmin[r] = clo;
+        c->sc.Q[r] = std::max(1, chi - clo + 1);
+        c->sc.step[r] = 1;
+    }
+    c->sc.Q[2] = 1;
+    c->sc.step[2] = 1;
+    return EDP_OK;
+}
+struct CoarseLayout {
+    size_t img[2], labels, solve, end;
+};
+CoarseLayout coarse_layout(const CoarseGeometry &c, int iters) {
+    CoarseLayout L;
+    L.img[0] = kHeader;
+    L.img[1] = align_up(L.img[0] + (size_t)c.Wc * c.Hc);
+    L.labels = align_up(L.img[1] + (size_t)c.Wc * c.Hc);
+    L.solve = align_up(L.labels + (size_t)c.Wc * c.Hc * 4);
+    L.end = L.solve + images_layout(c.Wc, c.Hc, c.sc.Q[0] * c.sc.Q[1], 2, iters).end;
+    return L;
+}
+}  // namespace
+
 size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space, const edp_params *params) {
     Geometry g;
     if (W < 1 || H < 1 || check_space(space, &g) || !params) return 0;
@@ -592,6 +660,11 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space, co
         return solve_layout(W, H, g.Q, g.R, iters).end;
     case EDP_OP_SOLVE_IMAGES:
         return images_layout(W, H, g.Q, g.R, iters).end;
+    case EDP_OP_COARSE: {
+        CoarseGeometry c;
+        if (coarse_geometry(W, H, space, &c)) return 0;
+        return coarse_layout(c, iters).end;
+    }
     default:
         return 0;
     }
@@ -767,7 +840,7 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     // one block shape for the wave: 8 warps (one-axis bands of 8 rows, or
     // teams of the multi-axis body)
     const int threads = 256;
-    int em = 9;
+    int lm = 9, gen = 0;
     size_t smem = 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -782,10 +855,15 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
         int rc = plan_solve(C, pr.W, pr.H, g, &pr.params, pr.labels, pws, &plans[k], threads);
         if (rc) return rc;
         off += problem_bytes(pr, g);
-        if (!plans[k].r1) em = std::max(em, plans[k].em);
+        if (!plans[k].r1) {
+            if (plans[k].ta.lean)
+                lm = std::max(lm, plans[k].em);
+            else
+                gen = 1;
+        }
         smem = std::max(smem, plans[k].smem);
     }
-    const int occ = std::max(1, edp_batched_occupancy(em, threads, smem));
+    const int occ = std::max(1, edp_batched_occupancy(lm, gen, threads, smem));
     off = ctrl;
     for (int k = 0; k < n; ++k) {
         const edp_problem &pr = probs[first + k];
@@ -856,7 +934,7 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     if (launch_zero_batched(zb, st)) return EDP_ERR_CUDA;
     if (launch_cost_batched(cb, max_entries, st)) return EDP_ERR_CUDA;
     const int grid = std::max(1, std::min(B.slots * B.per_slot, occ * sms));
-    if (launch_edp_batched(B, em, threads, smem, grid, st)) return EDP_ERR_CUDA;
+    if (launch_edp_batched(B, lm, gen, threads, smem, grid, st)) return EDP_ERR_CUDA;
     if (launch_energy_batched(eb, max_pixels, st)) return EDP_ERR_CUDA;
     return EDP_OK;
 }
@@ -1119,6 +1197,61 @@ int edp_net_centres(const float *out, int n, const edp_label_space *space, int32
     if (!out || !centre || !space || n < 1 || space->R != 2) return EDP_ERR_INVALID_ARG;
     return net_centres_launch(out, n, space->Q[0], space->Q[1], centre, (cudaStream_t)stream) ? EDP_ERR_CUDA
                                                                                                 : EDP_OK;
+}
+
+int edp_coarse_labels(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, const edp_label_space *space,
+                      const edp_params *params, int32_t *labels, void *ws, size_t ws_bytes, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if ((rc = check_images(I0, I1, nullptr, W, H, pitch, space, params))) return rc;
+    if (!labels || !ws || params->iters < 1) return EDP_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
+    CoarseGeometry c;
+    if ((rc = coarse_geometry(W, H, space, &c))) return rc;
+    if (ws_bytes < edp_workspace_size(EDP_OP_COARSE, W, H, space, params)) return EDP_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    const CoarseLayout L = coarse_layout(c, params->iters);
+    uint8_t *h0 = w + L.img[0], *h1 = w + L.img[1];
+    int32_t *lc = reinterpret_cast<int32_t *>(w + L.labels);
+    if (pyr_down2_launch(I0, W, H, pitch, h0, st) || pyr_down2_launch(I1, W, H, pitch, h1, st)) return EDP_ERR_CUDA;
+    rc = edp_solve_images(h0, h1, nullptr, c.Wc, c.Hc, c.Wc, &c.sc, params, lc, nullptr, w + L.solve, L.end - L.solve,
+                          stream);
+    if (rc) return rc;
+    return labels_up2_launch(lc, c.Wc, c.Hc, c.sc.Q[0], c.sc.vmin[0], c.sc.vmin[1], W, H, space->Q[0], space->Q[1],
+                             space->vmin[0], space->vmin[1], labels, st)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
+}
+
+int edp_net_features_labels(const uint8_t *I0, const uint8_t *I1, const int32_t *labels, int W, int H, int pitch,
+                            const edp_label_space *space, const edp_params *params, float scale, void *x,
+                            edp_stream_t stream) {
+    if (!I0 || !I1 || !labels || !x || !space || !params || W < 1 || H < 1 || pitch < W) return EDP_ERR_INVALID_ARG;
+    if (space->R != 2 || space->step[0] != 1 || space->step[1] != 1 || !(scale > 0.f) || params->cmax < 1)
+        return EDP_ERR_INVALID_ARG;
+    return net_features_lab_launch(I0, I1, labels, W, H, pitch, space->Q[0], space->Q[1], space->vmin[0],
+                                   space->vmin[1], params->l2, params->cmax, scale, x, (cudaStream_t)stream)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
+}
+
+int edp_net_centres_residual(const float *out, const int32_t *base, int n, const edp_label_space *space,
+                             int32_t *centre, edp_stream_t stream) {
+    if (!out || !base || !centre || !space || n < 1 || space->R != 2) return EDP_ERR_INVALID_ARG;
+    return net_centres_base_launch(out, base, n, space->Q[0], space->Q[1], centre, (cudaStream_t)stream)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
+}
+
+int edp_net_targets(const int32_t *labels, const int32_t *base, int n, const edp_label_space *space, float *target,
+                    edp_stream_t stream) {
+    if (!labels || !target || !space || n < 1 || space->R != 2) return EDP_ERR_INVALID_ARG;
+    return net_targets_launch(labels, base, n, space->Q[0], space->Q[1], target, (cudaStream_t)stream)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
 }
 
 int edp_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stream_t stream) {

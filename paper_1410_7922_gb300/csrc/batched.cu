@@ -20,7 +20,7 @@ namespace edp {
 
 static_assert(sizeof(BatchArgs) <= 32000, "batch descriptors must fit the kernel parameter space");
 
-template <int EM>
+template <int LM, bool GEN>
 __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -78,7 +78,15 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
             a.final_ = f.final_;
             a.cons = P.cons + (size_t)slot * P.nbands;
             a.tag0 = 1 + slot * P.laps;
-            ok = team_band<EM>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+            if (a.lean)
+                ok = team_band<LM, true>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+            else if constexpr (GEN)
+                ok = team_band<33, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+            else {
+                // the host never puts a generic-body problem in a lean-only wave
+                if (tid == 0) atomicCAS(B.status, 0, 2 /* EDP_ERR_UNSUPPORTED */);
+                ok = false;
+            }
         }
         if (!ok) return;
         // both bodies end with a block barrier: every write of this band is done
@@ -89,24 +97,25 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
     }
 }
 
-template <int EM>
+template <int LM, bool GEN>
 static void *batched_kernel() {
-    return reinterpret_cast<void *>(edp_batched_kernel<EM>);
+    return reinterpret_cast<void *>(edp_batched_kernel<LM, GEN>);
 }
-static void *batched_kernel_for(int em) {
-    return em == 9 ? batched_kernel<9>() : (em == 17 ? batched_kernel<17>() : batched_kernel<33>());
+static void *batched_kernel_for(int lm, int gen) {
+    (void)lm;  // the lean body dispatches on the line lengths itself
+    return gen ? batched_kernel<33, true>() : batched_kernel<33, false>();
 }
 
-int edp_batched_occupancy(int em, int threads, size_t smem) {
-    void *k = batched_kernel_for(em);
+int edp_batched_occupancy(int lm, int gen, int threads, size_t smem) {
+    void *k = batched_kernel_for(lm, gen);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
     return occ;
 }
 
-int launch_edp_batched(const BatchArgs &a, int em, int threads, size_t smem, int grid, cudaStream_t st) {
-    void *k = batched_kernel_for(em);
+int launch_edp_batched(const BatchArgs &a, int lm, int gen, int threads, size_t smem, int grid, cudaStream_t st) {
+    void *k = batched_kernel_for(lm, gen);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     void *args[] = {const_cast<BatchArgs *>(&a)};
     return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, st) == cudaSuccess ? 0 : -2;

@@ -4,8 +4,8 @@
 
 namespace edp {
 
-template <int EM>
-__global__ void __launch_bounds__(EM > 17 ? 256 : 384) edp_pass_team_kernel(TeamArgs A) {
+template <int EM, bool LEAN>
+__global__ void __launch_bounds__(LEAN || EM > 17 ? 256 : 384, 1) edp_pass_team_kernel(TeamArgs A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
     __shared__ volatile int s_abort;
@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(EM > 17 ? 256 : 384) edp_pass_team_kernel(Team
         __syncthreads();
         const int band = s_band;
         if (band >= A.nbands) break;
-        if (!team_band<EM>(A, band, smem_i, &s_abort)) return;
+        if (!team_band<EM, LEAN>(A, band, smem_i, &s_abort)) return;
     }
 }
 
@@ -25,16 +25,17 @@ size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb) {
     return (size_t)NT * team::team_ints(Qm, R, nbuf, kmb) * 4;
 }
 
-template <int EM>
+template <int EM, bool LEAN>
 static void *team_kernel() {
-    return reinterpret_cast<void *>(edp_pass_team_kernel<EM>);
+    return reinterpret_cast<void *>(edp_pass_team_kernel<EM, LEAN>);
 }
-static void *team_kernel_for(int em) {
-    return em == 9 ? team_kernel<9>() : (em == 17 ? team_kernel<17>() : team_kernel<33>());
+static void *team_kernel_for(int em, int lean) {
+    if (lean) return team_kernel<33, true>();  // the lean body dispatches on the line lengths itself
+    return em == 9 ? team_kernel<9, false>() : (em == 17 ? team_kernel<17, false>() : team_kernel<33, false>());
 }
 
-int edp_pass_team_occupancy(int em, int threads, size_t smem) {
-    void *k = team_kernel_for(em);
+int edp_pass_team_occupancy(int em, int lean, int threads, size_t smem) {
+    void *k = team_kernel_for(em, lean);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
@@ -42,7 +43,7 @@ int edp_pass_team_occupancy(int em, int threads, size_t smem) {
 }
 
 int launch_edp_pass_team(const TeamArgs &a, int threads, size_t smem, cudaStream_t st) {
-    void *k = team_kernel_for(a.em);
+    void *k = team_kernel_for(a.em, a.lean);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     void *args[] = {const_cast<TeamArgs *>(&a)};
     if (cudaLaunchKernel(k, dim3(a.grid), dim3(threads), args, smem, st) != cudaSuccess) return -2;

@@ -54,13 +54,14 @@ struct TeamArgs {
     int T, NT;              // warps per team (one row), teams per block
     int nbuf, kmb, ring;    // staging buffers, mailbox slots, record ring columns
     int tag0;               // tag of the first ring lap of this pass
-    int em;                 // labels-per-lane bound of the instantiation
+    int lean;               // 1: lanes own whole lines of one vector (two or more axes)
+    int em;                 // instantiation bound: labels per lane, or line length (lean)
     int nbands, grid;
     long long spin_limit;
     unsigned long long *trace;  // optional: per band {start ns, end ns, 0, sm id}
 };
 int launch_edp_pass_team(const TeamArgs &a, int threads, size_t smem, cudaStream_t st);
-int edp_pass_team_occupancy(int em, int threads, size_t smem);
+int edp_pass_team_occupancy(int em, int lean, int threads, size_t smem);
 size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb);
 
 // one EDP scan pass, one label axis, one warp per row (edp_pass_r1.cu)
@@ -124,8 +125,10 @@ struct BatchArgs {
     long long spin_limit;
     BatchProblem p[kMaxBatch];
 };
-int launch_edp_batched(const BatchArgs &a, int em, int threads, size_t smem, int grid, cudaStream_t st);
-int edp_batched_occupancy(int em, int threads, size_t smem);
+// lm: line-length bound of the lean team body (9, 17, 33, 65); gen: the wave
+// also holds problems for the generic team body
+int launch_edp_batched(const BatchArgs &a, int lm, int gen, int threads, size_t smem, int grid, cudaStream_t st);
+int edp_batched_occupancy(int lm, int gen, int threads, size_t smem);
 
 
 
@@ -196,5 +199,12 @@ int net_features_launch(const uint8_t *I0, const uint8_t *I1, const int *wta_q, 
                         int Q0, int Q1, float scale, float cmax, void *out, cudaStream_t st);
 int net_centres_launch(const float *out, int n, int Q0, int Q1, int *centre, cudaStream_t st);
 int wta_launch(const CostArgs &a, int radius, int *labels, int *cost, cudaStream_t st);
+int pyr_down2_launch(const uint8_t *I, int W, int H, int pitch, uint8_t *out, cudaStream_t st);
+int labels_up2_launch(const int *lc, int Wc, int Hc, int Qc0, int vminc0, int vminc1, int W, int H, int Q0, int Q1,
+                      int vmin0, int vmin1, int *out, cudaStream_t st);
+int net_features_lab_launch(const uint8_t *I0, const uint8_t *I1, const int *lab, int W, int H, int pitch, int Q0,
+                            int Q1, int vmin0, int vmin1, int l2, int cmax, float scale, void *out, cudaStream_t st);
+int net_centres_base_launch(const float *out, const int *base, int n, int Q0, int Q1, int *centre, cudaStream_t st);
+int net_targets_launch(const int *lab, const int *base, int n, int Q0, int Q1, float *t, cudaStream_t st);
 
 }  // namespace edp

@@ -219,6 +219,82 @@ __global__ void net_centres(const float *out, int n, int Q0, int Q1, int *centre
     }
 }
 
+// Coarse level of the proposal: 2x2 box average of an image, rounded half
+// up (edge pixels repeat on odd sizes).
+__global__ void pyr_down2(const uint8_t *I, int W, int H, int pitch, uint8_t *out, int Wc, int Hc) {
+    const int n = Wc * Hc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int xc = i % Wc, yc = i / Wc;
+        const int x0 = min(2 * xc, W - 1), x1 = min(2 * xc + 1, W - 1);
+        const int y0 = min(2 * yc, H - 1), y1 = min(2 * yc + 1, H - 1);
+        const int sum = I[(size_t)y0 * pitch + x0] + I[(size_t)y0 * pitch + x1] + I[(size_t)y1 * pitch + x0] +
+                        I[(size_t)y1 * pitch + x1];
+        out[i] = (uint8_t)((sum + 2) >> 2);
+    }
+}
+
+// Coarse labels to full resolution: pixel (x, y) takes the label of coarse
+// pixel (x/2, y/2); its offsets double and are clamped into the full space.
+__global__ void labels_up2(const int *lc, int Wc, int Hc, int Qc0, int vminc0, int vminc1, int W, int H, int Q0,
+                           int Q1, int vmin0, int vmin1, int *out) {
+    const int n = W * H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = i % W, y = i / W;
+        const int q = lc[min(y / 2, Hc - 1) * Wc + min(x / 2, Wc - 1)];
+        const int o0 = 2 * (vminc0 + q % Qc0), o1 = 2 * (vminc1 + q / Qc0);
+        const int q0 = min(max(o0 - vmin0, 0), Q0 - 1), q1 = min(max(o1 - vmin1, 0), Q1 - 1);
+        out[i] = q0 + Q0 * q1;
+    }
+}
+
+// Network input from a labeling: I0/255, I1/255, the label's coordinates
+// centred on the space's middle / scale, and its data cost (Eq. Cost_value)
+// / cmax.
+__global__ void net_features_lab(const uint8_t *I0, const uint8_t *I1, const int *lab, int W, int H, int pitch,
+                                 int Q0, int Q1, int vmin0, int vmin1, int l2, int cmax, float scale,
+                                 __nv_bfloat16 *out) {
+    const int n = W * H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = i % W, y = i / W;
+        const int q = lab[i], q0 = q % Q0, q1 = q / Q0;
+        const int xs = x + vmin0 + q0, ys = y + vmin1 + q1;
+        int c = cmax;
+        if (xs >= 0 && xs < W && ys >= 0 && ys < H) {
+            const int d = abs((int)I1[(size_t)ys * pitch + xs] - (int)I0[(size_t)y * pitch + x]);
+            c = min(l2 == 1 ? d : d * d, cmax);
+        }
+        __nv_bfloat16 *o = out + (size_t)i * 5;
+        o[0] = f2bf(I0[(size_t)y * pitch + x] / 255.f);
+        o[1] = f2bf(I1[(size_t)y * pitch + x] / 255.f);
+        o[2] = f2bf(((float)q0 - 0.5f * (Q0 - 1)) / scale);
+        o[3] = f2bf(((float)q1 - 0.5f * (Q1 - 1)) / scale);
+        o[4] = f2bf((float)c / (float)cmax);
+    }
+}
+
+// Centres as a correction of a base labeling: base coordinates plus the
+// network output (label units), rounded and clamped into the label space.
+__global__ void net_centres_base(const float *out, const int *base, int n, int Q0, int Q1, int *centre) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b0 = base[i] % Q0, b1 = base[i] / Q0;
+        const int c0 = b0 + (int)roundf(out[2 * i]);
+        const int c1 = b1 + (int)roundf(out[2 * i + 1]);
+        centre[2 * i] = min(max(c0, 0), Q0 - 1);
+        centre[2 * i + 1] = min(max(c1, 0), Q1 - 1);
+    }
+}
+
+// Training targets: label coordinates minus those of the base labeling, or
+// centred on the space's middle without one (label units).
+__global__ void net_targets(const int *lab, const int *base, int n, int Q0, int Q1, float *t) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float b0 = base ? (float)(base[i] % Q0) : 0.5f * (Q0 - 1);
+        const float b1 = base ? (float)(base[i] / Q0) : 0.5f * (Q1 - 1);
+        t[2 * i] = (float)(lab[i] % Q0) - b0;
+        t[2 * i + 1] = (float)(lab[i] / Q0) - b1;
+    }
+}
+
 // Winner-take-all over the full label space straight from the images (no
 // cost volume): lowest-index minimum of Eq. Cost_value per pixel, summed over
 // a (2 radius + 1)^2 window of pixels around it (radius 0: the plain cost),
@@ -390,6 +466,29 @@ int net_features_launch(const uint8_t *I0, const uint8_t *I1, const int *wta_q, 
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
+int pyr_down2_launch(const uint8_t *I, int W, int H, int pitch, uint8_t *out, cudaStream_t st) {
+    pyr_down2<<<152 * 4, 256, 0, st>>>(I, W, H, pitch, out, (W + 1) / 2, (H + 1) / 2);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+int labels_up2_launch(const int *lc, int Wc, int Hc, int Qc0, int vminc0, int vminc1, int W, int H, int Q0, int Q1,
+                      int vmin0, int vmin1, int *out, cudaStream_t st) {
+    labels_up2<<<152 * 4, 256, 0, st>>>(lc, Wc, Hc, Qc0, vminc0, vminc1, W, H, Q0, Q1, vmin0, vmin1, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+int net_features_lab_launch(const uint8_t *I0, const uint8_t *I1, const int *lab, int W, int H, int pitch, int Q0,
+                            int Q1, int vmin0, int vmin1, int l2, int cmax, float scale, void *out, cudaStream_t st) {
+    net_features_lab<<<152 * 4, 256, 0, st>>>(I0, I1, lab, W, H, pitch, Q0, Q1, vmin0, vmin1, l2, cmax, scale,
+                                               reinterpret_cast<__nv_bfloat16 *>(out));
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+int net_centres_base_launch(const float *out, const int *base, int n, int Q0, int Q1, int *centre, cudaStream_t st) {
+    net_centres_base<<<152 * 4, 256, 0, st>>>(out, base, n, Q0, Q1, centre);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+int net_targets_launch(const int *lab, const int *base, int n, int Q0, int Q1, float *t, cudaStream_t st) {
+    net_targets<<<152 * 4, 256, 0, st>>>(lab, base, n, Q0, Q1, t);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
 int net_centres_launch(const float *out, int n, int Q0, int Q1, int *centre, cudaStream_t st) {
     net_centres<<<152 * 4, 256, 0, st>>>(out, n, Q0, Q1, centre);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;

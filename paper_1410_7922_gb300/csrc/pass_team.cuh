@@ -104,6 +104,14 @@ __device__ __forceinline__ void cp16(int *dst, const int *src, int bytes) {
                  "r"(bytes)
                  : "memory");
 }
+// 32-bit shared-memory addressing (the buffers below live in dynamic shared memory)
+__device__ __forceinline__ unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int lds(unsigned a) {
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts(unsigned a, int v) { asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory"); }
 __device__ __forceinline__ void wait_groups(int keep) {
     switch (keep) {
     case 0: cp_async_wait_0(); break;
@@ -196,7 +204,115 @@ __host__ __device__ inline size_t team_ints(int Qm, int R, int nbuf, int kmb) {
 
 // One row band of one scan pass.  Every thread of the block calls it with the
 // same band; returns false when the pass was aborted (a wait timed out).
-template <int EM>
+// ---- lean form: one lane owns one whole line (L labels) of one vector ----
+
+// Backward sweep into b, forward sweep combined with it and the clip cl
+// (Eq. L_dec3, Eq. L_dec5 over a whole line held by one lane): h <- min(fwd,
+// bwd, cl).  Returns the line minimum of the input.
+template <int L>
+__device__ __forceinline__ int lean_dt(int (&h)[L], int lam, int cl_add, bool per_axis, int cl_fixed) {
+    int b[L];
+    int lmin = h[L - 1], sw = h[L - 1];
+    b[L - 1] = sw;
+#pragma unroll
+    for (int i = L - 2; i >= 0; --i) {
+        lmin = min(lmin, h[i]);
+        sw = min(h[i], sw + lam);
+        b[i] = sw;
+    }
+    const int cl = per_axis ? lmin + cl_add : cl_fixed;
+    int f = h[0];
+    h[0] = min(b[0], cl);
+#pragma unroll
+    for (int i = 1; i < L; ++i) {
+        f = min(h[i], f + lam);
+        h[i] = min(min(f, b[i]), cl);
+    }
+    return lmin;
+}
+
+// Phase 0 of one line of axis 0 (contiguous labels q0 .. q0 + L - 1): the
+// halved sums of Eq. DP_2D_base for vector `vsel` from the staged inputs,
+// the final-pass argmin key (vector a lanes), the sweeps; result into X.
+template <int L>
+__device__ __forceinline__ int lean_phase0(unsigned aC, unsigned aCc, unsigned aCd, unsigned aMa, unsigned aMb,
+                                           unsigned aX, int q0, int vsel, bool final_a, bool per_axis, int lam,
+                                           int capv, unsigned long long &key) {
+    const unsigned o = 4u * (unsigned)q0;
+    int h[L];
+    if (final_a) {
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            const int c = team::lds(aCc + o + 4 * i), d = team::lds(aCd + o + 4 * i);
+            const int t = team::lds(aC + o + 4 * i) + team::lds(aMa + o + 4 * i) + team::lds(aMb + o + 4 * i);
+            const int so = t + c + d;
+            key = min(key, ((unsigned long long)((unsigned)so ^ 0x80000000u) << 32) | (unsigned)(q0 + i));
+            h[i] = floor_half(t + d - c);
+        }
+    } else {
+        const int sgn = vsel ? -1 : 1;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            const int e = team::lds(aCd + o + 4 * i) - team::lds(aCc + o + 4 * i);
+            h[i] = floor_half(team::lds(aC + o + 4 * i) + team::lds(aMa + o + 4 * i) + team::lds(aMb + o + 4 * i) +
+                              sgn * e);
+        }
+    }
+    const int lmin = lean_dt<L>(h, lam, capv, per_axis, kBig);
+#pragma unroll
+    for (int i = 0; i < L; ++i) team::sts(aX + o + 4 * i, h[i]);
+    return lmin;
+}
+
+// Phase r >= 1 of one line (first label qb, neighbour stride st): sweeps of
+// the values in X, clip; result back into X or, on the last axis, out as
+// the messages.
+struct LeanOut {
+    unsigned aMa, aBox;    // shared: m_a of the next column, mailbox slot of the next row (0: none)
+    int *pMa, *pMb;        // global M[a], M[b] (null: not written)
+    int2 *pRec;            // record ring slot (null: none)
+    int tag;
+};
+template <int L>
+__device__ __forceinline__ void lean_phase_r(unsigned aX, int qb, int st, bool last, int vsel, bool per_axis, int lam,
+                                             int capv, int gv, const LeanOut &O) {
+    const unsigned o = aX + 4u * (unsigned)qb, st4 = 4u * (unsigned)st;
+    int h[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) h[i] = team::lds(o + i * st4);
+    lean_dt<L>(h, lam, capv, per_axis, last ? gv + capv : kBig);
+    if (!last) {
+#pragma unroll
+        for (int i = 0; i < L; ++i) team::sts(o + i * st4, h[i]);
+    } else if (vsel == 0) {
+        const unsigned om = O.aMa + 4u * (unsigned)qb;
+#pragma unroll
+        for (int i = 0; i < L; ++i) team::sts(om + i * st4, h[i]);
+        if (O.pMa) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) O.pMa[qb + i * st] = h[i];
+        }
+    } else {
+        if (O.aBox) {
+            const unsigned ob = O.aBox + 4u * (unsigned)qb;
+#pragma unroll
+            for (int i = 0; i < L; ++i) team::sts(ob + i * st4, h[i]);
+        } else if (O.pRec) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) team::st_record(O.pRec + qb + i * st, h[i], O.tag);
+        }
+        if (O.pMb) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) O.pMb[qb + i * st] = h[i];
+        }
+    }
+}
+
+// lean line lengths
+__host__ __device__ inline bool lean_length(int L) { return L == 9 || L == 17 || L == 33; }
+
+// EM: labels-per-lane bound (generic form) or line-length bound (LEAN).
+template <int EM, bool LEAN>
 __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int *smem, volatile int *s_abort) {
     using namespace team;
     const int Q = A.Q, Qm = A.Qm, W = A.W, H = A.H, T = A.T, NT = A.NT, R = A.R;
@@ -215,6 +331,12 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
     auto mbox_of = [&](int i) { return ma_of(i) + Qm * (1 + (R >= 2 ? 2 : 0)); };
     auto misc_of = [&](int i) { return mbox_of(i) + (size_t)kmb * Qm; };
     for (int i = tid; i < NT * 32; i += blockDim.x) misc_of(i >> 5)[i & 31] = 0;
+    if (LEAN) {
+        // m_a into the first column and m_b into the image's first row are zero
+        for (int i = tid; i < NT * Qm; i += blockDim.x) ma_of(i / Qm)[i % Qm] = 0;
+        if (band == 0)
+            for (int i = tid; i < kmb * Qm; i += blockDim.x) mbox_of(0)[i] = 0;
+    }
     __syncthreads();
     unsigned long long t_band0 = (A.trace && tid == 0) ? global_ns() : 0;
 
@@ -356,29 +478,126 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             }
             if (sync_or(tm, T, bad || *s_abort)) break;  // barrier 1
 
-            // ---- phase 0: sums, halving, axis-0 sweeps ----
+            // ---- column s: inputs in shared memory, outputs ----
             const int *sb = stg + (size_t)(s % nbuf) * 3 * Qs;
             const int *sC = sb + (int)((((size_t)y * W + (incx ? s : W - 1 - s)) * Q + cshift) & 3);
             const int *sc = sb + Qs, *sd = sb + 2 * Qs;
             const int *mbv = (r > 0) ? mbox + (s % kmb) * Qm : nullptr;
             const bool has_ma = s > 0;
-            int ja = kBig, jb = kBig;                 // joint minima of the halved sums
             unsigned long long key = ~0ull;           // final pass: (S_Omega, q) minimum
             const int x = incx ? s : W - 1 - s;
             const int xn = incx ? x + 1 : x - 1;
             const bool a_out = A.write_a && s + 1 < W;
             const int tag_out = A.tag0 + s / ring;
-            auto emit = [&](int q, int oa, int ob) {
+            int *const pMa = a_out ? Ma + ((size_t)y * W + xn) * Qm : nullptr;
+            int *const pMb = (has_next && A.write_b) ? Mb + ((size_t)y_next * W + x) * Qm : nullptr;
+            int *const pBox = to_mbox ? nx_mbox + (s % kmb) * Qm : nullptr;
+            int2 *const pRec = to_ring ? ll_out + (size_t)(s % ring) * Qm : nullptr;
+            // message into the next column of the row (m_a) and into the next row (m_b)
+            auto emit_a = [&](int q, int oa) {
                 maS[q] = oa;
-                if (a_out) Ma[((size_t)y * W + xn) * Qm + q] = oa;
-                if (has_next) {
-                    if (to_mbox)
-                        nx_mbox[(s % kmb) * Qm + q] = ob;
-                    else
-                        st_record(ll_out + (size_t)(s % ring) * Qm + q, ob, tag_out);
-                    if (A.write_b) Mb[((size_t)y_next * W + x) * Qm + q] = ob;
-                }
+                if (pMa) pMa[q] = oa;
             };
+            auto emit_b = [&](int q, int ob) {
+                if (pBox) pBox[q] = ob;
+                if (pRec) st_record(pRec + q, ob, tag_out);
+                if (pMb) pMb[q] = ob;
+            };
+            auto emit = [&](int q, int oa, int ob) {
+                emit_a(q, oa);
+                emit_b(q, ob);
+            };
+            // warp minimum / argmin into the team's control words, barrier 2,
+            // then the per-column bookkeeping of lane 0
+            auto barrier2 = [&](int ja, int jb) -> bool {
+                ja = __reduce_min_sync(kAllLanes, ja);
+                jb = __reduce_min_sync(kAllLanes, jb);
+                if (A.final_) {
+                    const unsigned hi = __reduce_min_sync(kAllLanes, (unsigned)(key >> 32));
+                    const unsigned lo =
+                        __reduce_min_sync(kAllLanes, (unsigned)(key >> 32) == hi ? (unsigned)key : 0xffffffffu);
+                    key = ((unsigned long long)hi << 32) | lo;
+                }
+                if (lane == 0) {
+                    wmin[2 * wt] = ja;
+                    wmin[2 * wt + 1] = jb;
+                    if (A.final_) wkey[wt] = key;
+                }
+                if (sync_or(tm, T, *s_abort != 0)) return false;  // barrier 2
+                // every lane of the team is done with this column's m_b
+                if (tl == 0) {
+                    if (from_mbox) st_rel_cta(misc + 16, s + 1);
+                    // the consumer's record loads above have returned (their values
+                    // went through shared memory and a barrier) before this store
+                    if (from_ring && ((s & 3) == 3 || s + 1 == W)) st_relaxed_gpu(A.cons + band - 1, (unsigned)(s + 1));
+                    if (A.final_) {
+                        unsigned long long best = wkey[0];
+                        for (int w = 1; w < T; ++w) best = min(best, wkey[w]);
+                        A.labels[(size_t)y * W + x] = (int)(best & 0xffffffffu);
+                    }
+                }
+                return true;
+            };
+            if constexpr (LEAN) {
+            // Lean form (two or more axes): lane lv of vector v (warps
+            // [v*Tv, v*Tv + Tv)) owns whole lines; the backward sweep goes to the
+            // vector's shared buffer X, the forward sweep combines on the way.
+            // m_a (maS) and the first row's m_b (mbox) start zero-filled.
+            const int Tv = T >> 1;
+            const int vsel = wt / Tv;                  // 0: S_a / m_a, 1: S_b / m_b
+            const int lv = (wt - vsel * Tv) * 32 + lane;
+            const int NLV = 32 * Tv;
+            const unsigned aX = saddr(vsel ? tB : tA);
+            const unsigned aC = saddr(sC), aCc = saddr(sc), aCd = saddr(sd);
+            const unsigned aMa = saddr(maS), aMb = saddr(mbox + (s % kmb) * Qm);
+            const int lam = A.lam;
+            const bool final_a = A.final_ && vsel == 0;
+            int vmin = kBig;                           // minimum of this vector's halved sums
+            {
+                const int L = A.ax[0].L, nl = A.ax[0].nlines;
+#pragma unroll 1
+                for (int li = lv; li < nl; li += NLV) {
+                    int lm;
+                    if (L == 33)
+                        lm = lean_phase0<33>(aC, aCc, aCd, aMa, aMb, aX, li * 33, vsel, final_a, per_axis, lam, A.capv, key);
+                    else if (L == 17)
+                        lm = lean_phase0<17>(aC, aCc, aCd, aMa, aMb, aX, li * 17, vsel, final_a, per_axis, lam, A.capv, key);
+                    else
+                        lm = lean_phase0<9>(aC, aCc, aCd, aMa, aMb, aX, li * 9, vsel, final_a, per_axis, lam, A.capv, key);
+                    vmin = min(vmin, lm);
+                }
+            }
+            if (!barrier2(vsel ? kBig : vmin, vsel ? vmin : kBig)) break;
+            {
+                int gv = kBig;
+                if (!per_axis)
+                    for (int w = vsel * Tv; w < vsel * Tv + Tv; ++w) gv = min(gv, wmin[2 * w + vsel]);
+                LeanOut O;
+                O.aMa = aMa;
+                O.aBox = pBox ? saddr(pBox) : 0u;
+                O.pMa = pMa;
+                O.pMb = pMb;
+                O.pRec = pRec;
+                O.tag = tag_out;
+#pragma unroll 1
+                for (int ax = 1; ax < R; ++ax) {
+                    if (ax == 2) sync(tm, T);
+                    const TeamAxis Xr = A.ax[ax];
+                    const bool last = (ax == R - 1);
+#pragma unroll 1
+                    for (int li = lv; li < Xr.nlines; li += NLV) {
+                        const int qb = line_first(Xr, li);
+                        if (Xr.L == 33)
+                            lean_phase_r<33>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
+                        else if (Xr.L == 17)
+                            lean_phase_r<17>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
+                        else
+                            lean_phase_r<9>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
+                    }
+                }
+            }
+            } else {
+            int ja = kBig, jb = kBig;  // joint minima of the halved sums
             {
                 const TeamAxis X = A.ax[0];
                 const int lg = __ffs(X.G) - 1;
@@ -437,32 +656,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                     }
                 }
             }
-            // warp partial minima and argmin keys
-            ja = __reduce_min_sync(kAllLanes, ja);
-            jb = __reduce_min_sync(kAllLanes, jb);
-            if (A.final_) {
-                const unsigned hi = __reduce_min_sync(kAllLanes, (unsigned)(key >> 32));
-                const unsigned lo = __reduce_min_sync(kAllLanes, (unsigned)(key >> 32) == hi ? (unsigned)key : 0xffffffffu);
-                key = ((unsigned long long)hi << 32) | lo;
-            }
-            if (lane == 0) {
-                wmin[2 * wt] = ja;
-                wmin[2 * wt + 1] = jb;
-                if (A.final_) wkey[wt] = key;
-            }
-            if (sync_or(tm, T, *s_abort != 0)) break;  // barrier 2
-            // every lane of the team is done with this column's m_b
-            if (tl == 0) {
-                if (from_mbox) st_rel_cta(misc + 16, s + 1);
-                // the consumer's record loads above have returned (their values
-                // went through shared memory and a barrier) before this store
-                if (from_ring && ((s & 3) == 3 || s + 1 == W)) st_relaxed_gpu(A.cons + band - 1, (unsigned)(s + 1));
-                if (A.final_) {
-                    unsigned long long best = wkey[0];
-                    for (int w = 1; w < T; ++w) best = min(best, wkey[w]);
-                    A.labels[(size_t)y * W + x] = (int)(best & 0xffffffffu);
-                }
-            }
+            if (!barrier2(ja, jb)) break;
             // ---- phases 1 .. R-1: sweeps of the other axes, clip, emit ----
             if (R >= 2) {
                 int ga = kBig, gb = kBig;
@@ -515,6 +709,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                     }
                 }
             }
+            }
             if (to_mbox) {
                 __syncwarp();
                 if (lane == 0) st_rel_cta(produced + wt, s + 1);
@@ -532,13 +727,20 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
     return *s_abort == 0;
 }
 
-// dispatch on the labels-per-lane bound
+// dispatch on the form and its bound
 template <typename F>
-__device__ __forceinline__ bool team_dispatch(int em, F &&f) {
+__device__ __forceinline__ bool team_dispatch(int em, bool lean, F &&f) {
+    if (lean) {
+        switch (em) {
+        case 9: return f(std::integral_constant<int, 9>(), std::true_type());
+        case 17: return f(std::integral_constant<int, 17>(), std::true_type());
+        default: return f(std::integral_constant<int, 33>(), std::true_type());
+        }
+    }
     switch (em) {
-    case 9: return f(std::integral_constant<int, 9>());
-    case 17: return f(std::integral_constant<int, 17>());
-    default: return f(std::integral_constant<int, 33>());
+    case 9: return f(std::integral_constant<int, 9>(), std::false_type());
+    case 17: return f(std::integral_constant<int, 17>(), std::false_type());
+    default: return f(std::integral_constant<int, 33>(), std::false_type());
     }
 }
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libedp.so")
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_RANGE, ERR_TIMEOUT, ERR_CUDA = range(7)
 PRIOR = {"joint": 0, "per_axis": 1}
 COST = {"pair": 0, "pair_stereo3": 1, "composite": 2}
-OP_SCANLINE_DP, OP_SOLVE, OP_SOLVE_IMAGES = 1, 2, 3
+OP_SCANLINE_DP, OP_SOLVE, OP_SOLVE_IMAGES, OP_COARSE = 1, 2, 3, 4
 
 
 class EdpError(RuntimeError):
@@ -80,6 +80,10 @@ def load() -> ctypes.CDLL:
         "edp_cost_window": ([P, P, P, I, I, I, LS, PR, P, I, P, P], I),
         "edp_solve_windowed": ([P, P, I, I, I, LS, PR, P, P, SZ, P], I),
         "edp_wta": ([P, P, I, I, I, LS, PR, I, P, P, P], I),
+        "edp_coarse_labels": ([P, P, I, I, I, LS, PR, P, P, SZ, P], I),
+        "edp_net_features_labels": ([P, P, P, I, I, I, LS, PR, ctypes.c_float, P, P], I),
+        "edp_net_centres_residual": ([P, P, I, LS, P, P], I),
+        "edp_net_targets": ([P, P, I, LS, P, P], I),
         "edp_net_param_count": ([], ctypes.c_longlong),
         "edp_net_workspace_size": ([I, I, I], SZ),
         "edp_net_forward": ([P, P, I, I, I, P, P, SZ, P], I),
@@ -105,7 +109,8 @@ def exported_symbols() -> list[str]:
             "edp_solve_images_host", "edp_get_device_status", "edp_batch_workspace_size",
             "edp_solve_batched", "edp_workspace_size_windowed", "edp_cost_window", "edp_solve_windowed",
             "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_forward", "edp_net_backward",
-            "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc"]
+            "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc", "edp_coarse_labels",
+            "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets"]
 
 
 def status_string(code: int) -> str:
@@ -171,11 +176,13 @@ def version() -> int:
     return load().edp_version()
 
 
-def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0, general_kernel: bool = False,
+def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0, general_kernel: int = 0,
                warps_per_row: int = 0) -> None:
-    """Launch shape of the DP kernels (0 = automatic); results never depend on it."""
+    """Launch shape of the DP kernels (0 = automatic); results never depend on it.
+    general_kernel: 1 = one-axis spaces take the multi-axis kernel, 2 = and
+    multi-axis spaces its lane-group form."""
     _check(load().edp_set_tuning(int(rows_per_block), int(labels_per_lane), int(warps_per_row),
-                                 int(bool(general_kernel))), "set_tuning")
+                                 int(general_kernel)), "set_tuning")
 
 
 _prof_keep = None
@@ -479,6 +486,65 @@ def net_features(I0, I1, wta_labels, wta_cost, space: dict, scale: float, cmax: 
                                  W, H, ctypes.byref(ls), float(scale), float(cmax), _dev(out, torch.bfloat16, "x"),
                                  _stream(stream))
     _check(rc, "net_features")
+    return out
+
+
+def coarse_labels(I0, I1, space: dict, prior: dict, l2: int, cmax: int, cost_mode: str = "pair", iters: int = 1,
+                  ws=None, labels=None, stream=None):
+    """edp_coarse_labels: full-resolution labels (int32 [H][W]) from EDP on the
+    halved images and label space."""
+    H, W = I0.shape
+    pr = params(prior, iters=iters, l2=l2, cmax=cmax, cost_mode=cost_mode)
+    ls = label_space(space)
+    if ws is None:
+        ws = workspace(OP_COARSE, W, H, space, prior, iters, device=I0.device, l2=l2, cmax=cmax, cost_mode=cost_mode)
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=I0.device)
+    rc = load().edp_coarse_labels(_dev(I0, torch.uint8, "I0"), _dev(I1, torch.uint8, "I1"), W, H, I0.stride(0),
+                                  ctypes.byref(ls), ctypes.byref(pr), _dev(labels, torch.int32, "labels"),
+                                  _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(rc, "coarse_labels")
+    return labels
+
+
+def net_features_labels(I0, I1, labels, space: dict, l2: int, cmax: int, scale: float, out=None, stream=None):
+    """edp_net_features_labels: bf16 [H][W][5] from a labeling."""
+    H, W = I0.shape
+    if out is None:
+        out = torch.empty((H, W, 5), dtype=torch.bfloat16, device=I0.device)
+    ls = label_space(space)
+    pr = params({"lam": 0, "g": 1}, l2=l2, cmax=cmax)
+    rc = load().edp_net_features_labels(_dev(I0, torch.uint8, "I0"), _dev(I1, torch.uint8, "I1"),
+                                        _dev(labels, torch.int32, "labels"), W, H, I0.stride(0), ctypes.byref(ls),
+                                        ctypes.byref(pr), float(scale), _dev(out, torch.bfloat16, "x"),
+                                        _stream(stream))
+    _check(rc, "net_features_labels")
+    return out
+
+
+def net_centres_residual(out, base, space: dict, centre=None, stream=None):
+    """edp_net_centres_residual: int32 [..][2] centres = base label + network output."""
+    n = out.numel() // 2
+    if centre is None:
+        centre = torch.empty(out.shape[:-1] + (2,), dtype=torch.int32, device=out.device)
+    ls = label_space(space)
+    rc = load().edp_net_centres_residual(_dev(out, torch.float32, "out"), _dev(base, torch.int32, "base"), n,
+                                         ctypes.byref(ls), _dev(centre, torch.int32, "centre"), _stream(stream))
+    _check(rc, "net_centres_residual")
+    return centre
+
+
+def net_targets(labels, space: dict, base=None, out=None, stream=None):
+    """edp_net_targets: float [..][2] label coordinates minus the base's (or
+    minus the space's middle without a base)."""
+    n = labels.numel()
+    if out is None:
+        out = torch.empty(tuple(labels.shape) + (2,), dtype=torch.float32, device=labels.device)
+    ls = label_space(space)
+    bp = _dev(base, torch.int32, "base") if base is not None else None
+    rc = load().edp_net_targets(_dev(labels, torch.int32, "labels"), bp, n, ctypes.byref(ls),
+                                _dev(out, torch.float32, "target"), _stream(stream))
+    _check(rc, "net_targets")
     return out
 
 

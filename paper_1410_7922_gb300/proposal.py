@@ -1,18 +1,23 @@
 """Learned proposal + windowed EDP (two-axis motion label spaces).
 
 Pipeline, every arithmetic step in libedp.so:
-  1. winner-take-all over the full label space (edp_wta) and the network
-     features (edp_net_features);
-  2. the proposal network predicts each pixel's label centre
-     (edp_net_forward, edp_net_centres);
-  3. EDP runs on a win x win label box around that centre
-     (edp_cost_window, edp_solve_windowed);
+  1. a coarse labeling: full EDP on the 2x2-averaged images over the label
+     space with halved offsets, doubled back to full resolution
+     (edp_coarse_labels);
+  2. the proposal network reads the frames and that labeling
+     (edp_net_features_labels) and predicts a correction of it, in label
+     units (edp_net_forward); centre = coarse label + rounded correction
+     (edp_net_centres_residual);
+  3. EDP runs on a win x win label box around each centre
+     (edp_cost_window, edp_solve_windowed), optionally re-centred on its own
+     result for more rounds;
   4. the energy of the result is evaluated on the full label space
      (edp_cost_volume, edp_energy): full-label EDP is the reference the gap is
-     measured against.
+     measured against, and the fallback.
 Training targets are labelings that full-label EDP (edp_solve_images)
-produces on synthetic pairs; training is Adam on the smooth-L1 loss with the
-project's forward/backward kernels.  torch only holds device memory.
+produces on synthetic pairs, as corrections of the coarse labeling
+(edp_net_targets); training is Adam on the smooth-L1 loss with the project's
+forward/backward kernels.  torch only holds device memory.
 """
 from __future__ import annotations
 
@@ -24,7 +29,6 @@ import torch
 from . import edp, synth
 
 FLOW_SCALE = 16.0
-WTA_RADIUS = 3  # winner-take-all feature on costs summed over 7x7 pixels
 
 
 def pair(pair_id: int, W: int, H: int, vmax: int = 32) -> dict:
@@ -35,19 +39,14 @@ def to_device(w: dict) -> tuple[torch.Tensor, torch.Tensor]:
     return torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
 
 
-def features(I0, I1, w: dict, radius: int = WTA_RADIUS) -> torch.Tensor:
-    lab, cost = edp.wta(I0, I1, w["space"], w["l2"], w["cmax"], radius=radius)
-    area = (2 * radius + 1) ** 2
-    return edp.net_features(I0, I1, lab, cost, w["space"], FLOW_SCALE, float(w["cmax"] * area))
+def coarse(I0, I1, w: dict, ws=None, iters: int = 1) -> torch.Tensor:
+    """Coarse-level labeling in the full label space (int32 [H][W])."""
+    return edp.coarse_labels(I0, I1, w["space"], w["prior"], w["l2"], w["cmax"], iters=iters, ws=ws)
 
 
-def targets(labels: torch.Tensor, space: dict) -> torch.Tensor:
-    """Label coordinates of a labeling, centred on the space's middle (the
-    network's output convention)."""
-    Q0, Q1 = space["Q"][0], space["Q"][1]
-    q0 = (labels % Q0).float() - 0.5 * (Q0 - 1)
-    q1 = torch.div(labels, Q0, rounding_mode="floor").float() - 0.5 * (Q1 - 1)
-    return torch.stack([q0, q1], dim=-1).contiguous()
+def features(I0, I1, w: dict, base: torch.Tensor) -> torch.Tensor:
+    """Network input bf16 [H][W][5] from the frames and the coarse labeling."""
+    return edp.net_features_labels(I0, I1, base, w["space"], w["l2"], w["cmax"], FLOW_SCALE)
 
 
 def full_edp(I0, I1, w: dict, iters: int = 1, ws=None):
@@ -69,19 +68,41 @@ def init_params(seed: int = 0) -> torch.Tensor:
     return p
 
 
-def build_training_set(n_pairs: int, W: int, H: int, first_pair: int = 0, iters: int = 1, vmax: int = 32):
-    """Features and full-label EDP targets of n_pairs synthetic pairs."""
+def build_training_set(n_pairs: int, W: int, H: int, first_pair: int = 0, iters: int = 1, vmax: int = 32,
+                       pool=None):
+    """Network inputs (bf16 [P][H][W][5]), targets (float32 [P][H][W][2]:
+    full-label EDP labels as corrections of the coarse labeling) and the
+    coarse labelings of n_pairs synthetic pairs.  `pool`: an optional
+    process pool (spawn) that synthesises the pairs."""
+    ids = [first_pair + k for k in range(n_pairs)]
+    gen = pool.imap(_pair_images, [(i, W, H, vmax) for i in ids], chunksize=4) if pool else (
+        _pair_images((i, W, H, vmax)) for i in ids)
     xs, ts = [], []
-    ws = None
-    for k in range(n_pairs):
-        w = pair(first_pair + k, W, H, vmax)
-        I0, I1 = to_device(w)
+    ws = wsc = None
+    for pid, (I0n, I1n) in zip(ids, gen):
+        w = pair_meta(W, H, vmax)
+        I0, I1 = torch.from_numpy(I0n).cuda(), torch.from_numpy(I1n).cuda()
         if ws is None:
             ws = edp.workspace(edp.OP_SOLVE_IMAGES, W, H, w["space"], w["prior"], iters)
+            wsc = edp.workspace(edp.OP_COARSE, W, H, w["space"], w["prior"], iters, l2=w["l2"], cmax=w["cmax"])
         lab, _ = full_edp(I0, I1, w, iters, ws)
-        xs.append(features(I0, I1, w))
-        ts.append(targets(lab, w["space"]))
+        base = coarse(I0, I1, w, wsc, iters)
+        xs.append(features(I0, I1, w, base))
+        ts.append(edp.net_targets(lab, w["space"], base=base))
     return torch.stack(xs).contiguous(), torch.stack(ts).contiguous()
+
+
+def _pair_images(args):
+    pid, W, H, vmax = args
+    w = pair(pid, W, H, vmax)
+    return w["I0"], w["I1"]
+
+
+def pair_meta(W: int, H: int, vmax: int = 32) -> dict:
+    """Label space, prior and cost parameters of the motion pairs (no images)."""
+    Q = 2 * vmax + 1
+    return {"space": synth.space_motion(Q), "prior": {"lam": 15, "g": 3, "l1": 1, "mode": "per_axis"},
+            "l2": 1, "cmax": 20, "cost_mode": "pair", "W": W, "H": H}
 
 
 def train(x: torch.Tensor, t: torch.Tensor, epochs: int = 30, batch: int = 8, lr: float = 2e-3, seed: int = 0,
@@ -116,21 +137,14 @@ def train(x: torch.Tensor, t: torch.Tensor, epochs: int = 30, batch: int = 8, lr
     return P, losses
 
 
-def propose(P: torch.Tensor, I0, I1, w: dict) -> torch.Tensor:
-    """Box centres int32 [H][W][2] from the trained network."""
-    x = features(I0, I1, w)[None].contiguous()
+def propose(P: torch.Tensor, I0, I1, w: dict, base: torch.Tensor | None = None, ws=None) -> torch.Tensor:
+    """Box centres int32 [H][W][2]: coarse labeling + the network's correction."""
+    if base is None:
+        base = coarse(I0, I1, w, ws)
+    x = features(I0, I1, w, base)[None].contiguous()
     H, W = I0.shape
-    ws = edp.net_workspace(1, H, W)
-    out = edp.net_forward(P, x, ws)
-    return edp.net_centres(out[0].contiguous(), w["space"])
-
-
-def wta_centres(I0, I1, w: dict, radius: int = WTA_RADIUS) -> torch.Tensor:
-    """Centres straight from (window-aggregated) winner-take-all: the
-    proposal without a network."""
-    lab, _ = edp.wta(I0, I1, w["space"], w["l2"], w["cmax"], radius=radius)
-    Q0 = w["space"]["Q"][0]
-    return torch.stack([lab % Q0, torch.div(lab, Q0, rounding_mode="floor")], dim=-1).int().contiguous()
+    out = edp.net_forward(P, x, edp.net_workspace(1, H, W))
+    return edp.net_centres_residual(out[0].contiguous(), base, w["space"])
 
 
 def windowed_edp(I0, I1, w: dict, centre: torch.Tensor, win: int = 9, iters: int = 1, ws=None):
@@ -140,8 +154,8 @@ def windowed_edp(I0, I1, w: dict, centre: torch.Tensor, win: int = 9, iters: int
 
 def label_centres(labels: torch.Tensor, space: dict) -> torch.Tensor:
     """Label coordinates of a labeling as box centres int32 [H][W][2]."""
-    Q0 = space["Q"][0]
-    return torch.stack([labels % Q0, torch.div(labels, Q0, rounding_mode="floor")], dim=-1).int().contiguous()
+    zero = torch.zeros(tuple(labels.shape) + (2,), dtype=torch.float32, device=labels.device)
+    return edp.net_centres_residual(zero, labels, space)
 
 
 def refine(I0, I1, w: dict, centre: torch.Tensor, rounds: int, win: int = 9, iters: int = 1, ws=None):
@@ -154,9 +168,10 @@ def refine(I0, I1, w: dict, centre: torch.Tensor, rounds: int, win: int = 9, ite
 
 
 def evaluate(P: torch.Tensor, pairs: list[int], W: int, H: int, win: int = 9, iters: int = 1, reps: int = 3,
-             vmax: int = 32):
-    """Energy gap and time of (network + windowed EDP) against full-label EDP,
-    and of (WTA centres + windowed EDP), on held-out pairs."""
+             vmax: int = 32, rounds: int = 1):
+    """Energy gap and time against full-label EDP on held-out pairs of
+    (coarse labeling + network + windowed EDP) and of the same path without
+    the network (windows centred on the coarse labeling)."""
     rows = []
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
@@ -174,32 +189,38 @@ def evaluate(P: torch.Tensor, pairs: list[int], W: int, H: int, win: int = 9, it
             best = ms if best is None else min(best, ms)
         return r, best
 
-    ws_full = ws_win = None
+    ws_full = ws_win = ws_c = None
+    net_ws = edp.net_workspace(1, H, W)
     for pid in pairs:
         w = pair(pid, W, H, vmax)
         I0, I1 = to_device(w)
         if ws_full is None:
             ws_full = edp.workspace(edp.OP_SOLVE_IMAGES, W, H, w["space"], w["prior"], iters)
             ws_win = edp.workspace_windowed(W, H, w["space"], w["prior"], win, iters)
+            ws_c = edp.workspace(edp.OP_COARSE, W, H, w["space"], w["prior"], iters, l2=w["l2"], cmax=w["cmax"])
         (lab_f, e_f), ms_full = timed(lambda: full_edp(I0, I1, w, iters, ws_full))
         e_full = int(e_f[3].item())
         C = edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"])
 
         def net_path():
-            c = propose(P, I0, I1, w)
-            return windowed_edp(I0, I1, w, c, win, iters, ws_win)
+            base = coarse(I0, I1, w, ws_c, iters)
+            x = features(I0, I1, w, base)[None].contiguous()
+            out = edp.net_forward(P, x, net_ws)
+            c = edp.net_centres_residual(out[0].contiguous(), base, w["space"])
+            return refine(I0, I1, w, c, rounds, win, iters, ws_win)
 
-        def wta_path():
-            c = wta_centres(I0, I1, w)
-            return windowed_edp(I0, I1, w, c, win, iters, ws_win)
+        def coarse_path():
+            base = coarse(I0, I1, w, ws_c, iters)
+            return refine(I0, I1, w, label_centres(base, w["space"]), rounds, win, iters, ws_win)
 
         lab_n, ms_net = timed(net_path)
-        lab_w, ms_wta = timed(wta_path)
+        lab_c, ms_coarse = timed(coarse_path)
         e_net = int(edp.energy(C, lab_n, w["space"], w["prior"])[3].item())
-        e_wta = int(edp.energy(C, lab_w, w["space"], w["prior"])[3].item())
+        e_coarse = int(edp.energy(C, lab_c, w["space"], w["prior"])[3].item())
         del C
-        rows.append({"pair": pid, "E_full": e_full, "E_net": e_net, "E_wta": e_wta,
-                     "gap_net": (e_net - e_full) / e_full, "gap_wta": (e_wta - e_full) / e_full,
-                     "ms_full": ms_full, "ms_net": ms_net, "ms_wta": ms_wta,
-                     "label_agree_net": float((lab_n == lab_f).float().mean().item())})
+        rows.append({"pair": pid, "E_full": e_full, "E_net": e_net, "E_coarse": e_coarse,
+                     "gap_net": (e_net - e_full) / e_full, "gap_coarse": (e_coarse - e_full) / e_full,
+                     "ms_full": ms_full, "ms_net": ms_net, "ms_coarse": ms_coarse,
+                     "label_agree_net": float((lab_n == lab_f).float().mean().item()),
+                     "label_agree_coarse": float((lab_c == lab_f).float().mean().item())})
     return rows

@@ -103,6 +103,43 @@ def test_wta_and_features(edp_lib):
     assert c.tolist() == [[[32, 31], [64, 0]]]
 
 
+@pytest.mark.parametrize("W,H,vmax", [(24, 20, 4), (23, 17, 3)])
+def test_coarse_labels(edp_lib, W, H, vmax):
+    """edp_coarse_labels = 2x2 pyramid, EDP on the halved label space,
+    labels doubled back to full resolution (odd sizes included)."""
+    w = synth.workload_motion_640x480(pair=3, W=W, H=H, vmax=vmax)
+    space, prior = w["space"], w["prior"]
+    h0, h1 = rnet.pyr_down2(w["I0"]), rnet.pyr_down2(w["I1"])
+    vc, qc = rnet.halved_space(space["vmin"][:2], space["Q"][:2])
+    sc = {"R": 2, "Q": (qc[0], qc[1], 1), "vmin": (vc[0], vc[1], 0), "step": (1, 1, 1)}
+    lc = oracle.edp(oracle.cost_volume(h0, h1, None, sc, w["l2"], w["cmax"]), sc, prior, iters=1, tier=1)
+    want = rnet.labels_up2(lc, vc, qc, space["vmin"][:2], space["Q"][:2], H, W)
+    I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
+    got = edp_lib.coarse_labels(I0, I1, space, prior, w["l2"], w["cmax"]).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+def test_features_labels_targets_residual_centres(edp_lib):
+    w = synth.workload_motion_640x480(pair=4, W=37, H=29, vmax=6)
+    space = w["space"]
+    Q = space["Q"][:2]
+    rng = np.random.default_rng(5)
+    lab = rng.integers(0, Q[0] * Q[1], size=(29, 37)).astype(np.int32)
+    base = rng.integers(0, Q[0] * Q[1], size=(29, 37)).astype(np.int32)
+    I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
+    x = edp_lib.net_features_labels(I0, I1, torch.from_numpy(lab).cuda(), space, w["l2"], w["cmax"], 16.0)
+    want = rnet.features_from_labels(w["I0"], w["I1"], lab, space["vmin"][:2], Q, w["l2"], w["cmax"], 16.0)
+    assert np.allclose(x.float().cpu().numpy().transpose(2, 0, 1), rnet.bf16(want), rtol=8e-3, atol=1e-7)
+    t = edp_lib.net_targets(torch.from_numpy(lab).cuda(), space, base=torch.from_numpy(base).cuda())
+    assert np.array_equal(t.cpu().numpy(), rnet.targets(lab, Q, base))
+    t0 = edp_lib.net_targets(torch.from_numpy(lab).cuda(), space)
+    assert np.array_equal(t0.cpu().numpy(), rnet.targets(lab, Q))
+    out = (rng.standard_normal((29, 37, 2)) * 3).astype(np.float32)
+    out[0, :4, 0] = [0.5, -0.5, 1.5, -2.5]  # ties round away from zero
+    c = edp_lib.net_centres_residual(torch.from_numpy(out).cuda(), torch.from_numpy(base).cuda(), space)
+    assert np.array_equal(c.cpu().numpy(), rnet.centres_residual(out.astype(np.float64), base, Q))
+
+
 def test_net_training_lowers_loss(edp_lib):
     rng = np.random.default_rng(9)
     N, H, W = 4, 32, 32

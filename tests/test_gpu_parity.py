@@ -133,7 +133,8 @@ def run_edp(edp_lib, C, space, prior, iters):
 
 @pytest.mark.parametrize("Q,mode", [((7,), "joint"), ((64,), "joint"), ((33,), "joint"), ((130,), "joint"),
                                     ((5, 4), "per_axis"), ((5, 4), "joint"), ((9, 9), "per_axis"),
-                                    ((33, 33), "per_axis"), ((33, 33), "joint"), ((3, 4, 3), "joint"),
+                                    ((33, 33), "per_axis"), ((33, 33), "joint"), ((17, 9), "per_axis"),
+                                    ((17, 17, 9), "joint"), ((9, 9, 9), "per_axis"), ((3, 4, 3), "joint"),
                                     ((5, 5, 3), "per_axis"), ((1,), "joint")])
 @pytest.mark.parametrize("iters", [1, 2])
 def test_edp_random(edp_lib, Q, mode, iters):
@@ -159,6 +160,21 @@ def test_edp_degenerate_shapes(edp_lib, W, H, general):
         assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 50), (50, 3)])
+@pytest.mark.parametrize("form", [0, 2])
+def test_edp_degenerate_shapes_two_axes(edp_lib, W, H, form):
+    """Image shapes at the edges of the wavefront, both forms of the
+    multi-axis kernel."""
+    rng = np.random.default_rng(W * 1000 + H)
+    C = rng.integers(0, 20, size=(H, W, 12)).astype(np.int32)
+    for mode in ("joint", "per_axis"):
+        prior = {"lam": 4, "g": 2, "l1": 1, "mode": mode}
+        edp_lib.set_tuning(0, 0, form)
+        for iters in (1, 3):
+            want, got = run_edp(edp_lib, C, sp((4, 3)), prior, iters)
+            assert np.array_equal(got, want), (mode, iters)
+
+
 @pytest.mark.parametrize("Q", [1, 5, 16, 31, 32, 33, 64, 100, 129, 256])
 @pytest.mark.parametrize("g", [1, 2, 4, 9, 300])
 def test_edp_one_axis_kernel(edp_lib, Q, g):
@@ -182,10 +198,12 @@ def test_edp_one_axis_rows_per_block(edp_lib, rows):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("rb,t", [(1, 1), (2, 2), (3, 4), (6, 3), (4, 8), (1, 12), (15, 1)])
-def test_edp_launch_shapes(edp_lib, rb, t):
+def test_edp_launch_shapes(edp_lib, rb, t, form):
     """Results never depend on the launch shape of the multi-axis kernel
-    (rows per block, warps per row)."""
+    (rows per block, warps per row) nor on its form (whole lines per lane /
+    lane groups)."""
     rng = np.random.default_rng(rb * 31 + t)
     for Q, mode in (((24,), "joint"), ((7, 6), "per_axis"), ((7, 6), "joint"), ((33, 33), "joint"),
                     ((5, 4, 3), "per_axis")):
@@ -194,9 +212,9 @@ def test_edp_launch_shapes(edp_lib, rb, t):
         C = rng.integers(0, 21, size=(H, W, n)).astype(np.int32)
         prior = {"lam": 6, "g": 3, "l1": 1, "mode": mode}
         want = oracle.edp(C, sp(Q), prior, iters=2, tier=1)
-        edp_lib.set_tuning(rb, 0, True, warps_per_row=t)
+        edp_lib.set_tuning(rb, 0, form, warps_per_row=t)
         got = host(edp_lib.solve(dev(C), sp(Q), prior, iters=2))
-        assert np.array_equal(got, want), (Q, mode, rb, t)
+        assert np.array_equal(got, want), (Q, mode, rb, t, form)
 
 
 def test_edp_stereo_450x375_full_size(edp_lib):

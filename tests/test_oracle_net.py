@@ -70,3 +70,52 @@ def test_smooth_l1_closed_form():
     loss, g = net.smooth_l1(out, tgt)
     assert loss == pytest.approx((0 + 0.125 + 2.5 + 1.5) / 4)
     assert np.allclose(g, np.array([0.0, 0.5, 1.0, -1.0]) / 4)
+
+
+# --------------------------------------------------------------------------
+# coarse-level proposal inputs: hand-worked cases
+# --------------------------------------------------------------------------
+
+def test_pyr_down2_hand_worked():
+    I = np.arange(9, dtype=np.uint8).reshape(3, 3)
+    # (0+1+3+4+2)//4 = 2; odd edge repeats: (2+2+5+5+2)//4 = 4, (6+7+6+7+2)//4 = 7, (4*8+2)//4 = 8
+    assert net.pyr_down2(I).tolist() == [[2, 4], [7, 8]]
+    # rounding half up: 1+1+1+2 = 5 -> (5+2)//4 = 1; 1+2+2+2 = 7 -> 2
+    assert net.pyr_down2(np.array([[1, 1], [1, 2]], dtype=np.uint8)).tolist() == [[1]]
+    assert net.pyr_down2(np.array([[1, 2], [2, 2]], dtype=np.uint8)).tolist() == [[2]]
+
+
+def test_halved_space():
+    assert net.halved_space((-32, -32), (65, 65)) == ((-16, -16), (33, 33))
+    # offsets -3..2 -> -1..1; offsets 0..4 -> 0..2
+    assert net.halved_space((-3, 0), (6, 5)) == ((-1, 0), (3, 3))
+
+
+def test_labels_up2_hand_worked():
+    # coarse space offsets -1..1 per axis; label 2 = offset (1, -1)
+    lc = np.array([[2]])
+    up = net.labels_up2(lc, (-1, -1), (3, 3), (-2, -2), (5, 5), 2, 3)
+    # doubled offset (2, -2) -> label (4, 0) = 4 everywhere
+    assert up.tolist() == [[4, 4, 4], [4, 4, 4]]
+    # clamped into a smaller space: offsets -1..1 -> label (2, 0)
+    assert net.labels_up2(lc, (-1, -1), (3, 3), (-1, -1), (3, 3), 1, 1).tolist() == [[2]]
+
+
+def test_features_from_labels_hand_worked():
+    I0 = np.array([[10, 20]], dtype=np.uint8)
+    I1 = np.array([[30, 40]], dtype=np.uint8)
+    lab = np.array([[5, 5]])  # (q0, q1) = (2, 1): offset (+1, 0) in vmin (-1, -1)
+    f = net.features_from_labels(I0, I1, lab, (-1, -1), (3, 3), 1, 50, 2.0)
+    assert f[:, 0, 0].tolist() == pytest.approx([10 / 255, 30 / 255, 0.5, 0.0, 30 / 50])
+    assert f[4, 0, 1] == 1.0  # x + 1 leaves the image: cmax
+
+
+def test_targets_and_residual_centres():
+    Q = (5, 4)
+    lab = np.array([7])            # (2, 1)
+    base = np.array([5])           # (0, 1)
+    assert net.targets(lab, Q, base).tolist() == [[2.0, 0.0]]
+    assert net.targets(lab, Q).tolist() == [[0.0, -0.5]]
+    out = np.array([[0.5, -0.5], [1.49, -2.6], [9.0, 9.0]])
+    b = np.array([6, 6, 6])        # (1, 1)
+    assert net.centres_residual(out, b, Q).tolist() == [[2, 0], [2, 0], [4, 3]]
