@@ -1,12 +1,15 @@
 #!/usr/bin/env python
-"""Benchmark: EDP pixel-label updates/s on the 450x375 stereo workload.
+"""Benchmark: EDP pixel-label updates/s.
 
-One step = the whole hot path over one synthetic stereo pair (450x375, 64
-labels, truncated-abs cost T = 20, truncated-linear prior lambda = 20, K = 4):
-cost volume, one EDP iteration (four scan passes, Algorithm 1) with the
-marginal/argmin, and the energy -- one call of edp_solve_images.
-Pixel-label updates per step = N * Q * (8 * j + 1): two sums written per
-pass, four passes per iteration, plus the marginal.
+One step = the whole hot path over one synthetic pair: cost volume, j EDP
+iterations (four scan passes each, Algorithm 1) with the marginal/argmin, and
+the energy -- one call of edp_solve_images.  Pixel-label updates per step =
+N * Q * (8 * j + 1): two sums written per pass, four passes per iteration,
+plus the marginal.  Workloads (--workload):
+  stereo_edp_450x375_Q64     450x375 stereo, 64 labels, cost min(|IL-IR|, 20),
+                             truncated-linear prior lambda = 20, K = 4 (default);
+  motion_edp_320x240_Q33x33  320x240 motion, 33x33 labels, per-axis lambda = 15, K = 3;
+  motion_edp_640x480_Q65x65  640x480 motion, full 65x65 labels, same prior.
 
 Prints one JSON line (rank 0).  --impl reference runs the CPU oracle on the
 host cores instead (a bounded sample of the same workload).
@@ -28,6 +31,21 @@ sys.path.insert(0, ROOT)
 METRIC = "EDP pixel-label updates/s"
 UNIT = "pixel-label updates/s"
 WORKLOAD = "stereo_edp_450x375_Q64"
+WORKLOADS = ("stereo_edp_450x375_Q64", "motion_edp_320x240_Q33x33", "motion_edp_640x480_Q65x65")
+
+
+def make_workload(name: str, pair: int = 0) -> dict:
+    from paper_1410_7922_gb300 import synth
+    if name == "stereo_edp_450x375_Q64":
+        w = synth.workload_stereo_450x375(pair=pair)
+        w["desc"] = {"prior": "truncated linear, lambda=20, K=4", "cost": "min(|IL-IR|, 20)"}
+    elif name == "motion_edp_320x240_Q33x33":
+        w = synth.workload_motion_320x240(pair=pair)
+        w["desc"] = {"prior": "per-axis truncated linear, lambda=15, K=3", "cost": "min(|I1(x+o)-I0(x)|, 20)"}
+    else:
+        w = synth.workload_motion_640x480(pair=pair)
+        w["desc"] = {"prior": "per-axis truncated linear, lambda=15, K=3", "cost": "min(|I1(x+o)-I0(x)|, 20)"}
+    return w
 PASS_NAMES = ["P1", "P2", "P3", "P4"]
 
 
@@ -38,6 +56,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--iters", type=int, default=1, help="EDP iterations j per step")
     ap.add_argument("--impl", default="edp", choices=["edp", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS)
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--extra", default="", help="comma list of longer side measurements: batched,proposal")
@@ -102,22 +121,29 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {
+    "edp_pass_r1_kernel": ("pass_r1.cuh", "edp_pass_r1.cu", "common.cuh"),
+    "edp_pass_team_kernel": ("pass_team.cuh", "edp_pass_team.cu", "common.cuh"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in ("pass_r1.cuh", "edp_pass_r1.cu", "common.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_1410_7922_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the pass kernel from a committed ncu summary,
-    or None if there is none for the current kernel source."""
+def profiled_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of the pass kernel from a committed ncu summary
+    (profiles/edp_pass_traffic.json: workload -> {kernel, source_hash,
+    dram_bytes_per_launch}), or None if there is none for the current source."""
     p = os.path.join(ROOT, "profiles", "edp_pass_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     e = d.get(workload)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("kernel") != kernel or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return float(e["dram_bytes_per_launch"])
 
@@ -216,32 +242,40 @@ def cpu_oracle_sample(w, iters: int, min_seconds: float = 10.0, max_reps: int = 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    from paper_1410_7922_gb300 import synth
     import oracle
     oracle.build()
-    w = synth.workload_stereo_450x375()
+    w = make_workload(args.workload)
     H, W = w["I0"].shape
-    Q = 64
-    # each step: one full frame through the oracle (about 2 s on one core)
-    def step():
-        C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+    Q = 1
+    for r in range(w["space"]["R"]):
+        Q *= w["space"]["Q"][r]
+
+    def frame(rows):
+        C = oracle.cost_volume(w["I0"][:rows], w["I1"][:rows], None, w["space"], w["l2"], w["cmax"])
         lab = oracle.edp(C, w["space"], w["prior"], iters=args.iters, tier=1)
         oracle.energy(C, lab, w["space"], w["prior"])
+
+    # each step: the first `rows` image rows of the frame, sized to about one
+    # second of oracle work on one host core (the whole frame when it fits)
+    t0 = time.perf_counter()
+    frame(2)
+    t2 = max(time.perf_counter() - t0, 1e-4)
+    rows = max(2, min(H, int(2 * 1.0 / t2)))
     for _ in range(args.warmup):
-        step()
+        frame(rows)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        frame(rows)
     el = time.perf_counter() - t0
-    value = W * H * Q * (8 * args.iters + 1) * args.steps / el
+    value = W * rows * Q * (8 * args.iters + 1) * args.steps / el
+    sample = (f"{W}x{rows} of the {W}x{H} frame per step (top rows), oracle cost volume + EDP (RMS tier) "
+              "+ energy on 1 host core")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "W": W, "H": H, "Q": Q, "iters": args.iters},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one full {W}x{H} frame per step, oracle cost volume + EDP (RMS tier) "
-                                       "+ energy on 1 host core"},
+            "config": {"workload": args.workload, "W": W, "H": H, "Q": Q, "iters": args.iters},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -414,7 +448,7 @@ def run_gpu(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     j = args.iters
-    w = synth.workload_stereo_450x375(pair=rank)  # weak scaling: one pair per rank
+    w = make_workload(args.workload, pair=rank)  # weak scaling: one pair per rank
     H, W = w["I0"].shape
     space, prior = w["space"], w["prior"]
     Q = edp.n_labels(space)
@@ -483,9 +517,10 @@ def run_gpu(args, world, rank, local):
     pass_total_s = sum(pass_ms) * 1e-3 / args.steps
     achieved = nbytes / pass_total_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic(WORKLOAD)
+    kernel = "edp_pass_r1_kernel" if (space["R"] == 1 and Q <= 256) else "edp_pass_team_kernel"
+    traffic = profiled_traffic(args.workload, kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": "edp_pass_r1_kernel",
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
                 "bytes_per_launch_avg": nbytes / npass, "launch_ms_avg": sum(pass_ms) / args.steps / npass,
                 "pass_ms": [p / args.steps for p in pass_ms]}
 
@@ -511,7 +546,7 @@ def run_gpu(args, world, rank, local):
     assert np.array_equal(lab_h.numpy(), labels.cpu().numpy())
 
     rows = None
-    if not args.no_rows and rank == 0:
+    if not args.no_rows and rank == 0 and args.workload == WORKLOAD:
         rows = time_solve_rows(edp, synth, torch)
     extra = {}
     if rank == 0:
@@ -527,8 +562,8 @@ def run_gpu(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "W": W, "H": H, "Q": Q, "iters": j,
-                           "prior": "truncated linear, lambda=20, K=4", "cost": "min(|IL-IR|, 20)",
+                "config": {"workload": args.workload, "W": W, "H": H, "Q": Q, "iters": j,
+                           "prior": w["desc"]["prior"], "cost": w["desc"]["cost"],
                            "l2_cache": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world} (one independent pair per GPU)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -285,10 +285,12 @@ int edp_net_features_labels(const uint8_t *I0, const uint8_t *I1, const int32_t 
                             edp_stream_t stream);
 
 /* Box centres (int32 [n][2]) as a correction of a base labeling: the base
- * label's coordinates plus the rounded network output (label units), clamped
- * into the space.  out: float [n][2]; base: int32 [n]. */
+ * label's coordinates plus the network output (label units) rounded half away
+ * from zero; a correction whose larger component is below min_shift labels
+ * is dropped (0: every correction applies); clamped into the space.
+ * out: float [n][2]; base: int32 [n]. */
 int edp_net_centres_residual(const float *out, const int32_t *base, int n, const edp_label_space *space,
-                             int32_t *centre, edp_stream_t stream);
+                             int min_shift, int32_t *centre, edp_stream_t stream);
 
 /* Training targets (float [n][2], label units) of a labeling: its label
  * coordinates minus those of `base` (int32 [n]), or minus (Q_r - 1)/2 when

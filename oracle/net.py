@@ -229,10 +229,13 @@ def targets(labels: np.ndarray, Q, base: np.ndarray | None = None) -> np.ndarray
     return np.stack([q0 - b0, q1 - b1], axis=-1).astype(np.float64)
 
 
-def centres_residual(out: np.ndarray, base: np.ndarray, Q) -> np.ndarray:
+def centres_residual(out: np.ndarray, base: np.ndarray, Q, min_shift: int = 0) -> np.ndarray:
     """[..][2] int centres: base coordinates + out rounded half away from
-    zero, clamped into the space."""
+    zero (dropped when its larger component is below min_shift), clamped
+    into the space."""
     r = np.where(out >= 0, np.floor(out + 0.5), -np.floor(-out + 0.5)).astype(np.int64)
+    small = np.maximum(np.abs(r[..., 0]), np.abs(r[..., 1])) < min_shift
+    r = np.where(small[..., None], 0, r)
     c0 = np.clip(base % Q[0] + r[..., 0], 0, Q[0] - 1)
     c1 = np.clip(base // Q[0] + r[..., 1], 0, Q[1] - 1)
     return np.stack([c0, c1], axis=-1)

@@ -337,17 +337,22 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         return EDP_OK;
     }
     // multi-axis (team) kernel.  Lean form: two or more axes whose lines hold
-    // 9, 17 or 33 labels, Tv warps per message vector, lanes owning whole lines.
+    // 9, 17 or 33 labels (or all 65), Tv warps per message vector, lanes
+    // owning whole lines.
     TeamShape S;
     bool lean = g.R >= 2 && !g_generic_team;
     int LM = 0, Tv = 0;
+    bool short_lines = true, all65 = true;
     for (int r = 0; r < g.R; ++r) {
         LM = std::max(LM, g.Qr[r]);
-        lean = lean && (g.Qr[r] == 9 || g.Qr[r] == 17 || g.Qr[r] == 33);
+        short_lines = short_lines && (g.Qr[r] == 9 || g.Qr[r] == 17 || g.Qr[r] == 33);
+        all65 = all65 && g.Qr[r] == 65;
     }
+    // 65-label lines: a build of their own (single-problem kernel only)
+    lean = lean && (short_lines || (all65 && !fixed_threads));
     const int tmax = fixed_threads ? std::min(12, fixed_threads / 32) : (lean ? 8 : 12);
     if (lean) {
-        LM = LM <= 9 ? 9 : (LM <= 17 ? 17 : 33);
+        LM = all65 ? 65 : 33;
         int maxlines = 1;
         for (int r = 0; r < g.R; ++r) maxlines = std::max(maxlines, g.Q / g.Qr[r]);
         Tv = g_tune_t > 0 ? std::max(1, g_tune_t / 2) : std::min((maxlines + 31) / 32, 4);
@@ -986,22 +991,6 @@ int edp_solve_batched(const edp_problem *probs, int n, void *ws, size_t ws_bytes
 }
 
 namespace {
-struct WinLayout {
-    size_t counters, ll, msg[4], end;
-};
-WinLayout win_layout(int W, int H, int Qw, int iters) {
-    WinLayout L;
-    L.counters = kHeader;
-    L.ll = align_up(L.counters + 4 * (size_t)iters * 4);
-    size_t off = align_up(L.ll + (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * W * Qw * 8);
-    for (int k = 0; k < 4; ++k) {
-        L.msg[k] = off;
-        off = align_up(off + (size_t)W * H * Qw * 4);
-    }
-    L.end = off;
-    return L;
-}
-
 int check_window(const edp_label_space *space, const edp_params *params, int win, Geometry *g) {
     int rc = check_space(space, g);
     if (rc) return rc;
@@ -1019,7 +1008,7 @@ size_t edp_workspace_size_windowed(int W, int H, const edp_label_space *space, c
     Geometry g;
     if (W < 1 || H < 1 || check_window(space, params, win, &g)) return 0;
     const int Qw = space->R == 2 ? win * win : win;
-    return win_layout(W, H, Qw, std::max(1, params->iters)).end;
+    return solve_layout(W, H, Qw, space->R, std::max(1, params->iters)).end;
 }
 
 int edp_cost_window(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H, int pitch,
@@ -1068,52 +1057,67 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *w = static_cast<unsigned char *>(ws);
     const int Qw = space->R == 2 ? win * win : win;
-    const WinLayout L = win_layout(W, H, Qw, params->iters);
-    WinArgs a;
+    // the multi-axis pass kernel in its windowed form: one warp per row, the
+    // workspace laid out as edp_solve's with Q = Qw
+    const SolveLayout L = solve_layout(W, H, Qw, space->R, params->iters);
+    TeamArgs a;
     memset(&a, 0, sizeof a);
-    a.Cw = Cw;
+    a.C = Cw;
     for (int k = 0; k < 4; ++k) a.M[k] = reinterpret_cast<int *>(w + L.msg[k]);
     a.labels = labels;
     a.ll = reinterpret_cast<int2 *>(w + L.ll);
-    a.centre = centre;
     a.status = reinterpret_cast<int *>(w);
     a.W = W;
     a.H = H;
-    a.Qw = Qw;
-    a.E = (Qw + 31) / 32;
-    a.EMt = a.E <= 1 ? 1 : a.E <= 2 ? 2 : a.E <= 4 ? 4 : 8;
-    a.n = win;
+    a.Q = Qw;
+    a.Qm = L.Qm;
     a.R = space->R;
-    a.Q0 = space->Q[0];
-    a.Q1 = space->Q[1];
     a.lam = params->lambda;
     a.capv = (int)cap_value(params);
     a.mode = params->prior_mode;
-    int NWR = g_tune_rb > 0 ? g_tune_rb : 8;
-    NWR = std::max(kMinRowsR1, std::min(NWR, std::min(16, H)));
-    while (NWR > kMinRowsR1 && pass_win_smem(NWR, a.E) > (size_t)kMaxSmem) --NWR;
-    const size_t smem = pass_win_smem(NWR, a.E);
+    a.T = 1;
+    int NT = g_tune_rb > 0 ? g_tune_rb : 8;
+    NT = std::max(1, std::min(NT, std::min(16, H)));
+    a.nbuf = 3;
+    a.kmb = 4;
+    // (the windowed form always has the two transpose buffers: R = 2 in the size)
+    while (NT > 1 && pass_team_smem(NT, L.Qm, 2, a.nbuf, a.kmb) > (size_t)kMaxSmem) --NT;
+    const size_t smem = pass_team_smem(NT, L.Qm, 2, a.nbuf, a.kmb);
     if (smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
-    a.NWR = NWR;
-    a.nbands = (H + NWR - 1) / NWR;
-    a.grid = a.nbands;
+    a.NT = NT;
+    a.ring = team_ring(W, kResidentMin);
+    a.win = win;
+    a.centre = centre;
+    a.Q0w = space->Q[0];
+    a.Q1w = space->Q[1];
+    a.em = 0;
+    a.nbands = (H + NT - 1) / NT;
     a.spin_limit = 4000000;
-    if ((rc = cuda_status(cudaMemsetAsync(w, 0, L.ll + (size_t)a.nbands * W * Qw * 8, st)))) return rc;
+    const int laps = (W + a.ring - 1) / a.ring;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = std::max(1, edp_pass_team_occupancy(0, 0, 32 * NT, smem));
+    a.grid = std::min(a.nbands, occ * sms);
+    if (a.grid < a.nbands && team_ring(W, a.grid) > a.ring) return EDP_ERR_UNSUPPORTED;
+    if ((rc = cuda_status(cudaMemsetAsync(w, 0, L.ll + (size_t)a.nbands * a.ring * L.Qm * 8, st)))) return rc;
     for (int it = 0; it < params->iters; ++it)
         for (int pass = 0; pass < 4; ++pass) {
             const int slot = it * 4 + pass;
             const PassFlags f = pass_flags(it, pass, params->iters);
-            a.pass = pass;
-            a.read_c = f.read_c;
-            a.read_d = f.read_d;
-            a.write_a = f.write_a;
-            a.write_b = f.write_b;
-            a.final_ = f.final_;
-            a.tag = slot + 1;
-            a.band_counter = reinterpret_cast<unsigned *>(w + L.counters) + slot;
+            TeamArgs b = a;
+            b.pass = pass;
+            b.read_c = f.read_c;
+            b.read_d = f.read_d;
+            b.write_a = f.write_a;
+            b.write_b = f.write_b;
+            b.final_ = f.final_;
+            b.cons = reinterpret_cast<unsigned *>(w + L.cons) + (size_t)slot * H;
+            b.tag0 = 1 + slot * laps;
+            b.band_counter = reinterpret_cast<unsigned *>(w + L.counters) + slot;
             const bool prof = g_prof_events && 2 * slot + 1 < g_prof_n;
             if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot], st) != cudaSuccess) return EDP_ERR_CUDA;
-            if (launch_edp_pass_win(a, 32 * NWR, smem, st)) return EDP_ERR_CUDA;
+            if (launch_edp_pass_team(b, 32 * NT, smem, st)) return EDP_ERR_CUDA;
             if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
                 return EDP_ERR_CUDA;
         }
@@ -1239,9 +1243,9 @@ int edp_net_features_labels(const uint8_t *I0, const uint8_t *I1, const int32_t 
 }
 
 int edp_net_centres_residual(const float *out, const int32_t *base, int n, const edp_label_space *space,
-                             int32_t *centre, edp_stream_t stream) {
-    if (!out || !base || !centre || !space || n < 1 || space->R != 2) return EDP_ERR_INVALID_ARG;
-    return net_centres_base_launch(out, base, n, space->Q[0], space->Q[1], centre, (cudaStream_t)stream)
+                             int min_shift, int32_t *centre, edp_stream_t stream) {
+    if (!out || !base || !centre || !space || n < 1 || space->R != 2 || min_shift < 0) return EDP_ERR_INVALID_ARG;
+    return net_centres_base_launch(out, base, n, space->Q[0], space->Q[1], min_shift, centre, (cudaStream_t)stream)
                ? EDP_ERR_CUDA
                : EDP_OK;
 }

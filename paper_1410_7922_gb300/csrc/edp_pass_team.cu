@@ -4,8 +4,8 @@
 
 namespace edp {
 
-template <int EM, bool LEAN>
-__global__ void __launch_bounds__(LEAN || EM > 17 ? 256 : 384, 1) edp_pass_team_kernel(TeamArgs A) {
+template <int EM, bool LEAN, bool WIN>
+__global__ void __launch_bounds__(WIN ? 512 : (LEAN || EM > 17 ? 256 : 384), 1) edp_pass_team_kernel(TeamArgs A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
     __shared__ volatile int s_abort;
@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(LEAN || EM > 17 ? 256 : 384, 1) edp_pass_team_
         __syncthreads();
         const int band = s_band;
         if (band >= A.nbands) break;
-        if (!team_band<EM, LEAN>(A, band, smem_i, &s_abort)) return;
+        if (!team_band<EM, LEAN, WIN>(A, band, smem_i, &s_abort)) return;
     }
 }
 
@@ -25,17 +25,19 @@ size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb) {
     return (size_t)NT * team::team_ints(Qm, R, nbuf, kmb) * 4;
 }
 
-template <int EM, bool LEAN>
+template <int EM, bool LEAN, bool WIN = false>
 static void *team_kernel() {
-    return reinterpret_cast<void *>(edp_pass_team_kernel<EM, LEAN>);
+    return reinterpret_cast<void *>(edp_pass_team_kernel<EM, LEAN, WIN>);
 }
-static void *team_kernel_for(int em, int lean) {
-    if (lean) return team_kernel<33, true>();  // the lean body dispatches on the line lengths itself
+static void *team_kernel_for(int em, int lean, int win = 0) {
+    if (win) return team_kernel<9, false, true>();  // the windowed body dispatches on the box side
+    // the lean body dispatches on the line lengths itself: 9/17/33, or 65 only
+    if (lean) return em == 65 ? team_kernel<65, true>() : team_kernel<33, true>();
     return em == 9 ? team_kernel<9, false>() : (em == 17 ? team_kernel<17, false>() : team_kernel<33, false>());
 }
 
 int edp_pass_team_occupancy(int em, int lean, int threads, size_t smem) {
-    void *k = team_kernel_for(em, lean);
+    void *k = team_kernel_for(em, lean, em == 0);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
@@ -43,7 +45,7 @@ int edp_pass_team_occupancy(int em, int lean, int threads, size_t smem) {
 }
 
 int launch_edp_pass_team(const TeamArgs &a, int threads, size_t smem, cudaStream_t st) {
-    void *k = team_kernel_for(a.em, a.lean);
+    void *k = team_kernel_for(a.em, a.lean, a.win);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     void *args[] = {const_cast<TeamArgs *>(&a)};
     if (cudaLaunchKernel(k, dim3(a.grid), dim3(threads), args, smem, st) != cudaSuccess) return -2;

@@ -55,6 +55,9 @@ struct TeamArgs {
     int nbuf, kmb, ring;    // staging buffers, mailbox slots, record ring columns
     int tag0;               // tag of the first ring lap of this pass
     int lean;               // 1: lanes own whole lines of one vector (two or more axes)
+    int win;                // > 0: windowed form, box side (odd, <= 15)
+    const int *centre;      // windowed form: [H][W][R] box centres (label coordinates)
+    int Q0w, Q1w;           // windowed form: full label space sizes
     int em;                 // instantiation bound: labels per lane, or line length (lean)
     int nbands, grid;
     long long spin_limit;
@@ -83,25 +86,6 @@ struct PassR1Args {
 };
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st);
 size_t pass_r1_smem(int NWR, int E);
-
-// one EDP scan pass on per-pixel label boxes (pass_win.cu)
-struct WinArgs {
-    const int *Cw;          // [H][W][Qw] cost of each pixel's box labels
-    int *M[4];              // messages, box coordinates of the receiving pixel
-    int *labels;            // [H][W] full-space label index
-    int2 *ll;               // [nbands][W][Qw] hand-off records
-    const int *centre;      // [H][W][R] proposed centres (label coordinates)
-    unsigned *band_counter;
-    int *status;
-    int W, H, Qw, E, EMt;
-    int n, R, Q0, Q1;       // box side, label axes, full-space sizes
-    int lam, capv, mode;
-    int pass, read_c, read_d, write_a, write_b, final_;
-    int NWR, nbands, grid, tag;
-    long long spin_limit;
-};
-int launch_edp_pass_win(const WinArgs &a, int threads, size_t smem, cudaStream_t st);
-size_t pass_win_smem(int NWR, int E);
 
 // batched solve: up to kMaxBatch problems of one wave, passed by value
 constexpr int kMaxBatch = 48;
@@ -204,7 +188,8 @@ int labels_up2_launch(const int *lc, int Wc, int Hc, int Qc0, int vminc0, int vm
                       int vmin0, int vmin1, int *out, cudaStream_t st);
 int net_features_lab_launch(const uint8_t *I0, const uint8_t *I1, const int *lab, int W, int H, int pitch, int Q0,
                             int Q1, int vmin0, int vmin1, int l2, int cmax, float scale, void *out, cudaStream_t st);
-int net_centres_base_launch(const float *out, const int *base, int n, int Q0, int Q1, int *centre, cudaStream_t st);
+int net_centres_base_launch(const float *out, const int *base, int n, int Q0, int Q1, int min_shift, int *centre,
+                            cudaStream_t st);
 int net_targets_launch(const int *lab, const int *base, int n, int Q0, int Q1, float *t, cudaStream_t st);
 
 }  // namespace edp

@@ -273,12 +273,16 @@ __global__ void net_features_lab(const uint8_t *I0, const uint8_t *I1, const int
 }
 
 // Centres as a correction of a base labeling: base coordinates plus the
-// network output (label units), rounded and clamped into the label space.
-__global__ void net_centres_base(const float *out, const int *base, int n, int Q0, int Q1, int *centre) {
+// network output (label units), rounded; a correction whose larger component
+// is below min_shift labels is dropped; clamped into the label space.
+__global__ void net_centres_base(const float *out, const int *base, int n, int Q0, int Q1, int min_shift,
+                                 int *centre) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int b0 = base[i] % Q0, b1 = base[i] / Q0;
-        const int c0 = b0 + (int)roundf(out[2 * i]);
-        const int c1 = b1 + (int)roundf(out[2 * i + 1]);
+        int r0 = (int)roundf(out[2 * i]), r1 = (int)roundf(out[2 * i + 1]);
+        if (max(abs(r0), abs(r1)) < min_shift) r0 = r1 = 0;
+        const int c0 = b0 + r0;
+        const int c1 = b1 + r1;
         centre[2 * i] = min(max(c0, 0), Q0 - 1);
         centre[2 * i + 1] = min(max(c1, 0), Q1 - 1);
     }
@@ -481,8 +485,9 @@ int net_features_lab_launch(const uint8_t *I0, const uint8_t *I1, const int *lab
                                                reinterpret_cast<__nv_bfloat16 *>(out));
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
-int net_centres_base_launch(const float *out, const int *base, int n, int Q0, int Q1, int *centre, cudaStream_t st) {
-    net_centres_base<<<152 * 4, 256, 0, st>>>(out, base, n, Q0, Q1, centre);
+int net_centres_base_launch(const float *out, const int *base, int n, int Q0, int Q1, int min_shift, int *centre,
+                            cudaStream_t st) {
+    net_centres_base<<<152 * 4, 256, 0, st>>>(out, base, n, Q0, Q1, min_shift, centre);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 int net_targets_launch(const int *lab, const int *base, int n, int Q0, int Q1, float *t, cudaStream_t st) {

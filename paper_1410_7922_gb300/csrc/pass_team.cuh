@@ -195,9 +195,10 @@ __device__ __forceinline__ int2 seg_dt2(int (&a)[EM], int (&b)[EM], const int E,
 }
 
 // ints of shared memory of one team
+// stage of one column: C, m_c, m_d (Qm + 4 ints each) and 8 ints of box centres
+__host__ __device__ inline size_t stage_ints(int Qm) { return 3 * ((size_t)Qm + 4) + 8; }
 __host__ __device__ inline size_t team_ints(int Qm, int R, int nbuf, int kmb) {
-    const size_t Qs = (size_t)Qm + 4;
-    return (size_t)nbuf * 3 * Qs + (size_t)Qm * (1 + (R >= 2 ? 2 : 0) + kmb) + kMisc;
+    return (size_t)nbuf * stage_ints(Qm) + (size_t)Qm * (1 + (R >= 2 ? 2 : 0) + kmb) + kMisc;
 }
 
 }  // namespace team
@@ -231,6 +232,30 @@ __device__ __forceinline__ int lean_dt(int (&h)[L], int lam, int cl_add, bool pe
     return lmin;
 }
 
+// Same, with the backward sweep kept in shared memory at ab + i * st4 (the
+// line's own slots; lines longer than 33 labels).
+template <int L>
+__device__ __forceinline__ int lean_dt_smem(int (&h)[L], int lam, int cl_add, bool per_axis, int cl_fixed,
+                                            unsigned ab, unsigned st4) {
+    int lmin = h[L - 1], sw = h[L - 1];
+    team::sts(ab + (L - 1) * st4, sw);
+#pragma unroll
+    for (int i = L - 2; i >= 0; --i) {
+        lmin = min(lmin, h[i]);
+        sw = min(h[i], sw + lam);
+        team::sts(ab + i * st4, sw);
+    }
+    const int cl = per_axis ? lmin + cl_add : cl_fixed;
+    int f = h[0];
+    h[0] = min(team::lds(ab), cl);
+#pragma unroll
+    for (int i = 1; i < L; ++i) {
+        f = min(h[i], f + lam);
+        h[i] = min(min(f, team::lds(ab + i * st4)), cl);
+    }
+    return lmin;
+}
+
 // Phase 0 of one line of axis 0 (contiguous labels q0 .. q0 + L - 1): the
 // halved sums of Eq. DP_2D_base for vector `vsel` from the staged inputs,
 // the final-pass argmin key (vector a lanes), the sweeps; result into X.
@@ -258,7 +283,11 @@ __device__ __forceinline__ int lean_phase0(unsigned aC, unsigned aCc, unsigned a
                               sgn * e);
         }
     }
-    const int lmin = lean_dt<L>(h, lam, capv, per_axis, kBig);
+    int lmin;
+    if constexpr (L > 33)
+        lmin = lean_dt_smem<L>(h, lam, capv, per_axis, kBig, aX + o, 4u);
+    else
+        lmin = lean_dt<L>(h, lam, capv, per_axis, kBig);
 #pragma unroll
     for (int i = 0; i < L; ++i) team::sts(aX + o + 4 * i, h[i]);
     return lmin;
@@ -280,7 +309,10 @@ __device__ __forceinline__ void lean_phase_r(unsigned aX, int qb, int st, bool l
     int h[L];
 #pragma unroll
     for (int i = 0; i < L; ++i) h[i] = team::lds(o + i * st4);
-    lean_dt<L>(h, lam, capv, per_axis, last ? gv + capv : kBig);
+    if constexpr (L > 33)
+        lean_dt_smem<L>(h, lam, capv, per_axis, last ? gv + capv : kBig, o, st4);
+    else
+        lean_dt<L>(h, lam, capv, per_axis, last ? gv + capv : kBig);
     if (!last) {
 #pragma unroll
         for (int i = 0; i < L; ++i) team::sts(o + i * st4, h[i]);
@@ -309,10 +341,11 @@ __device__ __forceinline__ void lean_phase_r(unsigned aX, int qb, int st, bool l
 }
 
 // lean line lengths
-__host__ __device__ inline bool lean_length(int L) { return L == 9 || L == 17 || L == 33; }
+__host__ __device__ inline bool lean_length(int L) { return L == 9 || L == 17 || L == 33 || L == 65; }
 
 // EM: labels-per-lane bound (generic form) or line-length bound (LEAN).
-template <int EM, bool LEAN>
+// WIN: EDP on per-pixel label boxes (windowed form, one warp per row).
+template <int EM, bool LEAN, bool WIN = false>
 __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int *smem, volatile int *s_abort) {
     using namespace team;
     const int Q = A.Q, Qm = A.Qm, W = A.W, H = A.H, T = A.T, NT = A.NT, R = A.R;
@@ -322,16 +355,18 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
     const int wt = warp - tm * T;
     const int tl = wt * 32 + lane;
     const int NL = 32 * T;
-    const size_t tints = team_ints(Qm, R, nbuf, kmb);
+    const int Ralloc = WIN ? 2 : R;  // the windowed form uses the transpose buffers as scratch
+    const size_t tints = team_ints(Qm, Ralloc, nbuf, kmb);
     const int Qs = Qm + 4;
+    const int SS = (int)stage_ints(Qm);
     // regions of team i
     auto stg_of = [&](int i) { return smem + (size_t)i * tints; };
-    auto ma_of = [&](int i) { return stg_of(i) + (size_t)nbuf * 3 * Qs; };
+    auto ma_of = [&](int i) { return stg_of(i) + (size_t)nbuf * SS; };
     auto ta_of = [&](int i) { return ma_of(i) + Qm; };
-    auto mbox_of = [&](int i) { return ma_of(i) + Qm * (1 + (R >= 2 ? 2 : 0)); };
+    auto mbox_of = [&](int i) { return ma_of(i) + Qm * (1 + (Ralloc >= 2 ? 2 : 0)); };
     auto misc_of = [&](int i) { return mbox_of(i) + (size_t)kmb * Qm; };
     for (int i = tid; i < NT * 32; i += blockDim.x) misc_of(i >> 5)[i & 31] = 0;
-    if (LEAN) {
+    if (LEAN || WIN) {
         // m_a into the first column and m_b into the image's first row are zero
         for (int i = tid; i < NT * Qm; i += blockDim.x) ma_of(i / Qm)[i % Qm] = 0;
         if (band == 0)
@@ -388,7 +423,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 const int x = incx ? s : W - 1 - s;
                 const size_t pix = (size_t)y * W + x;
                 const bool c_ok = A.read_c && (incx ? x + 1 < W : x - 1 >= 0);
-                int *dst = stg + (size_t)(s % nbuf) * 3 * Qs;
+                int *dst = stg + (size_t)(s % nbuf) * SS;
                 const size_t e0 = pix * Q + cshift, e1 = e0 + Q, eend = NQ + cshift;
                 const size_t c0 = e0 >> 2, c1 = (e1 + 3) >> 2;
                 for (size_t c = c0 + tl; c < c1; c += NL) {
@@ -399,6 +434,14 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 for (int c = tl; c < Qm / 4; c += NL) {
                     cp16(dst + Qs + 4 * c, sc + 4 * c, c_ok ? 16 : 0);
                     cp16(dst + 2 * Qs + 4 * c, sd + 4 * c, d_ok ? 16 : 0);
+                }
+                if (WIN && tl < 3 * R) {
+                    // box centres of this pixel, of the next pixel of the row and of
+                    // the same column in the next row (zero where there is none)
+                    const int which = tl / R, r_ = tl - which * R;
+                    const bool ok = which == 0 || (which == 1 ? s + 1 < W : has_next);
+                    const size_t p2 = which == 0 ? pix : (which == 1 ? pix + (incx ? 1 : -1) : (size_t)y_next * W + x);
+                    cp_async4(dst + 3 * Qs + tl, A.centre + (ok ? p2 : pix) * R + r_, ok);
                 }
             }
             cp_async_commit();
@@ -479,7 +522,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             if (sync_or(tm, T, bad || *s_abort)) break;  // barrier 1
 
             // ---- column s: inputs in shared memory, outputs ----
-            const int *sb = stg + (size_t)(s % nbuf) * 3 * Qs;
+            const int *sb = stg + (size_t)(s % nbuf) * SS;
             const int *sC = sb + (int)((((size_t)y * W + (incx ? s : W - 1 - s)) * Q + cshift) & 3);
             const int *sc = sb + Qs, *sd = sb + 2 * Qs;
             const int *mbv = (r > 0) ? mbox + (s % kmb) * Qm : nullptr;
@@ -507,6 +550,8 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 emit_a(q, oa);
                 emit_b(q, ob);
             };
+            // windowed form: the box origin maps box labels to the full space
+            int map_lo0 = 0, map_lo1 = 0;
             // warp minimum / argmin into the team's control words, barrier 2,
             // then the per-column bookkeeping of lane 0
             auto barrier2 = [&](int ja, int jb) -> bool {
@@ -533,12 +578,177 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                     if (A.final_) {
                         unsigned long long best = wkey[0];
                         for (int w = 1; w < T; ++w) best = min(best, wkey[w]);
-                        A.labels[(size_t)y * W + x] = (int)(best & 0xffffffffu);
+                        int q = (int)(best & 0xffffffffu);
+                        if (WIN) q = (map_lo0 + q % A.win) + A.Q0w * (map_lo1 + q / A.win);
+                        A.labels[(size_t)y * W + x] = q;
                     }
                 }
                 return true;
             };
-            if constexpr (LEAN) {
+            if constexpr (WIN) {
+            // Windowed form.  Every pixel x keeps only the N^R labels of its box
+            // B(x) (origin lo(x), from a proposed centre clamped into the label
+            // space); costs, messages and sums are in the coordinates of the
+            // pixel's own box.  A message from x to a neighbour x' is the exact
+            // min-convolution between the two boxes,
+            //     m(v) = min_{u in B(x)} floor(S(x, u) / 2) + V(u, v),  v in B(x'),
+            // per label axis as in Sec. 3.2: the sweeps (Eq. L_dec3, Eq. L_dec5)
+            // along the source box's line give the L1 distance transform D at
+            // every source position; a target coordinate outside the source
+            // range takes D at the nearest source end plus lambda times the
+            // distance (all candidates then lie on one side).  The per-axis
+            // clip follows each axis; the joint clip (box minimum + lambda f(g),
+            // Eq. derivation1) follows the last axis.  Lanes [0, N) own the
+            // axis-0 lines of S_a's box, lanes [N, 2N) those of S_b (one line
+            // each for one label axis); one warp per image row.
+            const int N = A.win, hN = (N - 1) / 2;
+            const int *cs = sb + 3 * Qs;
+            auto origin = [&](int c, int Qr) { return min(max(c, hN), Qr - 1 - hN) - hN; };
+            const int lo0 = origin(cs[0], A.Q0w), lo1 = R == 2 ? origin(cs[1], A.Q1w) : 0;
+            const bool nxt = s + 1 < W;
+            const int la0 = nxt ? origin(cs[R], A.Q0w) : lo0;
+            const int la1 = R == 2 ? (nxt ? origin(cs[R + 1], A.Q1w) : lo1) : 0;
+            const int lb0 = has_next ? origin(cs[2 * R], A.Q0w) : lo0;
+            const int lb1 = R == 2 ? (has_next ? origin(cs[2 * R + 1], A.Q1w) : lo1) : 0;
+            map_lo0 = lo0;
+            map_lo1 = lo1;
+            // old messages no pass has written yet come from sums that are still
+            // zero: M(0) between the boxes (the c neighbour is the next pixel of
+            // the row, the d neighbour the same column of the next row)
+            const bool c_m0 = !A.read_c && nxt, d_m0 = !A.read_d && has_next;
+            const int v = R == 2 ? (lane < N ? 0 : (lane < 2 * N ? 1 : -1)) : (lane < 2 ? lane : -1);
+            const int l = R == 2 ? lane - (v > 0 ? N : 0) : 0;
+            const int d0 = (v == 1 ? lb0 : la0) - lo0, d1 = (v == 1 ? lb1 : la1) - lo1;
+            const unsigned aX = saddr(v == 1 ? tB : tA);
+            const unsigned aC = saddr(sC), aCc = saddr(sc), aCd = saddr(sd);
+            const unsigned aMa = saddr(maS), aMb = saddr(mbox + (s % kmb) * Qm);
+            const int lam = A.lam, capv = A.capv;
+            auto m0 = [&](int i0, int i1, int s0, int s1) {
+                const int a0 = lo0 + i0, a1 = lo1 + i1;
+                const int e0 = max(0, max(s0 - a0, a0 - (s0 + N - 1)));
+                const int e1 = R == 2 ? max(0, max(s1 - a1, a1 - (s1 + N - 1))) : 0;
+                return per_axis ? min(lam * e0, capv) + min(lam * e1, capv) : min(lam * (e0 + e1), capv);
+            };
+            auto body = [&](auto nc) -> bool {
+                constexpr int NN = decltype(nc)::value;
+                int lmin0 = kBig;
+                int out1[NN];  // one label axis: the messages, emitted after barrier 2
+                if (v >= 0) {
+                    // phase 0: halved sums of the own box, sweeps along axis 0,
+                    // values at the target box's axis-0 coordinates
+                    const int qb = R == 2 ? l * NN : 0;
+                    int hv[NN], bv[NN];
+#pragma unroll
+                    for (int i = 0; i < NN; ++i) {
+                        const int q = qb + i;
+                        const unsigned o4 = 4u * (unsigned)q;
+                        const int t = lds(aC + o4) + lds(aMa + o4) + lds(aMb + o4);
+                        const int c = c_m0 ? m0(i, l, la0, la1) : lds(aCc + o4);
+                        const int d = d_m0 ? m0(i, l, lb0, lb1) : lds(aCd + o4);
+                        if (A.final_ && v == 0)
+                            key = min(key, ((unsigned long long)((unsigned)(t + c + d) ^ 0x80000000u) << 32) | (unsigned)q);
+                        hv[i] = floor_half(v ? t + c - d : t + d - c);
+                        lmin0 = min(lmin0, hv[i]);
+                    }
+                    int sw = hv[NN - 1];
+                    bv[NN - 1] = sw;
+#pragma unroll
+                    for (int i = NN - 2; i >= 0; --i) {
+                        sw = min(hv[i], sw + lam);
+                        bv[i] = sw;
+                    }
+                    int f = hv[0];
+                    hv[0] = min(f, bv[0]);
+#pragma unroll
+                    for (int i = 1; i < NN; ++i) {
+                        f = min(hv[i], f + lam);
+                        hv[i] = min(f, bv[i]);
+                    }
+                    // values at the target box's coordinates t: source position
+                    // u = t + d0 clamped to the line, plus lambda per label beyond it
+                    const int cl = (R == 1 || per_axis) ? lmin0 + capv : kBig;
+                    const unsigned ax = aX + 4u * (unsigned)qb;
+#pragma unroll
+                    for (int i = 0; i < NN; ++i) sts(ax + 4u * i, hv[i]);
+#pragma unroll
+                    for (int tt = 0; tt < NN; ++tt) {
+                        const int u = min(max(tt + d0, 0), NN - 1);
+                        bv[tt] = min(lds(ax + 4u * (unsigned)u) + lam * abs(tt + d0 - u), cl);
+                    }
+                    if (R == 1) {
+                        // m_a of this column is still being read by the S_b lane
+#pragma unroll
+                        for (int i = 0; i < NN; ++i) out1[i] = bv[i];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < NN; ++i) sts(aX + 4u * (unsigned)(qb + i), bv[i]);
+                    }
+                }
+                const int vma = __reduce_min_sync(kAllLanes, v == 0 ? lmin0 : kBig);
+                const int vmb = __reduce_min_sync(kAllLanes, v == 1 ? lmin0 : kBig);
+                if (!barrier2(vma, vmb)) return false;
+                if (R == 1 && v == 0) {
+#pragma unroll
+                    for (int i = 0; i < NN; ++i) emit_a(i, out1[i]);
+                } else if (R == 1 && v == 1) {
+#pragma unroll
+                    for (int i = 0; i < NN; ++i) emit_b(i, out1[i]);
+                }
+                if (R == 2 && v >= 0) {
+                    // phase 1: sweeps along axis 1 of the target's axis-0 column l
+                    int hv[NN], bv[NN];
+                    int lmin = kBig;
+#pragma unroll
+                    for (int i = 0; i < NN; ++i) {
+                        hv[i] = lds(aX + 4u * (unsigned)(l + NN * i));
+                        lmin = min(lmin, hv[i]);
+                    }
+                    int sw = hv[NN - 1];
+                    bv[NN - 1] = sw;
+#pragma unroll
+                    for (int i = NN - 2; i >= 0; --i) {
+                        sw = min(hv[i], sw + lam);
+                        bv[i] = sw;
+                    }
+                    int f = hv[0];
+                    hv[0] = min(f, bv[0]);
+#pragma unroll
+                    for (int i = 1; i < NN; ++i) {
+                        f = min(hv[i], f + lam);
+                        hv[i] = min(f, bv[i]);
+                    }
+                    const int cl = (per_axis ? lmin : (v == 0 ? vma : vmb)) + capv;
+                    const unsigned ax = aX + 4u * (unsigned)l;
+#pragma unroll
+                    for (int i = 0; i < NN; ++i) sts(ax + 4u * (unsigned)(NN * i), hv[i]);
+#pragma unroll
+                    for (int tt = 0; tt < NN; ++tt) {
+                        const int u = min(max(tt + d1, 0), NN - 1);
+                        bv[tt] = min(lds(ax + 4u * (unsigned)(NN * u)) + lam * abs(tt + d1 - u), cl);
+                    }
+                    if (v == 0) {
+#pragma unroll
+                        for (int i = 0; i < NN; ++i) emit_a(l + NN * i, bv[i]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < NN; ++i) emit_b(l + NN * i, bv[i]);
+                    }
+                }
+                return true;
+            };
+            bool ok;
+            switch (N) {
+            case 1: ok = body(std::integral_constant<int, 1>()); break;
+            case 3: ok = body(std::integral_constant<int, 3>()); break;
+            case 5: ok = body(std::integral_constant<int, 5>()); break;
+            case 7: ok = body(std::integral_constant<int, 7>()); break;
+            case 9: ok = body(std::integral_constant<int, 9>()); break;
+            case 11: ok = body(std::integral_constant<int, 11>()); break;
+            case 13: ok = body(std::integral_constant<int, 13>()); break;
+            default: ok = body(std::integral_constant<int, 15>()); break;
+            }
+            if (!ok) break;
+            } else if constexpr (LEAN) {
             // Lean form (two or more axes): lane lv of vector v (warps
             // [v*Tv, v*Tv + Tv)) owns whole lines; the backward sweep goes to the
             // vector's shared buffer X, the forward sweep combines on the way.
@@ -558,7 +768,9 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
 #pragma unroll 1
                 for (int li = lv; li < nl; li += NLV) {
                     int lm;
-                    if (L == 33)
+                    if constexpr (EM >= 65) {
+                        lm = lean_phase0<65>(aC, aCc, aCd, aMa, aMb, aX, li * 65, vsel, final_a, per_axis, lam, A.capv, key);
+                    } else if (L == 33)
                         lm = lean_phase0<33>(aC, aCc, aCd, aMa, aMb, aX, li * 33, vsel, final_a, per_axis, lam, A.capv, key);
                     else if (L == 17)
                         lm = lean_phase0<17>(aC, aCc, aCd, aMa, aMb, aX, li * 17, vsel, final_a, per_axis, lam, A.capv, key);
@@ -587,7 +799,9 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
 #pragma unroll 1
                     for (int li = lv; li < Xr.nlines; li += NLV) {
                         const int qb = line_first(Xr, li);
-                        if (Xr.L == 33)
+                        if constexpr (EM >= 65)
+                            lean_phase_r<65>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
+                        else if (Xr.L == 33)
                             lean_phase_r<33>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
                         else if (Xr.L == 17)
                             lean_phase_r<17>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);

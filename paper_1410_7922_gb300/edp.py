@@ -82,7 +82,7 @@ def load() -> ctypes.CDLL:
         "edp_wta": ([P, P, I, I, I, LS, PR, I, P, P, P], I),
         "edp_coarse_labels": ([P, P, I, I, I, LS, PR, P, P, SZ, P], I),
         "edp_net_features_labels": ([P, P, P, I, I, I, LS, PR, ctypes.c_float, P, P], I),
-        "edp_net_centres_residual": ([P, P, I, LS, P, P], I),
+        "edp_net_centres_residual": ([P, P, I, LS, I, P, P], I),
         "edp_net_targets": ([P, P, I, LS, P, P], I),
         "edp_net_param_count": ([], ctypes.c_longlong),
         "edp_net_workspace_size": ([I, I, I], SZ),
@@ -522,14 +522,16 @@ def net_features_labels(I0, I1, labels, space: dict, l2: int, cmax: int, scale: 
     return out
 
 
-def net_centres_residual(out, base, space: dict, centre=None, stream=None):
-    """edp_net_centres_residual: int32 [..][2] centres = base label + network output."""
+def net_centres_residual(out, base, space: dict, min_shift: int = 0, centre=None, stream=None):
+    """edp_net_centres_residual: int32 [..][2] centres = base label + network
+    output (corrections below min_shift labels dropped)."""
     n = out.numel() // 2
     if centre is None:
         centre = torch.empty(out.shape[:-1] + (2,), dtype=torch.int32, device=out.device)
     ls = label_space(space)
     rc = load().edp_net_centres_residual(_dev(out, torch.float32, "out"), _dev(base, torch.int32, "base"), n,
-                                         ctypes.byref(ls), _dev(centre, torch.int32, "centre"), _stream(stream))
+                                         ctypes.byref(ls), int(min_shift), _dev(centre, torch.int32, "centre"),
+                                         _stream(stream))
     _check(rc, "net_centres_residual")
     return centre
 

@@ -29,6 +29,7 @@ import torch
 from . import edp, synth
 
 FLOW_SCALE = 16.0
+MIN_SHIFT = 2  # network corrections below this many labels are not applied
 
 
 def pair(pair_id: int, W: int, H: int, vmax: int = 32) -> dict:
@@ -137,14 +138,15 @@ def train(x: torch.Tensor, t: torch.Tensor, epochs: int = 30, batch: int = 8, lr
     return P, losses
 
 
-def propose(P: torch.Tensor, I0, I1, w: dict, base: torch.Tensor | None = None, ws=None) -> torch.Tensor:
+def propose(P: torch.Tensor, I0, I1, w: dict, base: torch.Tensor | None = None, ws=None,
+            min_shift: int = MIN_SHIFT) -> torch.Tensor:
     """Box centres int32 [H][W][2]: coarse labeling + the network's correction."""
     if base is None:
         base = coarse(I0, I1, w, ws)
     x = features(I0, I1, w, base)[None].contiguous()
     H, W = I0.shape
     out = edp.net_forward(P, x, edp.net_workspace(1, H, W))
-    return edp.net_centres_residual(out[0].contiguous(), base, w["space"])
+    return edp.net_centres_residual(out[0].contiguous(), base, w["space"], min_shift)
 
 
 def windowed_edp(I0, I1, w: dict, centre: torch.Tensor, win: int = 9, iters: int = 1, ws=None):
@@ -167,8 +169,21 @@ def refine(I0, I1, w: dict, centre: torch.Tensor, rounds: int, win: int = 9, ite
     return lab
 
 
+def coverage(centre: torch.Tensor, labels: torch.Tensor, space: dict, win: int) -> float:
+    """Fraction of pixels whose label (e.g. full-label EDP's) lies inside the
+    win x win box around the centre, boxes clamped into the space as the
+    windowed solve does (evaluation metric)."""
+    Q0, Q1 = space["Q"][0], space["Q"][1]
+    h = (win - 1) // 2
+    c0 = centre[..., 0].clamp(h, Q0 - 1 - h)
+    c1 = centre[..., 1].clamp(h, Q1 - 1 - h)
+    l0, l1 = labels % Q0, torch.div(labels, Q0, rounding_mode="floor")
+    inside = ((l0 - c0).abs() <= h) & ((l1 - c1).abs() <= h)
+    return float(inside.float().mean().item())
+
+
 def evaluate(P: torch.Tensor, pairs: list[int], W: int, H: int, win: int = 9, iters: int = 1, reps: int = 3,
-             vmax: int = 32, rounds: int = 1):
+             vmax: int = 32, rounds: int = 1, min_shift: int = MIN_SHIFT):
     """Energy gap and time against full-label EDP on held-out pairs of
     (coarse labeling + network + windowed EDP) and of the same path without
     the network (windows centred on the coarse labeling)."""
@@ -202,19 +217,31 @@ def evaluate(P: torch.Tensor, pairs: list[int], W: int, H: int, win: int = 9, it
         e_full = int(e_f[3].item())
         C = edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"])
 
+        centres = {}
+
         def net_path():
             base = coarse(I0, I1, w, ws_c, iters)
             x = features(I0, I1, w, base)[None].contiguous()
             out = edp.net_forward(P, x, net_ws)
-            c = edp.net_centres_residual(out[0].contiguous(), base, w["space"])
+            c = edp.net_centres_residual(out[0].contiguous(), base, w["space"], min_shift)
+            centres["net"] = c
             return refine(I0, I1, w, c, rounds, win, iters, ws_win)
 
         def coarse_path():
             base = coarse(I0, I1, w, ws_c, iters)
-            return refine(I0, I1, w, label_centres(base, w["space"]), rounds, win, iters, ws_win)
+            c = label_centres(base, w["space"])
+            centres["coarse"] = c
+            return refine(I0, I1, w, c, rounds, win, iters, ws_win)
 
         lab_n, ms_net = timed(net_path)
         lab_c, ms_coarse = timed(coarse_path)
+        # held-out smooth-L1 of the network's correction against full-label
+        # EDP, and of no correction (the coarse labeling as it is)
+        base = coarse(I0, I1, w, ws_c, iters)
+        out = edp.net_forward(P, features(I0, I1, w, base)[None].contiguous(), net_ws)
+        tgt = edp.net_targets(lab_f, w["space"], base=base)[None].contiguous()
+        loss_net = float(edp.net_backward(P, out, tgt, net_ws)[1].item())
+        loss_zero = float(edp.net_backward(P, torch.zeros_like(out), tgt, net_ws)[1].item())
         e_net = int(edp.energy(C, lab_n, w["space"], w["prior"])[3].item())
         e_coarse = int(edp.energy(C, lab_c, w["space"], w["prior"])[3].item())
         del C
@@ -222,5 +249,8 @@ def evaluate(P: torch.Tensor, pairs: list[int], W: int, H: int, win: int = 9, it
                      "gap_net": (e_net - e_full) / e_full, "gap_coarse": (e_coarse - e_full) / e_full,
                      "ms_full": ms_full, "ms_net": ms_net, "ms_coarse": ms_coarse,
                      "label_agree_net": float((lab_n == lab_f).float().mean().item()),
-                     "label_agree_coarse": float((lab_c == lab_f).float().mean().item())})
+                     "label_agree_coarse": float((lab_c == lab_f).float().mean().item()),
+                     "loss_net": loss_net, "loss_zero": loss_zero,
+                     "cover_net": coverage(centres["net"], lab_f, w["space"], win),
+                     "cover_coarse": coverage(centres["coarse"], lab_f, w["space"], win)})
     return rows

@@ -136,8 +136,9 @@ def test_features_labels_targets_residual_centres(edp_lib):
     assert np.array_equal(t0.cpu().numpy(), rnet.targets(lab, Q))
     out = (rng.standard_normal((29, 37, 2)) * 3).astype(np.float32)
     out[0, :4, 0] = [0.5, -0.5, 1.5, -2.5]  # ties round away from zero
-    c = edp_lib.net_centres_residual(torch.from_numpy(out).cuda(), torch.from_numpy(base).cuda(), space)
-    assert np.array_equal(c.cpu().numpy(), rnet.centres_residual(out.astype(np.float64), base, Q))
+    for gate in (0, 2, 3):
+        c = edp_lib.net_centres_residual(torch.from_numpy(out).cuda(), torch.from_numpy(base).cuda(), space, gate)
+        assert np.array_equal(c.cpu().numpy(), rnet.centres_residual(out.astype(np.float64), base, Q, gate))
 
 
 def test_net_training_lowers_loss(edp_lib):

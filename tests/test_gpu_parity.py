@@ -134,7 +134,8 @@ def run_edp(edp_lib, C, space, prior, iters):
 @pytest.mark.parametrize("Q,mode", [((7,), "joint"), ((64,), "joint"), ((33,), "joint"), ((130,), "joint"),
                                     ((5, 4), "per_axis"), ((5, 4), "joint"), ((9, 9), "per_axis"),
                                     ((33, 33), "per_axis"), ((33, 33), "joint"), ((17, 9), "per_axis"),
-                                    ((17, 17, 9), "joint"), ((9, 9, 9), "per_axis"), ((3, 4, 3), "joint"),
+                                    ((17, 17, 9), "joint"), ((9, 9, 9), "per_axis"), ((65, 65), "per_axis"),
+                                    ((65, 65), "joint"), ((3, 4, 3), "joint"),
                                     ((5, 5, 3), "per_axis"), ((1,), "joint")])
 @pytest.mark.parametrize("iters", [1, 2])
 def test_edp_random(edp_lib, Q, mode, iters):
@@ -158,6 +159,17 @@ def test_edp_degenerate_shapes(edp_lib, W, H, general):
     for iters in (1, 3):
         want, got = run_edp(edp_lib, C, sp((6,)), prior, iters)
         assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("Q,mode", [((7,), "joint"), ((5, 4), "per_axis"), ((9, 9), "joint")])
+def test_edp_sixteen_iterations(edp_lib, Q, mode):
+    """Long runs of Algorithm 1 (j = 16): later iterations read all four
+    message arrays and the sums keep growing."""
+    rng = np.random.default_rng(sum(Q) + 16)
+    C = rng.integers(0, 21, size=(11, 13, int(np.prod(Q)))).astype(np.int32)
+    prior = {"lam": 7, "g": 3, "l1": 1, "mode": mode}
+    want, got = run_edp(edp_lib, C, sp(Q), prior, 16)
+    assert np.array_equal(got, want)
 
 
 @pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 50), (50, 3)])

@@ -119,3 +119,5 @@ def test_targets_and_residual_centres():
     out = np.array([[0.5, -0.5], [1.49, -2.6], [9.0, 9.0]])
     b = np.array([6, 6, 6])        # (1, 1)
     assert net.centres_residual(out, b, Q).tolist() == [[2, 0], [2, 0], [4, 3]]
+    # corrections below 2 labels dropped: (1, -1) -> base; (1, -3) and (9, 9) kept
+    assert net.centres_residual(out, b, Q, min_shift=2).tolist() == [[1, 1], [2, 0], [4, 3]]
