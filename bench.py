@@ -342,7 +342,7 @@ def time_solve_rows(edp, synth, torch):
     return rows
 
 
-def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, budget_gb: float = 120.0):
+def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, budget_gb: float = 200.0):
     """64 heterogeneous pairs: per-pair edp_solve_images launches against one
     edp_solve_batched call (persistent kernel) and its CUDA-graph replay."""
     from paper_1410_7922_gb300 import autotune

@@ -869,6 +869,17 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
         smem = std::max(smem, plans[k].smem);
     }
     const int occ = std::max(1, edp_batched_occupancy(lm, gen, threads, smem));
+    // work items run problem by problem inside each pass: the largest problems
+    // (longest wavefronts) first, so that small ones fill in behind them
+    int order[kMaxBatch], slot_of[kMaxBatch];
+    for (int k = 0; k < n; ++k) order[k] = k;
+    auto work = [&](int k) {
+        const edp_problem &pr = probs[first + k];
+        return (double)pr.W * pr.H * geo[first + k].Q;
+    };
+    std::stable_sort(order, order + n, [&](int a, int b) { return work(a) > work(b); });
+    for (int j = 0; j < n; ++j) slot_of[order[j]] = j;
+    for (int j = 0; j < n; ++j) B.prefix[j + 1] = B.prefix[j] + plans[order[j]].nbands;
     off = ctrl;
     for (int k = 0; k < n; ++k) {
         const edp_problem &pr = probs[first + k];
@@ -879,17 +890,19 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
         const SolvePlan &P = plans[k];
         off += problem_bytes(pr, g);
         if (!P.r1 && team_ring(pr.W, occ * sms) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
-        BatchProblem &bp = B.p[k];
+        BatchProblem &bp = B.p[slot_of[k]];
         bp.r1 = P.r1;
         bp.nbands = P.nbands;
         bp.iters = iters;
         bp.laps = P.laps;
         bp.cons = reinterpret_cast<unsigned *>(pws + L.cons);
-        bp.t = P.ta;
-        bp.o = P.o;
-        bp.t.status = status;
-        bp.o.status = status;
-        B.prefix[k + 1] = B.prefix[k] + P.nbands;
+        if (P.r1) {
+            bp.o = P.o;
+            bp.o.status = status;
+        } else {
+            bp.t = P.ta;
+            bp.t.status = status;
+        }
         zb.ptr[zb.n] = pws;
         zb.bytes[zb.n++] = control_bytes(P, pr.W, g.Q);
         CostArgs &c = cb.c[k];

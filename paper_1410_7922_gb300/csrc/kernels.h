@@ -88,15 +88,17 @@ int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream
 size_t pass_r1_smem(int NWR, int E);
 
 // batched solve: up to kMaxBatch problems of one wave, passed by value
-constexpr int kMaxBatch = 48;
+constexpr int kMaxBatch = 64;
 struct BatchProblem {
     int r1;            // 1: warp-per-row band body, 0: team band body
     int nbands;
     int iters;
     int laps;          // record ring laps per pass (team body)
     unsigned *cons;    // team body: [4*iters][nbands] consumed columns
-    TeamArgs t;        // team body fields (pass / flags / tags set per item)
-    PassR1Args o;      // one-axis body fields
+    union {
+        TeamArgs t;    // team body fields (pass / flags / tags set per item)
+        PassR1Args o;  // one-axis body fields
+    };
 };
 struct BatchArgs {
     int n;
