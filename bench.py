@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--extra", default="", help="comma list of longer side measurements: batched,proposal")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="image scale of the batched workload")
-    ap.add_argument("--proposal-pairs", type=int, default=500, help="training pairs of the proposal network")
+    ap.add_argument("--proposal-pairs", type=int, default=2000, help="training pairs of the proposal network")
     return ap.parse_args()
 
 
@@ -414,26 +414,33 @@ def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, bu
             "autotune": {"rows": tuned[0], "warps_per_row": tuned[1], "table": tuned[3]}}
 
 
-def measure_proposal(edp, torch, train_pairs: int = 500, train_W: int = 160, train_H: int = 120, epochs: int = 20,
+def measure_proposal(edp, torch, train_pairs: int = 2000, epochs: int = 10,
                      eval_pairs=(1000, 1001, 1002, 1003), W: int = 640, H: int = 480, win: int = 9):
     """Learned proposal + 9x9 windowed EDP against full-label EDP (65x65
-    labels) on held-out 640x480 pairs; the network is trained here, by the
-    project's kernels, on full-label EDP labelings of smaller pairs."""
+    labels) on held-out 640x480 pairs.  The network is trained here, by the
+    project's kernels, on full-label EDP labelings of train_pairs synthetic
+    640x480 pairs (the images are synthesised by a spawned process pool)."""
+    import multiprocessing as mp
+
     from paper_1410_7922_gb300 import proposal
     t0 = time.perf_counter()
-    x, t = proposal.build_training_set(train_pairs, train_W, train_H, first_pair=0)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        x, t = proposal.build_training_set(train_pairs, W, H, first_pair=0, pool=pool)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     P, losses = proposal.train(x, t, epochs=epochs, batch=8, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    del x, t
     rows = proposal.evaluate(P, list(eval_pairs), W, H, win=win, reps=2)
-    return {"train_pairs": train_pairs, "train_size": [train_W, train_H], "epochs": epochs,
-            "loss_first": losses[0], "loss_last": losses[-1], "s_training_data": t_data, "s_training": t_train,
-            "eval": rows,
-            "mean_gap_net": sum(r["gap_net"] for r in rows) / len(rows),
-            "mean_gap_wta": sum(r["gap_wta"] for r in rows) / len(rows),
+    mean = lambda k: sum(r[k] for r in rows) / len(rows)
+    return {"train_pairs": train_pairs, "train_size": [W, H], "epochs": epochs, "window": win,
+            "min_shift": proposal.MIN_SHIFT, "loss_first": losses[0], "loss_last": losses[-1],
+            "s_training_data": t_data, "s_training": t_train, "eval": rows,
+            "mean_gap_net": mean("gap_net"), "mean_gap_coarse": mean("gap_coarse"),
+            "mean_heldout_loss_net": mean("loss_net"), "mean_heldout_loss_no_correction": mean("loss_zero"),
+            "mean_ms_full": mean("ms_full"), "mean_ms_net": mean("ms_net"), "mean_ms_coarse": mean("ms_coarse"),
             "mean_speedup_net": sum(r["ms_full"] / r["ms_net"] for r in rows) / len(rows)}
 
 

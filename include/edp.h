@@ -37,8 +37,14 @@
  *  Prior, Eq. Smooth_value_t with f(u) = |u|^l1:
  *    EDP_PRIOR_JOINT     V(q, q') = lambda * min(sum_r |q_r - q'_r|^l1, g^l1)
  *    EDP_PRIOR_PER_AXIS  V(q, q') = sum_r lambda * min(|q_r - q'_r|^l1, g^l1)
- *  (identical for R = 1).  This build supports l1 = 1 (truncated linear,
- *  the LRMS of Sec. 3.2); l1 = 2 returns EDP_ERR_UNSUPPORTED.
+ *  (identical for R = 1).  l1 = 1 (truncated linear) is evaluated with the
+ *  LRMS sweeps of Sec. 3.2 everywhere.  l1 = 2 (truncated quadratic, the
+ *  generalized RMS of Eq. M_decmp: per axis the 2g - 1 taps |u| < g, then
+ *  the clip) is built for edp_solve / edp_solve_images / edp_solve_batched
+ *  when every label axis is served by the one-axis kernel (R = 1, Q <= 256)
+ *  or by the whole-line form of the multi-axis kernel (all axes of 9, 17 or
+ *  33 labels, or all of 65), and for edp_solve_windowed; other shapes and
+ *  edp_scanline_dp return EDP_ERR_UNSUPPORTED for l1 = 2.
  *  Cost, Eq. Cost_value: C(x, q) = min(|I1(x + o(q)) - I0(x)|^l2, cmax),
  *  cmax where x + o(q) leaves the image.
  */
@@ -57,7 +63,7 @@ typedef struct CUstream_st *edp_stream_t; /* == cudaStream_t */
 enum edp_status {
     EDP_OK = 0,
     EDP_ERR_INVALID_ARG = 1, /* null pointer, bad size, bad enum value        */
-    EDP_ERR_UNSUPPORTED = 2, /* valid by the paper but not built (e.g. l1=2)  */
+    EDP_ERR_UNSUPPORTED = 2, /* valid by the paper but not built for this shape */
     EDP_ERR_WORKSPACE = 3,   /* ws_bytes smaller than edp_workspace_size      */
     EDP_ERR_RANGE = 4,       /* sizes or values could overflow int32          */
     EDP_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired            */
@@ -86,7 +92,7 @@ typedef struct {
 typedef struct {
     int32_t lambda;     /* prior weight, >= 0                            */
     int32_t g;          /* truncation threshold, >= 1                    */
-    int32_t l1;         /* prior power (1 supported)                     */
+    int32_t l1;         /* prior power, 1 or 2 (see above)               */
     int32_t prior_mode; /* EDP_PRIOR_*                                   */
     int32_t l2;         /* cost power, 1 or 2                            */
     int32_t cmax;       /* cost truncation C_max, >= 0                   */
@@ -99,7 +105,8 @@ enum {
     EDP_OP_SCANLINE_DP = 1,
     EDP_OP_SOLVE = 2,
     EDP_OP_SOLVE_IMAGES = 3, /* edp_solve_images and edp_solve_images_host */
-    EDP_OP_COARSE = 4        /* edp_coarse_labels */
+    EDP_OP_COARSE = 4,       /* edp_coarse_labels */
+    EDP_OP_SCANLINE_MARGINALS = 5 /* edp_scanline_marginals */
 };
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -163,6 +170,18 @@ int edp_scanline_dp(const int32_t *C, int W, int H, const edp_label_space *space
                     const edp_params *params, int32_t *labels, int64_t *row_energy, void *ws,
                     size_t ws_bytes, edp_stream_t stream);
 
+/* Min-marginal mode of the scanline DP (the modified DP of Sec. 4.1,
+ * Eq. DP_1D_3): per image row the forward sums F (Eq. base, from the left
+ * end) and the backward sums B (the same recurrence from the right end);
+ * the marginal is S_Omega(x, q) = M(F(x-1))(q) + C(x, q) + M(B(x+1))(q)
+ * = F(x, q) + B(x, q) - C(x, q), and labels[y][x] is its lowest-index
+ * argmin.  marginals: optional int32 [H][W][Q] output of S_Omega (NULL:
+ * not written).  ws: edp_workspace_size(EDP_OP_SCANLINE_MARGINALS, ...)
+ * bytes, 256-byte aligned.  l1 = 1 only (EDP_ERR_UNSUPPORTED otherwise);
+ * EDP_ERR_RANGE when W * (cmax + R * lambda * g^l1) >= 2^29. */
+int edp_scanline_marginals(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,
+                           int32_t *labels, int32_t *marginals, void *ws, size_t ws_bytes, edp_stream_t stream);
+
 /* EDP, Sec. 4.2 / Algorithm 1 steps 2-5: params->iters iterations of the
  * four scan passes P1..P4 (Eq. DP_2D_base with the data term added, D = 2,
  * messages M(floor(S_k(x_k) / 2)), zero outside the image), then the
@@ -211,7 +230,7 @@ int edp_solve_images_host(const uint8_t *I0_host, const uint8_t *I1_host,
  * min-convolution of Eq. M_strf restricted to the two boxes, evaluated with
  * the RMS sweeps of Sec. 3.2 per axis.  With every box equal to the whole
  * space this is edp_solve.  Supported: R = 1 or 2, odd win <= 15,
- * win <= Q[r], l1 = 1.
+ * win <= Q[r], l1 = 1 or 2 (quadratic taps between the boxes).
  *  Cw: int32 [H][W][win^R] box costs from edp_cost_window.  labels: int32
  *  [H][W] full-space linear label indexes. */
 size_t edp_workspace_size_windowed(int W, int H, const edp_label_space *space, const edp_params *params,

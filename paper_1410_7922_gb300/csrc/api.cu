@@ -297,7 +297,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
     if (P->r1) {
         const int E = (g.Q + 31) / 32;
         int NWR = fixed_threads ? fixed_threads / 32 : (g_tune_rb > 0 ? g_tune_rb : 8);
-        if (!fixed_threads) NWR = std::max(kMinRowsR1, std::min(NWR, std::min(16, H)));
+        if (!fixed_threads) NWR = std::max(kMinRowsR1, std::min(NWR, std::min(8, H)));  // kernel built for <= 256 threads
         while (!fixed_threads && NWR > kMinRowsR1 && pass_r1_smem(NWR, E) > (size_t)kMaxSmem) --NWR;
         P->smem = pass_r1_smem(NWR, E);
         if (P->smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
@@ -327,6 +327,8 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         a.lam = p->lambda;
         a.capv = (int)cap_value(p);
         a.kc = p->g <= 1 ? 0 : std::min(31, (p->g - 1 + E - 1) / E);
+        a.l1 = p->l1;
+        a.g = p->g;
         a.NWR = NWR;
         a.nbands = (H + NWR - 1) / NWR;
         a.grid = a.nbands;
@@ -348,14 +350,17 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         short_lines = short_lines && (g.Qr[r] == 9 || g.Qr[r] == 17 || g.Qr[r] == 33);
         all65 = all65 && g.Qr[r] == 65;
     }
-    // 65-label lines: a build of their own (single-problem kernel only)
-    lean = lean && (short_lines || (all65 && !fixed_threads));
+    // 65-label lines: a build of their own (single-problem kernel only; the
+    // quadratic-prior build serves every line length of the form)
+    lean = lean && (short_lines || (all65 && (!fixed_threads || p->l1 == 2)));
     const int tmax = fixed_threads ? std::min(12, fixed_threads / 32) : (lean ? 8 : 12);
     if (lean) {
-        LM = all65 ? 65 : 33;
+        LM = p->l1 == 2 ? 2 : (all65 ? 65 : 33);
         int maxlines = 1;
         for (int r = 0; r < g.R; ++r) maxlines = std::max(maxlines, g.Q / g.Qr[r]);
-        Tv = g_tune_t > 0 ? std::max(1, g_tune_t / 2) : std::min((maxlines + 31) / 32, 4);
+        // one lane per line and vector; 65-label lines (many labels per line,
+        // HBM-heavy) run best with the widest team (measured)
+        Tv = g_tune_t > 0 ? std::max(1, g_tune_t / 2) : std::min(maxlines > 64 ? 4 : (maxlines + 31) / 32, 4);
         if (2 * Tv > tmax) Tv = tmax / 2;
         if (Tv < 1) return EDP_ERR_UNSUPPORTED;
         S.T = 2 * Tv;
@@ -367,6 +372,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
             stride *= L;
         }
     } else {
+        if (p->l1 != 1) return EDP_ERR_UNSUPPORTED;  // quadratic taps: one-axis, lean and windowed forms
         bool have = false;
         if (g_tune_t > 0) {
             if (g_tune_t > tmax || !team_shape(g, g_tune_t, p->g, &S)) return EDP_ERR_UNSUPPORTED;
@@ -425,6 +431,8 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
     a.ring = team_ring(W, kResidentMin);
     a.em = S.em;
     a.lean = lean;
+    a.l1 = p->l1;
+    a.g = p->g;
     a.nbands = (H + NT - 1) / NT;
     a.spin_limit = 4000000;
     P->laps = (W + a.ring - 1) / a.ring;
@@ -452,7 +460,7 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int occ = std::max(1, edp_pass_team_occupancy(P.em, P.ta.lean, P.threads, P.smem));
+        const int occ = std::max(1, edp_pass_team_occupancy(P.em, P.ta.lean, 0, P.threads, P.smem));
         grid_t = std::min(P.nbands, occ * sms);
         // a smaller resident set than the ring was sized for could stall the back-pressure
         if (grid_t < P.nbands && team_ring(W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
@@ -665,6 +673,8 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space, co
         return solve_layout(W, H, g.Q, g.R, iters).end;
     case EDP_OP_SOLVE_IMAGES:
         return images_layout(W, H, g.Q, g.R, iters).end;
+    case EDP_OP_SCANLINE_MARGINALS:
+        return align_up(kHeader + (size_t)W * H * g.Q * 4) + align_up((size_t)W * H * g.Q * 4);
     case EDP_OP_COARSE: {
         CoarseGeometry c;
         if (coarse_geometry(W, H, space, &c)) return 0;
@@ -725,6 +735,51 @@ int edp_scanline_dp(const int32_t *C, int W, int H, const edp_label_space *space
     return launch_scanline(a, cfg.em, cfg.threads, cfg.smem, grid, st) ? EDP_ERR_CUDA : EDP_OK;
 }
 
+int edp_scanline_marginals(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,
+                           int32_t *labels, int32_t *marginals, void *ws, size_t ws_bytes, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if (!C || !labels || !ws || W < 1 || H < 1) return EDP_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
+    if (params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    if (ws_bytes < edp_workspace_size(EDP_OP_SCANLINE_MARGINALS, W, H, space, params)) return EDP_ERR_WORKSPACE;
+    // forward and backward sums stay below W * (cmax + R * lambda * g): their
+    // sum minus the cost fits int32
+    if ((long long)W * (params->cmax + (long long)g.R * cap_value(params)) >= (1LL << 29)) return EDP_ERR_RANGE;
+    if (params->lambda > (1 << 20)) return EDP_ERR_RANGE;
+    DpConfig cfg;
+    bool psm = false;
+    if ((rc = configure(g, H, true, W, 0, &psm, &cfg))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    int *F = reinterpret_cast<int *>(w + kHeader);
+    int *B = reinterpret_cast<int *>(w + align_up(kHeader + (size_t)W * H * g.Q * 4));
+    ScanArgs a;
+    memset(&a, 0, sizeof a);
+    a.C = C;
+    a.labels = labels;
+    a.W = W;
+    a.H = H;
+    a.Q = g.Q;
+    a.R = g.R;
+    for (int r = 0; r < 3; ++r) a.ax[r] = cfg.ax[r];
+    a.lam = params->lambda;
+    a.capv = (int)cap_value(params);
+    a.mode = params->prior_mode;
+    a.RB = cfg.RB;
+    a.no_ptr = 1;
+    const int grid = (H + cfg.RB - 1) / cfg.RB;
+    a.sums = F;
+    a.reverse = 0;
+    if (launch_scanline(a, cfg.em, cfg.threads, cfg.smem, grid, st)) return EDP_ERR_CUDA;
+    a.sums = B;
+    a.reverse = 1;
+    if (launch_scanline(a, cfg.em, cfg.threads, cfg.smem, grid, st)) return EDP_ERR_CUDA;
+    return launch_marginal_argmin(C, F, B, (long long)W * H, g.Q, labels, marginals, st) ? EDP_ERR_CUDA : EDP_OK;
+}
+
 int edp_solve(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,
               int32_t *labels, void *ws, size_t ws_bytes, edp_stream_t stream) {
     Geometry g;
@@ -733,7 +788,7 @@ int edp_solve(const int32_t *C, int W, int H, const edp_label_space *space, cons
     if ((rc = check_prior(params))) return rc;
     if (!C || !labels || !ws || W < 1 || H < 1 || params->iters < 1) return EDP_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
-    if (params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    // l1 = 2 (quadratic taps) is planned per kernel form; unsupported forms return EDP_ERR_UNSUPPORTED
     if (ws_bytes < edp_workspace_size(EDP_OP_SOLVE, W, H, space, params)) return EDP_ERR_WORKSPACE;
     if ((rc = check_range(W, H, g, params))) return rc;
     return run_solve(C, W, H, g, params, labels, static_cast<unsigned char *>(ws), (cudaStream_t)stream);
@@ -759,7 +814,7 @@ int edp_solve_images(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, in
     if ((rc = check_images(I0, I1, I2, W, H, pitch, space, params))) return rc;
     if (!labels || !ws || params->iters < 1) return EDP_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
-    if (params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    // l1 = 2 (quadratic taps) is planned per kernel form; unsupported forms return EDP_ERR_UNSUPPORTED
     if (ws_bytes < edp_workspace_size(EDP_OP_SOLVE_IMAGES, W, H, space, params)) return EDP_ERR_WORKSPACE;
     if ((rc = check_range(W, H, g, params))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -816,7 +871,7 @@ int check_problem(const edp_problem &pr, Geometry *g) {
     if ((rc = check_prior(&pr.params))) return rc;
     if ((rc = check_images(pr.I0, pr.I1, pr.I2, pr.W, pr.H, pr.pitch, &pr.space, &pr.params))) return rc;
     if (!pr.labels || pr.params.iters < 1) return EDP_ERR_INVALID_ARG;
-    if (pr.params.l1 != 1) return EDP_ERR_UNSUPPORTED;
+    // l1 = 2 (quadratic taps) is planned per kernel form; unsupported forms return EDP_ERR_UNSUPPORTED
     return check_range(pr.W, pr.H, *g, &pr.params);
 }
 
@@ -845,7 +900,7 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     // one block shape for the wave: 8 warps (one-axis bands of 8 rows, or
     // teams of the multi-axis body)
     const int threads = 256;
-    int lm = 9, gen = 0;
+    int quad = 0, gen = 0;
     size_t smem = 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -860,14 +915,11 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
         int rc = plan_solve(C, pr.W, pr.H, g, &pr.params, pr.labels, pws, &plans[k], threads);
         if (rc) return rc;
         off += problem_bytes(pr, g);
-        if (!plans[k].r1) {
-            if (plans[k].ta.lean)
-                lm = std::max(lm, plans[k].em);
-            else
-                gen = 1;
-        }
+        if (plans[k].r1 ? plans[k].o.l1 == 2 : plans[k].ta.l1 == 2) quad = 1;
+        if (!plans[k].r1 && !plans[k].ta.lean) gen = 1;
         smem = std::max(smem, plans[k].smem);
     }
+    const int lm = quad ? 2 : 33;  // batched build: quadratic-prior bodies only when needed
     const int occ = std::max(1, edp_batched_occupancy(lm, gen, threads, smem));
     // work items run problem by problem inside each pass: the largest problems
     // (longest wavefronts) first, so that small ones fill in behind them
@@ -1008,7 +1060,7 @@ int check_window(const edp_label_space *space, const edp_params *params, int win
     int rc = check_space(space, g);
     if (rc) return rc;
     if ((rc = check_prior(params))) return rc;
-    if (space->R > 2 || params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    if (space->R > 2) return EDP_ERR_UNSUPPORTED;
     if (win < 1 || (win & 1) == 0 || win > 15) return EDP_ERR_UNSUPPORTED;
     for (int r = 0; r < space->R; ++r)
         if (space->Q[r] < win) return EDP_ERR_INVALID_ARG;
@@ -1090,7 +1142,7 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
     a.mode = params->prior_mode;
     a.T = 1;
     int NT = g_tune_rb > 0 ? g_tune_rb : 8;
-    NT = std::max(1, std::min(NT, std::min(16, H)));
+    NT = std::max(1, std::min(NT, std::min(8, H)));  // the windowed builds take <= 256 threads
     a.nbuf = 3;
     a.kmb = 4;
     // (the windowed form always has the two transpose buffers: R = 2 in the size)
@@ -1100,17 +1152,19 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
     a.NT = NT;
     a.ring = team_ring(W, kResidentMin);
     a.win = win;
+    a.l1 = params->l1;
+    a.g = params->g;
     a.centre = centre;
     a.Q0w = space->Q[0];
     a.Q1w = space->Q[1];
-    a.em = 0;
+    a.em = params->l1;  // the windowed build of this prior power
     a.nbands = (H + NT - 1) / NT;
     a.spin_limit = 4000000;
     const int laps = (W + a.ring - 1) / a.ring;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int occ = std::max(1, edp_pass_team_occupancy(0, 0, 32 * NT, smem));
+    const int occ = std::max(1, edp_pass_team_occupancy(a.em, 0, 1, 32 * NT, smem));
     a.grid = std::min(a.nbands, occ * sms);
     if (a.grid < a.nbands && team_ring(W, a.grid) > a.ring) return EDP_ERR_UNSUPPORTED;
     if ((rc = cuda_status(cudaMemsetAsync(w, 0, L.ll + (size_t)a.nbands * a.ring * L.Qm * 8, st)))) return rc;

@@ -20,7 +20,9 @@ namespace edp {
 
 static_assert(sizeof(BatchArgs) <= 32000, "batch descriptors must fit the kernel parameter space");
 
-template <int LM, bool GEN>
+// LM: lean line bound; GEN: generic team body built in; QUAD: quadratic-prior
+// bodies built in (waves holding l1 = 2 problems)
+template <int LM, bool GEN, bool QUAD>
 __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -65,9 +67,14 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
             a.write_b = f.write_b;
             a.final_ = f.final_;
             a.tag = slot + 1;
-            ok = r1_dispatch(a.E, [&](auto e) {
-                return r1_band<decltype(e)::value>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
-            });
+            if (QUAD && a.l1 == 2)
+                ok = r1_dispatch(a.E, [&](auto e) {
+                    return r1_band<decltype(e)::value, QUAD>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+                });
+            else
+                ok = r1_dispatch(a.E, [&](auto e) {
+                    return r1_band<decltype(e)::value, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+                });
         } else {
             TeamArgs a = P.t;
             a.pass = pass;
@@ -78,7 +85,9 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
             a.final_ = f.final_;
             a.cons = P.cons + (size_t)slot * P.nbands;
             a.tag0 = 1 + slot * P.laps;
-            if (a.lean)
+            if (QUAD && a.lean && a.l1 == 2)
+                ok = team_band<QUAD ? 2 : LM, true>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+            else if (a.lean)
                 ok = team_band<LM, true>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
             else if constexpr (GEN)
                 ok = team_band<33, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
@@ -97,13 +106,15 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
     }
 }
 
-template <int LM, bool GEN>
+template <int LM, bool GEN, bool QUAD>
 static void *batched_kernel() {
-    return reinterpret_cast<void *>(edp_batched_kernel<LM, GEN>);
+    return reinterpret_cast<void *>(edp_batched_kernel<LM, GEN, QUAD>);
 }
 static void *batched_kernel_for(int lm, int gen) {
-    (void)lm;  // the lean body dispatches on the line lengths itself
-    return gen ? batched_kernel<33, true>() : batched_kernel<33, false>();
+    // lm: 2 = the wave holds quadratic-prior problems (the lean body
+    // dispatches on the line lengths itself otherwise)
+    if (lm == 2) return gen ? batched_kernel<33, true, true>() : batched_kernel<33, false, true>();
+    return gen ? batched_kernel<33, true, false>() : batched_kernel<33, false, false>();
 }
 
 int edp_batched_occupancy(int lm, int gen, int threads, size_t smem) {

@@ -4,7 +4,8 @@
 
 namespace edp {
 
-__global__ void __launch_bounds__(kMaxThreads) edp_pass_r1_kernel(PassR1Args A) {
+template <bool QUAD>
+__global__ void __launch_bounds__(QUAD ? 256 : kMaxThreads, 1) edp_pass_r1_kernel(PassR1Args A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
     __shared__ volatile int s_abort;
@@ -16,7 +17,8 @@ __global__ void __launch_bounds__(kMaxThreads) edp_pass_r1_kernel(PassR1Args A) 
         __syncthreads();
         const int band = s_band;
         if (band >= A.nbands) break;
-        const bool ok = r1_dispatch(A.E, [&](auto e) { return r1_band<decltype(e)::value>(A, band, smem_i, &s_abort); });
+        const bool ok =
+            r1_dispatch(A.E, [&](auto e) { return r1_band<decltype(e)::value, QUAD>(A, band, smem_i, &s_abort); });
         if (!ok) return;
     }
 }
@@ -27,9 +29,9 @@ size_t pass_r1_smem(int NWR, int E) {
 }
 
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st) {
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(edp_pass_r1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    edp_pass_r1_kernel<<<a.grid, threads, smem, st>>>(a);
+    auto k = a.l1 == 2 ? edp_pass_r1_kernel<true> : edp_pass_r1_kernel<false>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<a.grid, threads, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -5,7 +5,7 @@
 namespace edp {
 
 template <int EM, bool LEAN, bool WIN>
-__global__ void __launch_bounds__(WIN ? 512 : (LEAN || EM > 17 ? 256 : 384), 1) edp_pass_team_kernel(TeamArgs A) {
+__global__ void __launch_bounds__(WIN || LEAN || EM > 17 ? 256 : 384, 1) edp_pass_team_kernel(TeamArgs A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
     __shared__ volatile int s_abort;
@@ -30,14 +30,15 @@ static void *team_kernel() {
     return reinterpret_cast<void *>(edp_pass_team_kernel<EM, LEAN, WIN>);
 }
 static void *team_kernel_for(int em, int lean, int win = 0) {
-    if (win) return team_kernel<9, false, true>();  // the windowed body dispatches on the box side
+    // the windowed body dispatches on the box side; em is its prior power
+    if (win) return em == 2 ? team_kernel<2, false, true>() : team_kernel<1, false, true>();
     // the lean body dispatches on the line lengths itself: 9/17/33, or 65 only
-    if (lean) return em == 65 ? team_kernel<65, true>() : team_kernel<33, true>();
+    if (lean) return em == 2 ? team_kernel<2, true>() : (em == 65 ? team_kernel<65, true>() : team_kernel<33, true>());
     return em == 9 ? team_kernel<9, false>() : (em == 17 ? team_kernel<17, false>() : team_kernel<33, false>());
 }
 
-int edp_pass_team_occupancy(int em, int lean, int threads, size_t smem) {
-    void *k = team_kernel_for(em, lean, em == 0);
+int edp_pass_team_occupancy(int em, int lean, int win, int threads, size_t smem) {
+    void *k = team_kernel_for(em, lean, win);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);

@@ -50,6 +50,7 @@ struct TeamArgs {
     int W, H, Q, Qm, R;     // Qm: message stride, Q rounded up to a multiple of 4
     TeamAxis ax[3];
     int lam, capv, mode;    // mode 0 joint, 1 per axis truncation
+    int l1, g;              // prior power (1: linear sweeps, 2: quadratic taps, lean / windowed forms) and truncation
     int pass, read_c, read_d, write_a, write_b, final_;
     int T, NT;              // warps per team (one row), teams per block
     int nbuf, kmb, ring;    // staging buffers, mailbox slots, record ring columns
@@ -64,7 +65,7 @@ struct TeamArgs {
     unsigned long long *trace;  // optional: per band {start ns, end ns, 0, sm id}
 };
 int launch_edp_pass_team(const TeamArgs &a, int threads, size_t smem, cudaStream_t st);
-int edp_pass_team_occupancy(int em, int lean, int threads, size_t smem);
+int edp_pass_team_occupancy(int em, int lean, int win, int threads, size_t smem);
 size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb);
 
 // one EDP scan pass, one label axis, one warp per row (edp_pass_r1.cu)
@@ -78,6 +79,7 @@ struct PassR1Args {
     int W, H, Q, Qm, E, EMt; // Qm: message stride; E labels per lane
     int vw;                 // ints per prefetch copy (1, 2, 4): divides E and Q, aligned
     int lam, capv, kc;      // kc: lanes of carry in the truncated sweeps
+    int l1, g;              // prior power (1: linear sweeps, 2: quadratic taps) and truncation
     int pass, read_c, read_d, write_a, write_b, final_;
     int NWR;                // rows (warps) per block
     int nbands, grid, tag;
@@ -130,8 +132,14 @@ struct ScanArgs {
     AxisCfg ax[3];
     int lam, capv, mode;
     int RB;
+    int *sums;              // optional [H][W][Q]: S of every column (min-marginal mode)
+    int reverse;            // 1: the chain runs from column W-1 to 0
+    int no_ptr;             // 1: no back-pointers and no backtrack (min-marginal mode)
 };
 int launch_scanline(const ScanArgs &a, int em, int threads, size_t smem, int grid, cudaStream_t st);
+// S_Omega = F + B - C per pixel, lowest-index argmin (min-marginal mode)
+int launch_marginal_argmin(const int *C, const int *F, const int *B, long long npix, int Q, int *labels, int *marg,
+                           cudaStream_t st);
 
 // cost volume
 struct CostArgs {

@@ -135,6 +135,53 @@ __device__ __forceinline__ void dt_pair(int (&a)[E], int (&b)[E], int lane, int 
     }
 }
 
+// Truncated quadratic prior (l1 = 2, Eq. M_decmp: the generalized RMS): the
+// min-convolution of two row vectors a, b with lambda d^2 over the taps
+// |d| < g (farther sources cost at least the clip value lambda g^2 applied
+// afterwards).  The window slides one label per tap: every lane shifts its E
+// values and takes the boundary value from its neighbour lane.  Positions
+// past the vector hold kBig.
+template <int E>
+__device__ __forceinline__ void quad_pair(int (&a)[E], int (&b)[E], int lane, int lam, int g) {
+    int oa[E], ob[E], ua[E], ub[E], da[E], db[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        oa[i] = ua[i] = da[i] = a[i];
+        ob[i] = ub[i] = db[i] = b[i];
+    }
+    const int dmax = min(g, 32 * E);
+    for (int d = 1; d < dmax; ++d) {
+        // u: value at position p + d; v: value at position p - d
+        const int na = __shfl_down_sync(kFull, ua[0], 1), nb = __shfl_down_sync(kFull, ub[0], 1);
+        const int pa = __shfl_up_sync(kFull, da[E - 1], 1), pb = __shfl_up_sync(kFull, db[E - 1], 1);
+#pragma unroll
+        for (int i = 0; i < E - 1; ++i) {
+            ua[i] = ua[i + 1];
+            ub[i] = ub[i + 1];
+        }
+        ua[E - 1] = lane < 31 ? na : kBig;
+        ub[E - 1] = lane < 31 ? nb : kBig;
+#pragma unroll
+        for (int i = E - 1; i > 0; --i) {
+            da[i] = da[i - 1];
+            db[i] = db[i - 1];
+        }
+        da[0] = lane > 0 ? pa : kBig;
+        db[0] = lane > 0 ? pb : kBig;
+        const int w = lam * d * d;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            oa[i] = min(oa[i], min(ua[i], da[i]) + w);
+            ob[i] = min(ob[i], min(ub[i], db[i]) + w);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        a[i] = oa[i];
+        b[i] = ob[i];
+    }
+}
+
 // vector shared-memory load / store of a lane's E consecutive ints
 template <int E>
 __device__ __forceinline__ void lds_vec(const int *p, int (&v)[E]) {
@@ -177,7 +224,8 @@ __device__ __forceinline__ void sts_vec(int *p, const int (&v)[E]) {
 // One row band (NWR rows, one warp each) of one scan pass.  Every thread of
 // the block calls it with the same band; returns false when the pass was
 // aborted (a wait timed out).
-template <int E>
+// QUAD: the build for the truncated quadratic prior (l1 = 2).
+template <int E, bool QUAD = false>
 __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int *smem_i, volatile int *s_abort) {
     const int Q = A.Q, W = A.W, H = A.H, NWR = A.NWR;
     constexpr int Qp = 32 * E;  // padded vector length in shared memory
@@ -320,7 +368,10 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                 lb = min(lb, hb[i]);
             }
             const int ga = redux_min(la), gb = redux_min(lb);
-            dt_pair<E>(ha, hb, lane, A.lam, A.kc);
+            if constexpr (QUAD)
+                quad_pair<E>(ha, hb, lane, A.lam, A.g);
+            else
+                dt_pair<E>(ha, hb, lane, A.lam, A.kc);
             const int clipa = ga + A.capv, clipb = gb + A.capv;
 #pragma unroll
             for (int i = 0; i < E; ++i) {

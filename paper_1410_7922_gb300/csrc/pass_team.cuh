@@ -256,13 +256,43 @@ __device__ __forceinline__ int lean_dt_smem(int (&h)[L], int lam, int cl_add, bo
     return lmin;
 }
 
+// Truncated quadratic prior (l1 = 2, Eq. M_decmp, the generalized RMS) on a
+// whole line held by one lane: the input is first stored at ab + i * st4;
+// h[i] <- min over taps |d| < g of input[i + d] + lambda d^2 (farther sources
+// cost at least the clip lambda g^2), then the clip.  Returns the line minimum.
+template <int L>
+__device__ __forceinline__ int lean_quad(int (&h)[L], int lam, int g, int cl_add, bool per_axis, int cl_fixed,
+                                         unsigned ab, unsigned st4) {
+    int lmin = kBig;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        team::sts(ab + i * st4, h[i]);
+        lmin = min(lmin, h[i]);
+    }
+    const int dmax = min(g, L);
+    for (int d = 1; d < dmax; ++d) {
+        const int w = lam * d * d;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            int c = kBig;
+            if (i + d < L) c = team::lds(ab + (i + d) * st4);
+            if (i - d >= 0) c = min(c, team::lds(ab + (i - d) * st4));
+            h[i] = min(h[i], c + w);
+        }
+    }
+    const int cl = per_axis ? lmin + cl_add : cl_fixed;
+#pragma unroll
+    for (int i = 0; i < L; ++i) h[i] = min(h[i], cl);
+    return lmin;
+}
+
 // Phase 0 of one line of axis 0 (contiguous labels q0 .. q0 + L - 1): the
 // halved sums of Eq. DP_2D_base for vector `vsel` from the staged inputs,
 // the final-pass argmin key (vector a lanes), the sweeps; result into X.
-template <int L>
+template <int L, bool QUAD = false>
 __device__ __forceinline__ int lean_phase0(unsigned aC, unsigned aCc, unsigned aCd, unsigned aMa, unsigned aMb,
                                            unsigned aX, int q0, int vsel, bool final_a, bool per_axis, int lam,
-                                           int capv, unsigned long long &key) {
+                                           int capv, unsigned long long &key, int g) {
     const unsigned o = 4u * (unsigned)q0;
     int h[L];
     if (final_a) {
@@ -284,7 +314,9 @@ __device__ __forceinline__ int lean_phase0(unsigned aC, unsigned aCc, unsigned a
         }
     }
     int lmin;
-    if constexpr (L > 33)
+    if constexpr (QUAD)
+        lmin = lean_quad<L>(h, lam, g, capv, per_axis, kBig, aX + o, 4u);
+    else if constexpr (L > 33)
         lmin = lean_dt_smem<L>(h, lam, capv, per_axis, kBig, aX + o, 4u);
     else
         lmin = lean_dt<L>(h, lam, capv, per_axis, kBig);
@@ -302,14 +334,16 @@ struct LeanOut {
     int2 *pRec;            // record ring slot (null: none)
     int tag;
 };
-template <int L>
+template <int L, bool QUAD = false>
 __device__ __forceinline__ void lean_phase_r(unsigned aX, int qb, int st, bool last, int vsel, bool per_axis, int lam,
-                                             int capv, int gv, const LeanOut &O) {
+                                             int capv, int gv, const LeanOut &O, int g) {
     const unsigned o = aX + 4u * (unsigned)qb, st4 = 4u * (unsigned)st;
     int h[L];
 #pragma unroll
     for (int i = 0; i < L; ++i) h[i] = team::lds(o + i * st4);
-    if constexpr (L > 33)
+    if constexpr (QUAD)
+        lean_quad<L>(h, lam, g, capv, per_axis, last ? gv + capv : kBig, o, st4);
+    else if constexpr (L > 33)
         lean_dt_smem<L>(h, lam, capv, per_axis, last ? gv + capv : kBig, o, st4);
     else
         lean_dt<L>(h, lam, capv, per_axis, last ? gv + capv : kBig);
@@ -343,8 +377,10 @@ __device__ __forceinline__ void lean_phase_r(unsigned aX, int qb, int st, bool l
 // lean line lengths
 __host__ __device__ inline bool lean_length(int L) { return L == 9 || L == 17 || L == 33 || L == 65; }
 
-// EM: labels-per-lane bound (generic form) or line-length bound (LEAN).
-// WIN: EDP on per-pixel label boxes (windowed form, one warp per row).
+// EM: labels-per-lane bound (generic form) or line-length bound (LEAN: 33
+// serves 9/17/33, 65 serves 65, 2 is the quadratic-prior build for all).
+// WIN: EDP on per-pixel label boxes (windowed form, one warp per row); EM is
+// then the prior power l1 of the build (1 linear sweeps, 2 quadratic taps).
 template <int EM, bool LEAN, bool WIN = false>
 __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int *smem, volatile int *s_abort) {
     using namespace team;
@@ -625,8 +661,13 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             const int lam = A.lam, capv = A.capv;
             auto m0 = [&](int i0, int i1, int s0, int s1) {
                 const int a0 = lo0 + i0, a1 = lo1 + i1;
-                const int e0 = max(0, max(s0 - a0, a0 - (s0 + N - 1)));
-                const int e1 = R == 2 ? max(0, max(s1 - a1, a1 - (s1 + N - 1))) : 0;
+                // distances beyond g are clipped anyway (and must not overflow)
+                int e0 = min(A.g, max(0, max(s0 - a0, a0 - (s0 + N - 1))));
+                int e1 = R == 2 ? min(A.g, max(0, max(s1 - a1, a1 - (s1 + N - 1)))) : 0;
+                if (A.l1 == 2) {  // f(u) = u^2
+                    e0 *= e0;
+                    e1 *= e1;
+                }
                 return per_axis ? min(lam * e0, capv) + min(lam * e1, capv) : min(lam * (e0 + e1), capv);
             };
             auto body = [&](auto nc) -> bool {
@@ -650,30 +691,44 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                         hv[i] = floor_half(v ? t + c - d : t + d - c);
                         lmin0 = min(lmin0, hv[i]);
                     }
-                    int sw = hv[NN - 1];
-                    bv[NN - 1] = sw;
-#pragma unroll
-                    for (int i = NN - 2; i >= 0; --i) {
-                        sw = min(hv[i], sw + lam);
-                        bv[i] = sw;
-                    }
-                    int f = hv[0];
-                    hv[0] = min(f, bv[0]);
-#pragma unroll
-                    for (int i = 1; i < NN; ++i) {
-                        f = min(hv[i], f + lam);
-                        hv[i] = min(f, bv[i]);
-                    }
-                    // values at the target box's coordinates t: source position
-                    // u = t + d0 clamped to the line, plus lambda per label beyond it
                     const int cl = (R == 1 || per_axis) ? lmin0 + capv : kBig;
                     const unsigned ax = aX + 4u * (unsigned)qb;
+                    if constexpr (EM == 2) {  // windowed build for the quadratic prior
+                        // quadratic taps |u - (t + d0)| < g between the boxes
 #pragma unroll
-                    for (int i = 0; i < NN; ++i) sts(ax + 4u * i, hv[i]);
+                        for (int tt = 0; tt < NN; ++tt) {
+                            int o = kBig;
 #pragma unroll
-                    for (int tt = 0; tt < NN; ++tt) {
-                        const int u = min(max(tt + d0, 0), NN - 1);
-                        bv[tt] = min(lds(ax + 4u * (unsigned)u) + lam * abs(tt + d0 - u), cl);
+                            for (int u = 0; u < NN; ++u) {
+                                const int dd = u - tt - d0;
+                                if (abs(dd) < A.g) o = min(o, hv[u] + lam * dd * dd);
+                            }
+                            bv[tt] = min(o, cl);
+                        }
+                    } else {
+                        int sw = hv[NN - 1];
+                        bv[NN - 1] = sw;
+#pragma unroll
+                        for (int i = NN - 2; i >= 0; --i) {
+                            sw = min(hv[i], sw + lam);
+                            bv[i] = sw;
+                        }
+                        int f = hv[0];
+                        hv[0] = min(f, bv[0]);
+#pragma unroll
+                        for (int i = 1; i < NN; ++i) {
+                            f = min(hv[i], f + lam);
+                            hv[i] = min(f, bv[i]);
+                        }
+                        // values at the target box's coordinates t: source position
+                        // u = t + d0 clamped to the line, plus lambda per label beyond it
+#pragma unroll
+                        for (int i = 0; i < NN; ++i) sts(ax + 4u * i, hv[i]);
+#pragma unroll
+                        for (int tt = 0; tt < NN; ++tt) {
+                            const int u = min(max(tt + d0, 0), NN - 1);
+                            bv[tt] = min(lds(ax + 4u * (unsigned)u) + lam * abs(tt + d0 - u), cl);
+                        }
                     }
                     if (R == 1) {
                         // m_a of this column is still being read by the S_b lane
@@ -703,28 +758,41 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                         hv[i] = lds(aX + 4u * (unsigned)(l + NN * i));
                         lmin = min(lmin, hv[i]);
                     }
-                    int sw = hv[NN - 1];
-                    bv[NN - 1] = sw;
-#pragma unroll
-                    for (int i = NN - 2; i >= 0; --i) {
-                        sw = min(hv[i], sw + lam);
-                        bv[i] = sw;
-                    }
-                    int f = hv[0];
-                    hv[0] = min(f, bv[0]);
-#pragma unroll
-                    for (int i = 1; i < NN; ++i) {
-                        f = min(hv[i], f + lam);
-                        hv[i] = min(f, bv[i]);
-                    }
                     const int cl = (per_axis ? lmin : (v == 0 ? vma : vmb)) + capv;
                     const unsigned ax = aX + 4u * (unsigned)l;
+                    if constexpr (EM == 2) {  // windowed build for the quadratic prior
 #pragma unroll
-                    for (int i = 0; i < NN; ++i) sts(ax + 4u * (unsigned)(NN * i), hv[i]);
+                        for (int tt = 0; tt < NN; ++tt) {
+                            int o = kBig;
 #pragma unroll
-                    for (int tt = 0; tt < NN; ++tt) {
-                        const int u = min(max(tt + d1, 0), NN - 1);
-                        bv[tt] = min(lds(ax + 4u * (unsigned)(NN * u)) + lam * abs(tt + d1 - u), cl);
+                            for (int u = 0; u < NN; ++u) {
+                                const int dd = u - tt - d1;
+                                if (abs(dd) < A.g) o = min(o, hv[u] + lam * dd * dd);
+                            }
+                            bv[tt] = min(o, cl);
+                        }
+                    } else {
+                        int sw = hv[NN - 1];
+                        bv[NN - 1] = sw;
+#pragma unroll
+                        for (int i = NN - 2; i >= 0; --i) {
+                            sw = min(hv[i], sw + lam);
+                            bv[i] = sw;
+                        }
+                        int f = hv[0];
+                        hv[0] = min(f, bv[0]);
+#pragma unroll
+                        for (int i = 1; i < NN; ++i) {
+                            f = min(hv[i], f + lam);
+                            hv[i] = min(f, bv[i]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < NN; ++i) sts(ax + 4u * (unsigned)(NN * i), hv[i]);
+#pragma unroll
+                        for (int tt = 0; tt < NN; ++tt) {
+                            const int u = min(max(tt + d1, 0), NN - 1);
+                            bv[tt] = min(lds(ax + 4u * (unsigned)(NN * u)) + lam * abs(tt + d1 - u), cl);
+                        }
                     }
                     if (v == 0) {
 #pragma unroll
@@ -768,14 +836,14 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
 #pragma unroll 1
                 for (int li = lv; li < nl; li += NLV) {
                     int lm;
-                    if constexpr (EM >= 65) {
-                        lm = lean_phase0<65>(aC, aCc, aCd, aMa, aMb, aX, li * 65, vsel, final_a, per_axis, lam, A.capv, key);
+                    if (EM >= 65 || (EM == 2 && L == 65)) {
+                        lm = lean_phase0<65, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 65, vsel, final_a, per_axis, lam, A.capv, key, A.g);
                     } else if (L == 33)
-                        lm = lean_phase0<33>(aC, aCc, aCd, aMa, aMb, aX, li * 33, vsel, final_a, per_axis, lam, A.capv, key);
+                        lm = lean_phase0<33, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 33, vsel, final_a, per_axis, lam, A.capv, key, A.g);
                     else if (L == 17)
-                        lm = lean_phase0<17>(aC, aCc, aCd, aMa, aMb, aX, li * 17, vsel, final_a, per_axis, lam, A.capv, key);
+                        lm = lean_phase0<17, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 17, vsel, final_a, per_axis, lam, A.capv, key, A.g);
                     else
-                        lm = lean_phase0<9>(aC, aCc, aCd, aMa, aMb, aX, li * 9, vsel, final_a, per_axis, lam, A.capv, key);
+                        lm = lean_phase0<9, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 9, vsel, final_a, per_axis, lam, A.capv, key, A.g);
                     vmin = min(vmin, lm);
                 }
             }
@@ -799,14 +867,14 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
 #pragma unroll 1
                     for (int li = lv; li < Xr.nlines; li += NLV) {
                         const int qb = line_first(Xr, li);
-                        if constexpr (EM >= 65)
-                            lean_phase_r<65>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
+                        if (EM >= 65 || (EM == 2 && Xr.L == 65))
+                            lean_phase_r<65, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O, A.g);
                         else if (Xr.L == 33)
-                            lean_phase_r<33>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
+                            lean_phase_r<33, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O, A.g);
                         else if (Xr.L == 17)
-                            lean_phase_r<17>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
+                            lean_phase_r<17, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O, A.g);
                         else
-                            lean_phase_r<9>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O);
+                            lean_phase_r<9, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O, A.g);
                     }
                 }
             }

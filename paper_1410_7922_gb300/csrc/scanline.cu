@@ -11,6 +11,13 @@
 // the back-pointers (Sec. 4.1, Fig. 6a).
 //
 // A block owns RB rows and advances them together, one column per step.
+//
+// Min-marginal mode (the modified DP of Eq. DP_1D_3): the forward sums F and
+// the backward sums B (the same recurrence run from the right end) of every
+// column are stored; S_Omega(x) = M(F(x-1)) + C(x) + M(B(x+1)) = F(x) + B(x)
+// - C(x), and the label is its lowest-index argmin.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -41,11 +48,16 @@ __global__ void __launch_bounds__(kMaxThreads) scanline_kernel(ScanArgs A) {
 
     for (int i = tid; i < 2 * RB; i += blockDim.x) gkey[i] = kBigKey;
 
+    auto xe = [&](int x) { return A.reverse ? W - 1 - x : x; };  // column of chain step x
+    auto put_sum = [&](int w, int x, int q, int v) {
+        if (A.sums) A.sums[((size_t)(r0 + w) * W + xe(x)) * Q + q] = v;
+    };
     auto ptr_index = [&](int w, int x, int q) -> size_t {
         return A.ptr_in_smem ? ((size_t)w * W + x) * Q + q : ((size_t)(r0 + w) * W + x) * Q + q;
     };
     unsigned char *pbase = A.ptr_in_smem ? sptr : reinterpret_cast<unsigned char *>(A.ptr);
     auto put_ptr = [&](int w, int x, int q, unsigned v) {
+        if (A.no_ptr) return;
         const size_t idx = ptr_index(w, x, q);
         if (A.ptr_bytes == 1)
             pbase[idx] = (unsigned char)v;
@@ -68,7 +80,7 @@ __global__ void __launch_bounds__(kMaxThreads) scanline_kernel(ScanArgs A) {
                 if (gi >= ngroups0) continue;
                 const int w = gi / a0.nlines, l = gi % a0.nlines;
                 const int base = line_base(a0, l);
-                const size_t gpix = ((size_t)(r0 + w) * W + x) * Q;
+                const size_t gpix = ((size_t)(r0 + w) * W + xe(x)) * Q;
 #pragma unroll
                 for (int i = 0; i < EM; ++i) {
                     const int p = j0 * a0.E + i;
@@ -99,7 +111,10 @@ __global__ void __launch_bounds__(kMaxThreads) scanline_kernel(ScanArgs A) {
 #pragma unroll
                     for (int i = 0; i < EM; ++i) {
                         const int p = j0 * a0.E + i;
-                        if (i < a0.E && p < a0.L) Sv[w0 * Q + base0 + p] = cx[base0 + p];
+                        if (i < a0.E && p < a0.L) {
+                            Sv[w0 * Q + base0 + p] = cx[base0 + p];
+                            put_sum(w0, 0, base0 + p, cx[base0 + p]);
+                        }
                     }
                 }
                 continue;
@@ -122,6 +137,7 @@ __global__ void __launch_bounds__(kMaxThreads) scanline_kernel(ScanArgs A) {
                         const int q = base0 + p;
                         const long long o = min(k[i], lmin + cap_k);
                         Sv[w0 * Q + q] = cx[q] + (int)(o >> 32);
+                        put_sum(w0, x, q, cx[q] + (int)(o >> 32));
                         put_ptr(w0, x, q, (unsigned)(o & 0xffffffffLL));
                     }
                 }
@@ -171,6 +187,7 @@ __global__ void __launch_bounds__(kMaxThreads) scanline_kernel(ScanArgs A) {
                             const long long o = min(k[i], clip);
                             if (last_axis) {
                                 Sv[w * Q + q] = cx[q] + (int)(o >> 32);
+                                put_sum(w, x, q, cx[q] + (int)(o >> 32));
                                 put_ptr(w, x, q, (unsigned)(o & 0xffffffffLL));
                             } else {
                                 tmpk[w * Q + q] = o;
@@ -183,6 +200,7 @@ __global__ void __launch_bounds__(kMaxThreads) scanline_kernel(ScanArgs A) {
         }
     }
     cp_async_wait_0();
+    if (A.no_ptr) return;  // min-marginal mode: the sums are the output
     // ---- argmin of S(W-1), lowest index on ties ----
     for (int i = tid; i < RB; i += blockDim.x) gkey[i * 2 + 0] = kBigKey;
     __syncthreads();
@@ -219,6 +237,36 @@ __global__ void __launch_bounds__(kMaxThreads) scanline_kernel(ScanArgs A) {
             A.labels[(size_t)y * W + x - 1] = (int)lab;
         }
     }
+}
+
+// S_Omega = F + B - C and its lowest-index argmin, one warp per pixel.
+__global__ void marginal_argmin_kernel(const int *C, const int *F, const int *B, long long npix, int Q, int *labels,
+                                       int *marg) {
+    const int lane = threadIdx.x & 31;
+    for (long long pix = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; pix < npix;
+         pix += (long long)gridDim.x * blockDim.x / 32) {
+        const size_t o = (size_t)pix * Q;
+        int best = 0x7fffffff, bq = 0x7fffffff;
+        for (int q = lane; q < Q; q += 32) {
+            const int v = F[o + q] + B[o + q] - C[o + q];
+            if (marg) marg[o + q] = v;
+            if (v < best) {
+                best = v;
+                bq = q;
+            }
+        }
+        const int vb = __reduce_min_sync(0xffffffffu, best);
+        const int qb = __reduce_min_sync(0xffffffffu, best == vb ? bq : 0x7fffffff);
+        if (lane == 0) labels[pix] = qb;
+    }
+}
+
+int launch_marginal_argmin(const int *C, const int *F, const int *B, long long npix, int Q, int *labels, int *marg,
+                           cudaStream_t st) {
+    long long blocks = (npix * 32 + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    marginal_argmin_kernel<<<(unsigned)std::max(1LL, blocks), 256, 0, st>>>(C, F, B, npix, Q, labels, marg);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 int launch_scanline(const ScanArgs &a, int em, int threads, size_t smem, int grid, cudaStream_t st) {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libedp.so")
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_RANGE, ERR_TIMEOUT, ERR_CUDA = range(7)
 PRIOR = {"joint": 0, "per_axis": 1}
 COST = {"pair": 0, "pair_stereo3": 1, "composite": 2}
-OP_SCANLINE_DP, OP_SOLVE, OP_SOLVE_IMAGES, OP_COARSE = 1, 2, 3, 4
+OP_SCANLINE_DP, OP_SOLVE, OP_SOLVE_IMAGES, OP_COARSE, OP_SCANLINE_MARGINALS = 1, 2, 3, 4, 5
 
 
 class EdpError(RuntimeError):
@@ -71,6 +71,7 @@ def load() -> ctypes.CDLL:
         "edp_cost_volume": ([P, P, P, I, I, I, LS, PR, P, P], I),
         "edp_scanline_dp": ([P, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_solve": ([P, I, I, LS, PR, P, P, SZ, P], I),
+        "edp_scanline_marginals": ([P, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_energy": ([P, P, I, I, LS, PR, P, P], I),
         "edp_solve_images": ([P, P, P, I, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_solve_images_host": ([P, P, P, I, I, LS, PR, P, P, P, SZ, P], I),
@@ -110,7 +111,7 @@ def exported_symbols() -> list[str]:
             "edp_solve_batched", "edp_workspace_size_windowed", "edp_cost_window", "edp_solve_windowed",
             "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_forward", "edp_net_backward",
             "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc", "edp_coarse_labels",
-            "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets"]
+            "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_scanline_marginals"]
 
 
 def status_string(code: int) -> str:
@@ -255,6 +256,24 @@ def scanline_dp(C, space: dict, prior: dict, ws=None, labels=None, row_energy=No
                                 _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
     _check(rc, "scanline_dp")
     return labels, row_energy
+
+
+def scanline_marginals(C, space: dict, prior: dict, ws=None, labels=None, marginals=False, stream=None):
+    """edp_scanline_marginals: labels int32 [H][W] (argmin of the min-marginals),
+    and the marginals int32 [H][W][Q] when marginals=True."""
+    H, W, Q = C.shape
+    if ws is None:
+        ws = workspace(OP_SCANLINE_MARGINALS, W, H, space, prior, device=C.device)
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=C.device)
+    marg = torch.empty((H, W, Q), dtype=torch.int32, device=C.device) if marginals else None
+    ls, pr = label_space(space), params(prior)
+    rc = load().edp_scanline_marginals(_dev(C, torch.int32, "C"), W, H, ctypes.byref(ls), ctypes.byref(pr),
+                                       _dev(labels, torch.int32, "labels"),
+                                       _dev(marg, torch.int32, "marginals") if marginals else None,
+                                       _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(rc, "scanline_marginals")
+    return (labels, marg) if marginals else labels
 
 
 def solve(C, space: dict, prior: dict, iters: int = 1, ws=None, labels=None, stream=None):

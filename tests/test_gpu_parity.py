@@ -110,6 +110,23 @@ def test_scanline_random(edp_lib, Q, mode):
         assert np.array_equal(host(glab), lab), prior
 
 
+@pytest.mark.parametrize("Q,mode", [((16,), "joint"), ((64,), "joint"), ((130,), "joint"), ((5, 4), "per_axis"),
+                                    ((9, 9), "joint"), ((3, 4, 3), "per_axis")])
+def test_scanline_min_marginals(edp_lib, Q, mode):
+    """Min-marginal mode (Eq. DP_1D_3): S_Omega = M(F(x-1)) + C + M(B(x+1)) and
+    its lowest-index argmin against the oracle, on random and tie-heavy costs."""
+    rng = np.random.default_rng(sum(Q) * 3 + len(mode))
+    n = int(np.prod(Q))
+    H, W = 13, 29
+    for hi in (21, 3):
+        C = rng.integers(0, hi, size=(H, W, n)).astype(np.int32)
+        prior = {"lam": int(rng.integers(0, 9)), "g": int(rng.integers(1, 5)), "l1": 1, "mode": mode}
+        S = oracle.min_marginals(C, sp(Q), prior, tier=1)
+        lab, marg = edp_lib.scanline_marginals(dev(C), sp(Q), prior, marginals=True)
+        assert np.array_equal(host(marg).astype(np.int64), S), prior
+        assert np.array_equal(host(lab), np.argmin(S, axis=2)), prior
+
+
 @pytest.mark.parametrize("rb,e", [(1, 1), (3, 2), (7, 3), (2, 8), (5, 16)])
 def test_scanline_launch_shapes(edp_lib, rb, e):
     rng = np.random.default_rng(rb * 10 + e)
@@ -170,6 +187,35 @@ def test_edp_sixteen_iterations(edp_lib, Q, mode):
     prior = {"lam": 7, "g": 3, "l1": 1, "mode": mode}
     want, got = run_edp(edp_lib, C, sp(Q), prior, 16)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("Q,mode", [((7,), "joint"), ((64,), "joint"), ((100,), "joint"), ((9, 9), "joint"),
+                                    ((9, 9), "per_axis"), ((17, 9), "per_axis"), ((33, 33), "joint"),
+                                    ((17, 17, 9), "per_axis"), ((65, 65), "per_axis")])
+@pytest.mark.parametrize("g", [1, 2, 3, 5])
+def test_edp_quadratic_prior(edp_lib, Q, mode, g):
+    """Truncated quadratic prior (l1 = 2, the generalized RMS of Eq. M_decmp)
+    against the oracle's GRMS tier."""
+    rng = np.random.default_rng(sum(Q) * 7 + g)
+    n = int(np.prod(Q))
+    H, W = (6, 9) if n > 500 else (13, 17)
+    C = rng.integers(0, 30, size=(H, W, n)).astype(np.int32)
+    prior = {"lam": int(rng.integers(1, 6)), "g": g, "l1": 2, "mode": mode}
+    for iters in (1, 2):
+        want, got = run_edp(edp_lib, C, sp(Q), prior, iters)
+        assert np.array_equal(got, want), (prior, iters)
+
+
+def test_quadratic_prior_unsupported_shapes(edp_lib):
+    """Lines the quadratic taps are not built for say so."""
+    C = torch.zeros((4, 5, 20), dtype=torch.int32, device="cuda")
+    prior = {"lam": 2, "g": 3, "l1": 2, "mode": "joint"}
+    with pytest.raises(edp_lib.EdpError) as e:
+        edp_lib.solve(C, sp((5, 4)), prior)
+    assert e.value.code == edp_lib.ERR_UNSUPPORTED
+    with pytest.raises(edp_lib.EdpError) as e:
+        edp_lib.scanline_dp(C, sp((20,)), prior)
+    assert e.value.code == edp_lib.ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 50), (50, 3)])
@@ -300,8 +346,9 @@ def test_range_and_argument_errors(edp_lib):
     with pytest.raises(edp_lib.EdpError) as ei:
         edp_lib.solve(C, sp((8,)), {"lam": 2**21, "g": 1, "l1": 1, "mode": "joint"})
     assert ei.value.code == edp_lib.ERR_RANGE
-    with pytest.raises(edp_lib.EdpError) as ei:
-        edp_lib.solve(C, sp((8,)), {"lam": 1, "g": 2, "l1": 2, "mode": "joint"})
+    with pytest.raises(edp_lib.EdpError) as ei:  # quadratic taps: not built for 5 x 4 lines
+        edp_lib.solve(torch.zeros((4, 4, 20), dtype=torch.int32, device="cuda"), sp((5, 4)),
+                      {"lam": 1, "g": 2, "l1": 2, "mode": "joint"})
     assert ei.value.code == edp_lib.ERR_UNSUPPORTED
     ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
     with pytest.raises(edp_lib.EdpError) as ei:
@@ -371,10 +418,12 @@ def test_batched_waves_and_replay(edp_lib):
 # windowed EDP (per-pixel label boxes)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("Q,win,mode", [((13, 13), 5, "per_axis"), ((13, 13), 5, "joint"), ((11, 9), 9, "per_axis"),
-                                        ((20,), 7, "joint"), ((9, 9), 9, "joint"), ((17, 17), 15, "per_axis")])
+@pytest.mark.parametrize("Q,win,mode,l1", [((13, 13), 5, "per_axis", 1), ((13, 13), 5, "joint", 1),
+                                           ((11, 9), 9, "per_axis", 1), ((20,), 7, "joint", 1), ((9, 9), 9, "joint", 1),
+                                           ((17, 17), 15, "per_axis", 1), ((13, 13), 5, "per_axis", 2),
+                                           ((13, 13), 7, "joint", 2), ((20,), 7, "joint", 2), ((17, 17), 9, "per_axis", 2)])
 @pytest.mark.parametrize("iters", [1, 2])
-def test_windowed_matches_oracle(edp_lib, Q, win, mode, iters):
+def test_windowed_matches_oracle(edp_lib, Q, win, mode, l1, iters):
     rng = np.random.default_rng(sum(Q) * 10 + win + iters)
     H, W = 15, 21
     R = len(Q)
@@ -383,7 +432,7 @@ def test_windowed_matches_oracle(edp_lib, Q, win, mode, iters):
     I1 = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
     # centres: a smooth field plus jumps, some outside the valid range (clamped)
     centre = np.stack([rng.integers(-2, q + 2, size=(H, W)) for q in Q], axis=-1).astype(np.int32)
-    prior = {"lam": int(rng.integers(2, 9)), "g": 3, "l1": 1, "mode": mode}
+    prior = {"lam": int(rng.integers(2, 9)), "g": 3, "l1": l1, "mode": mode}
     Cw = oracle.cost_window(I0, I1, None, space, 1, 30, centre, win)
     gCw = edp_lib.cost_window(dev(I0), dev(I1), None, space, 1, 30, dev(centre), win)
     assert np.array_equal(host(gCw), Cw)
