@@ -113,6 +113,23 @@ def pass_units(pass_idx: int, it: int, iters: int) -> tuple[int, bool]:
     return 1 + read_c + read_d + write_a + write_b, (pass_idx == 3 and last)
 
 
+def launch_bytes(nlaunch: int, W: int, H: int, Q: int, iters: int) -> list[int]:
+    """Algorithmic bytes of each scan-pass launch of one solve: one pass per
+    launch (4 per iteration), or a paired sweep P1 + P2 / P3 + P4 (2 per
+    iteration), which moves the bytes of both its passes."""
+    per_it = nlaunch // iters
+    out = []
+    for i in range(nlaunch):
+        it, k = divmod(i, per_it)
+        passes = (2 * k, 2 * k + 1) if per_it == 2 else (k,)
+        b = 0
+        for p in passes:
+            units, lab = pass_units(p, it, iters)
+            b += units * W * H * Q * 4 + (W * H * 4 if lab else 0)
+        out.append(b)
+    return out
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -319,13 +336,13 @@ def time_solve_rows(edp, synth, torch):
     H, W, Q = C.shape
     ws = edp.workspace(edp.OP_SOLVE, W, H, w["space"], w["prior"], 1)
     lab = torch.empty((H, W), dtype=torch.int32, device="cuda")
-    evs = [ev() for _ in range(8)]
+    nl = edp.pass_launches(w["space"], 1)
+    evs = [ev() for _ in range(2 * nl)]
     edp.set_profile_events(evs)
     ms = timed(lambda: edp.solve(C, w["space"], w["prior"], iters=1, ws=ws, labels=lab), reps=10)
-    pass_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(4)]
+    pass_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(nl)]
     edp.set_profile_events(None)
-    nbytes = sum(pass_units(p, 0, 1)[0] * W * H * Q * 4 + (W * H * 4 if pass_units(p, 0, 1)[1] else 0)
-                 for p in range(4))
+    nbytes = sum(launch_bytes(nl, W, H, Q, 1))
     rows["edp_motion_320x240_Q33x33"] = {
         "ms": ms, "updates_per_s": W * H * Q * 9 / (ms * 1e-3), "pass_ms": pass_ms,
         "pass_gbs": nbytes / (sum(pass_ms) * 1e-3) / 1e9}
@@ -465,7 +482,7 @@ def run_gpu(args, world, rank, local):
     labels = torch.empty((H, W), dtype=torch.int32, device=dev)
     energy4 = torch.empty(4, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
-    npass = 4 * j
+    npass = edp.pass_launches(space, j)  # scan-pass launches per solve
     pev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * npass)]
 
     def step():
@@ -517,10 +534,7 @@ def run_gpu(args, world, rank, local):
     value = updates * world * args.steps / (total_ms * 1e-3)
 
     # roofline of the dominant kernel (the scan pass): algorithmic bytes / time
-    nbytes = 0
-    for i in range(npass):
-        units, lab = pass_units(i % 4, i // 4, j)
-        nbytes += units * W * H * Q * 4 + (W * H * 4 if lab else 0)
+    nbytes = sum(launch_bytes(npass, W, H, Q, j))
     pass_total_s = sum(pass_ms) * 1e-3 / args.steps
     achieved = nbytes / pass_total_s / 1e9
     peak, peak_kind = measured_peaks()
@@ -529,6 +543,7 @@ def run_gpu(args, world, rank, local):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
                 "bytes_per_launch_avg": nbytes / npass, "launch_ms_avg": sum(pass_ms) / args.steps / npass,
+                "launches_per_solve": npass, "schedule": "paired sweeps" if npass == 2 * j else "one pass per launch",
                 "pass_ms": [p / args.steps for p in pass_ms]}
 
     # end to end through the host-buffer C call (copies inside the timed region)

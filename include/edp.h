@@ -135,19 +135,38 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
  * Not thread-safe with concurrent solves. */
 int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, int general_kernel);
 
-/* Per-pass timing hook: while set, edp_solve (and edp_solve_images) record
+/* Pass schedule of edp_solve, edp_solve_images and edp_solve_windowed
+ * (Sec. 4.2: P1..P4 per iteration).  on = 1 (the default): P1 and P2, and
+ * P3 and P4, which share their vertical direction, run as one paired sweep
+ * each (two launches per iteration; each row sweeps left to right, then
+ * right to left, so the second pass starts on a row as soon as the first has
+ * finished it).  on = 0: one launch per pass.  Results never depend on it
+ * (edp_solve_batched always runs one pass per work item).  Returns
+ * EDP_ERR_INVALID_ARG unless on is 0 or 1.  Not thread-safe with concurrent
+ * solves. */
+int edp_set_pass_pairs(int on);
+
+/* Number of scan-pass launches edp_solve makes for `iters` iterations on a
+ * label space of R axes and Q labels under the current schedule: 2 * iters
+ * for paired sweeps, else 4 * iters (0 if iters, R or Q is below 1). */
+int edp_pass_launches(int R, int Q, int iters);
+
+/* Per-launch timing hook: while set, edp_solve (and edp_solve_images) record
  * events[2*i] / events[2*i + 1] (cudaEvent_t handles created by the caller)
- * on the solve's stream immediately before / after the launch of scan pass
- * i (i = 4 * iteration + pass), for i < n_events / 2.  NULL / 0 disables.
+ * on the solve's stream immediately before / after scan-pass launch i
+ * (i counts the launches of one solve in order: 4 * iteration + pass, or
+ * 2 * iteration + pair for paired sweeps), for i < n_events / 2.  NULL / 0
+ * disables.
  * The library keeps the pointer, not a copy: the array must outlive the
  * solves that use it. */
 int edp_set_profile_events(void *const *events, int n_events);
 
-/* Per-band trace of the scan passes (tracing hook): while set, pass i of a
- * solve writes, for every row band b, four uint64 at
- * device_buffer[(i * nbands + b) * 4 ...]: start and end %globaltimer (ns),
- * ns spent waiting for the previous band, and the SM id.  Passes whose
- * record would not fit in `bytes` are not traced.  NULL / 0 disables. */
+/* Per-band trace of the scan passes (tracing hook): while set, scan-pass
+ * launch i of a solve (counted as for edp_set_profile_events) writes, for
+ * every row band b, four uint64 at device_buffer[(i * nbands + b) * 4 ...]:
+ * start and end %globaltimer (ns), ns spent waiting for the previous band,
+ * and the SM id.  Launches whose record would not fit in `bytes` are not
+ * traced.  NULL / 0 disables. */
 int edp_set_trace(void *device_buffer, size_t bytes);
 
 /* Cost volume (DSI), Eq. Cost_value (Algorithm 1, step 1).

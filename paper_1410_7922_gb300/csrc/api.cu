@@ -23,6 +23,7 @@ int g_tune_e = 0;        // labels per lane target override, scanline DP (0 = au
 int g_tune_t = 0;        // warps per row override, multi-axis scan pass (0 = automatic)
 int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass kernel
 int g_generic_team = 0;  // 1: multi-axis problems take the generic team body (tests)
+int g_pass_pairs = 1;    // 1: P1 + P2 and P3 + P4 run as paired sweeps (one launch each)
 void *const *g_prof_events = nullptr;  // optional per-pass events (profiling hook)
 int g_prof_n = 0;
 unsigned long long *g_trace = nullptr;  // optional per-band trace buffer (device)
@@ -185,8 +186,9 @@ SolveLayout solve_layout(int W, int H, int Q, int R, int iters) {
     L.cons = kHeader;
     L.counters = align_up(L.cons + npass * H * 4);
     L.ll = align_up(L.counters + npass * 4);
-    const size_t r1 = (R == 1 && Q <= 256) ? (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * W * Q * 8 : 0;
-    const size_t tm = (size_t)H * team_ring(W, kResidentMin) * L.Qm * 8;
+    // one-axis kernel: a record per column of a paired sweep (2W) for every band boundary
+    const size_t r1 = (R == 1 && Q <= 256) ? (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * 2 * W * Q * 8 : 0;
+    const size_t tm = (size_t)H * team_ring(2 * W, kResidentMin) * L.Qm * 8;  // paired sweeps: 2W columns
     L.ll_bytes = std::max(r1, tm);
     size_t off = align_up(L.ll + L.ll_bytes);
     for (int k = 0; k < 4; ++k) {
@@ -298,8 +300,10 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         const int E = (g.Q + 31) / 32;
         int NWR = fixed_threads ? fixed_threads / 32 : (g_tune_rb > 0 ? g_tune_rb : 8);
         if (!fixed_threads) NWR = std::max(kMinRowsR1, std::min(NWR, std::min(8, H)));  // kernel built for <= 256 threads
-        while (!fixed_threads && NWR > kMinRowsR1 && pass_r1_smem(NWR, E) > (size_t)kMaxSmem) --NWR;
-        P->smem = pass_r1_smem(NWR, E);
+        // the batched kernel (fixed_threads) runs the staged body
+        auto smem_of = [&](int n) { return fixed_threads ? pass_r1_staged_smem(n, E) : pass_r1_smem(n, E); };
+        while (!fixed_threads && NWR > kMinRowsR1 && smem_of(NWR) > (size_t)kMaxSmem) --NWR;
+        P->smem = smem_of(NWR);
         if (P->smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
         PassR1Args &a = P->o;
         a.C = C;
@@ -428,7 +432,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
     a.NT = NT;
     a.nbuf = nbuf;
     a.kmb = kmb;
-    a.ring = team_ring(W, kResidentMin);
+    a.ring = team_ring(2 * W, kResidentMin);
     a.em = S.em;
     a.lean = lean;
     a.l1 = p->l1;
@@ -446,7 +450,29 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
 // Control words that must start from zero before the first pass: status,
 // consumed-column and band counters, and the used hand-off records.
 size_t control_bytes(const SolvePlan &P, int W, int Q) {
-    return P.r1 ? P.L.ll + (size_t)P.nbands * W * Q * 8 : P.L.ll + (size_t)P.nbands * P.ta.ring * P.L.Qm * 8;
+    return P.r1 ? P.L.ll + (size_t)P.nbands * 2 * W * Q * 8 : P.L.ll + (size_t)P.nbands * P.ta.ring * P.L.Qm * 8;
+}
+
+// Launch k of iteration `it`: one pass (k = 0..3), or with paired sweeps the
+// pair k = 0 (P1 + P2) or 1 (P3 + P4).  Sets the first pass and the flags of
+// both passes of the launch.
+template <typename Args>
+int set_launch(Args &a, int it, int k, int iters, bool pairs) {
+    const int pass = pairs ? 2 * k : k;
+    const PassFlags f = pass_flags(it, pass, iters);
+    const PassFlags f2 = pass_flags(it, pairs ? pass + 1 : pass, iters);
+    a.pass = pass;
+    a.read_c = f.read_c;
+    a.read_d = f.read_d;
+    a.write_a = f.write_a;
+    a.write_b = f.write_b;
+    a.final_ = f.final_;
+    a.pair = pairs;
+    a.read_c2 = f2.read_c;
+    a.write_a2 = f2.write_a;
+    a.write_b2 = f2.write_b;
+    a.final2 = f2.final_;
+    return pass;
 }
 
 int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
@@ -463,46 +489,39 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
         const int occ = std::max(1, edp_pass_team_occupancy(P.em, P.ta.lean, 0, P.threads, P.smem));
         grid_t = std::min(P.nbands, occ * sms);
         // a smaller resident set than the ring was sized for could stall the back-pressure
-        if (grid_t < P.nbands && team_ring(W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
+        if (grid_t < P.nbands && team_ring(2 * W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
     }
+    // paired sweeps: two launches per iteration (P1 + P2, P3 + P4)
+    const bool pairs = g_pass_pairs;
+    const int per_it = pairs ? 2 : 4;
     for (int it = 0; it < p->iters; ++it) {
-        for (int pass = 0; pass < 4; ++pass) {
-            const int slot = it * 4 + pass;
-            const PassFlags f = pass_flags(it, pass, p->iters);
-            unsigned long long *trace = (g_trace && (size_t)(slot + 1) * P.nbands * 32 <= g_trace_bytes)
-                                            ? g_trace + (size_t)slot * P.nbands * 4
+        for (int k = 0; k < per_it; ++k) {
+            const int launch = it * per_it + k;
+            unsigned long long *trace = (g_trace && (size_t)(launch + 1) * P.nbands * 32 <= g_trace_bytes)
+                                            ? g_trace + (size_t)launch * P.nbands * 4
                                             : nullptr;
-            unsigned *counter = reinterpret_cast<unsigned *>(ws + P.L.counters) + slot;
-            const bool prof = g_prof_events && 2 * slot + 1 < g_prof_n;
-            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot], st) != cudaSuccess) return EDP_ERR_CUDA;
+            const bool prof = g_prof_events && 2 * launch + 1 < g_prof_n;
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * launch], st) != cudaSuccess)
+                return EDP_ERR_CUDA;
             if (P.r1) {
                 PassR1Args a = P.o;
-                a.pass = pass;
-                a.read_c = f.read_c;
-                a.read_d = f.read_d;
-                a.write_a = f.write_a;
-                a.write_b = f.write_b;
-                a.final_ = f.final_;
+                const int slot = it * 4 + set_launch(a, it, k, p->iters, pairs);  // counters of the first pass
                 a.tag = slot + 1;
-                a.band_counter = counter;
+                a.band_counter = reinterpret_cast<unsigned *>(ws + P.L.counters) + slot;
                 a.trace = trace;
                 if (launch_edp_pass_r1(a, P.threads, P.smem, st)) return EDP_ERR_CUDA;
             } else {
                 TeamArgs a = P.ta;
-                a.pass = pass;
-                a.read_c = f.read_c;
-                a.read_d = f.read_d;
-                a.write_a = f.write_a;
-                a.write_b = f.write_b;
-                a.final_ = f.final_;
+                // a pair takes the record tags of both its passes' slots
+                const int slot = it * 4 + set_launch(a, it, k, p->iters, pairs);
                 a.cons = reinterpret_cast<unsigned *>(ws + P.L.cons) + (size_t)slot * H;
                 a.tag0 = 1 + slot * P.laps;
-                a.band_counter = counter;
+                a.band_counter = reinterpret_cast<unsigned *>(ws + P.L.counters) + slot;
                 a.grid = grid_t;
                 a.trace = trace;
                 if (launch_edp_pass_team(a, P.threads, P.smem, st)) return EDP_ERR_CUDA;
             }
-            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * launch + 1], st) != cudaSuccess)
                 return EDP_ERR_CUDA;
         }
     }
@@ -607,6 +626,17 @@ int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, i
     g_force_general = general_kernel >= 1;
     g_generic_team = general_kernel == 2;
     return EDP_OK;
+}
+
+int edp_set_pass_pairs(int on) {
+    if (on != 0 && on != 1) return EDP_ERR_INVALID_ARG;
+    g_pass_pairs = on;
+    return EDP_OK;
+}
+
+int edp_pass_launches(int R, int Q, int iters) {
+    if (iters < 1 || R < 1 || Q < 1) return 0;
+    return (g_pass_pairs ? 2 : 4) * iters;
 }
 
 int edp_set_profile_events(void *const *events, int n_events) {
@@ -1150,7 +1180,7 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
     const size_t smem = pass_team_smem(NT, L.Qm, 2, a.nbuf, a.kmb);
     if (smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
     a.NT = NT;
-    a.ring = team_ring(W, kResidentMin);
+    a.ring = team_ring(2 * W, kResidentMin);
     a.win = win;
     a.l1 = params->l1;
     a.g = params->g;
@@ -1166,26 +1196,23 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int occ = std::max(1, edp_pass_team_occupancy(a.em, 0, 1, 32 * NT, smem));
     a.grid = std::min(a.nbands, occ * sms);
-    if (a.grid < a.nbands && team_ring(W, a.grid) > a.ring) return EDP_ERR_UNSUPPORTED;
+    if (a.grid < a.nbands && team_ring(2 * W, a.grid) > a.ring) return EDP_ERR_UNSUPPORTED;
     if ((rc = cuda_status(cudaMemsetAsync(w, 0, L.ll + (size_t)a.nbands * a.ring * L.Qm * 8, st)))) return rc;
+    const bool pairs = g_pass_pairs;
+    const int per_it = pairs ? 2 : 4;
     for (int it = 0; it < params->iters; ++it)
-        for (int pass = 0; pass < 4; ++pass) {
-            const int slot = it * 4 + pass;
-            const PassFlags f = pass_flags(it, pass, params->iters);
+        for (int k = 0; k < per_it; ++k) {
+            const int launch = it * per_it + k;
             TeamArgs b = a;
-            b.pass = pass;
-            b.read_c = f.read_c;
-            b.read_d = f.read_d;
-            b.write_a = f.write_a;
-            b.write_b = f.write_b;
-            b.final_ = f.final_;
+            const int slot = it * 4 + set_launch(b, it, k, params->iters, pairs);
             b.cons = reinterpret_cast<unsigned *>(w + L.cons) + (size_t)slot * H;
             b.tag0 = 1 + slot * laps;
             b.band_counter = reinterpret_cast<unsigned *>(w + L.counters) + slot;
-            const bool prof = g_prof_events && 2 * slot + 1 < g_prof_n;
-            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot], st) != cudaSuccess) return EDP_ERR_CUDA;
+            const bool prof = g_prof_events && 2 * launch + 1 < g_prof_n;
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * launch], st) != cudaSuccess)
+                return EDP_ERR_CUDA;
             if (launch_edp_pass_team(b, 32 * NT, smem, st)) return EDP_ERR_CUDA;
-            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * slot + 1], st) != cudaSuccess)
+            if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * launch + 1], st) != cudaSuccess)
                 return EDP_ERR_CUDA;
         }
     return EDP_OK;

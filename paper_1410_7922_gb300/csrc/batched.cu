@@ -14,6 +14,7 @@
 // kernel's parameter block (no host tables, so the launch can be captured in
 // a CUDA graph).
 #include "pass_r1.cuh"
+#include "pass_r1_staged.cuh"
 #include "pass_team.cuh"
 
 namespace edp {
@@ -69,11 +70,11 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
             a.tag = slot + 1;
             if (QUAD && a.l1 == 2)
                 ok = r1_dispatch(a.E, [&](auto e) {
-                    return r1_band<decltype(e)::value, QUAD>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+                    return staged::r1_band_staged<decltype(e)::value, QUAD>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
                 });
             else
                 ok = r1_dispatch(a.E, [&](auto e) {
-                    return r1_band<decltype(e)::value, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+                    return staged::r1_band_staged<decltype(e)::value, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
                 });
         } else {
             TeamArgs a = P.t;
@@ -115,6 +116,13 @@ static void *batched_kernel_for(int lm, int gen) {
     // dispatches on the line lengths itself otherwise)
     if (lm == 2) return gen ? batched_kernel<33, true, true>() : batched_kernel<33, false, true>();
     return gen ? batched_kernel<33, true, false>() : batched_kernel<33, false, false>();
+}
+
+// shared memory of the staged one-axis body: per warp a (kPf + 1)-column
+// ring of C, m_c, m_d; the mailbox ring and the produced / consumed counters
+size_t pass_r1_staged_smem(int NWR, int E) {
+    const size_t Qp = 32 * (size_t)E;
+    return ((size_t)NWR * (staged::kPf + 1) * 3 * Qp + (size_t)NWR * staged::kMb * Qp + 2 * (size_t)NWR) * 4;
 }
 
 int edp_batched_occupancy(int lm, int gen, int threads, size_t smem) {

@@ -4,8 +4,8 @@
 
 namespace edp {
 
-template <bool QUAD>
-__global__ void __launch_bounds__(QUAD ? 256 : kMaxThreads, 1) edp_pass_r1_kernel(PassR1Args A) {
+template <int E, bool QUAD>
+__global__ void __launch_bounds__(256, 1) edp_pass_r1_kernel(PassR1Args A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
     __shared__ volatile int s_abort;
@@ -17,19 +17,34 @@ __global__ void __launch_bounds__(QUAD ? 256 : kMaxThreads, 1) edp_pass_r1_kerne
         __syncthreads();
         const int band = s_band;
         if (band >= A.nbands) break;
-        const bool ok =
-            r1_dispatch(A.E, [&](auto e) { return r1_band<decltype(e)::value, QUAD>(A, band, smem_i, &s_abort); });
-        if (!ok) return;
+        if (!r1_band<E, QUAD>(A, band, smem_i, &s_abort)) return;
+    }
+}
+
+// one build per labels-per-lane count (each allocates its own registers)
+using R1Kernel = void (*)(PassR1Args);
+template <bool QUAD>
+R1Kernel r1_kernel_for(int E) {
+    switch (E) {
+    case 1: return edp_pass_r1_kernel<1, QUAD>;
+    case 2: return edp_pass_r1_kernel<2, QUAD>;
+    case 3: return edp_pass_r1_kernel<3, QUAD>;
+    case 4: return edp_pass_r1_kernel<4, QUAD>;
+    case 5: return edp_pass_r1_kernel<5, QUAD>;
+    case 6: return edp_pass_r1_kernel<6, QUAD>;
+    case 7: return edp_pass_r1_kernel<7, QUAD>;
+    default: return edp_pass_r1_kernel<8, QUAD>;
     }
 }
 
 size_t pass_r1_smem(int NWR, int E) {
     const size_t Qp = 32 * (size_t)E;
-    return ((size_t)NWR * (kPf + 1) * 3 * Qp + (size_t)NWR * kMb * Qp + 2 * (size_t)NWR) * 4;
+    // staging rings, mailbox records, consumed counters
+    return ((size_t)NWR * (kPf + 1) * 3 * Qp + 2 * (size_t)NWR * kMb * Qp + (size_t)NWR) * 4;
 }
 
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st) {
-    auto k = a.l1 == 2 ? edp_pass_r1_kernel<true> : edp_pass_r1_kernel<false>;
+    const R1Kernel k = a.l1 == 2 ? r1_kernel_for<true>(a.E) : r1_kernel_for<false>(a.E);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<a.grid, threads, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;

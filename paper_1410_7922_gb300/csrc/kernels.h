@@ -52,6 +52,8 @@ struct TeamArgs {
     int lam, capv, mode;    // mode 0 joint, 1 per axis truncation
     int l1, g;              // prior power (1: linear sweeps, 2: quadratic taps, lean / windowed forms) and truncation
     int pass, read_c, read_d, write_a, write_b, final_;
+    int pair;               // 1: passes pass and pass + 1 (pass 0 or 2) as one sweep of 2W columns per row
+    int read_c2, write_a2, write_b2, final2;  // flags of the second pass of a pair (read_d is shared)
     int T, NT;              // warps per team (one row), teams per block
     int nbuf, kmb, ring;    // staging buffers, mailbox slots, record ring columns
     int tag0;               // tag of the first ring lap of this pass
@@ -73,7 +75,7 @@ struct PassR1Args {
     const int *C;
     int *M[4];
     int *labels;
-    int2 *ll;               // [nbands][W][Q] {value, tag} hand-off records between blocks
+    int2 *ll;               // [nbands][W or 2W][Q] {value, tag} hand-off records between blocks
     unsigned *band_counter;
     int *status;
     int W, H, Q, Qm, E, EMt; // Qm: message stride; E labels per lane
@@ -81,6 +83,8 @@ struct PassR1Args {
     int lam, capv, kc;      // kc: lanes of carry in the truncated sweeps
     int l1, g;              // prior power (1: linear sweeps, 2: quadratic taps) and truncation
     int pass, read_c, read_d, write_a, write_b, final_;
+    int pair;               // 1: passes pass and pass + 1 (pass 0 or 2) as one sweep of 2W columns per row
+    int read_c2, write_a2, write_b2, final2;  // flags of the second pass of a pair (read_d is shared)
     int NWR;                // rows (warps) per block
     int nbands, grid, tag;
     long long spin_limit;
@@ -88,6 +92,7 @@ struct PassR1Args {
 };
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st);
 size_t pass_r1_smem(int NWR, int E);
+size_t pass_r1_staged_smem(int NWR, int E);  // the batched kernel's one-axis body (batched.cu)
 
 // batched solve: up to kMaxBatch problems of one wave, passed by value
 constexpr int kMaxBatch = 64;

@@ -6,16 +6,23 @@
 // image row and keeps the message into its next pixel (m_a) in registers;
 // lane j holds the E labels j*E .. j*E+E-1 of the row's current pixel.
 //
-// Per column the only work that waits for the row above is: two adds, the
-// halving, the min search M and the hand-off of m_b.  Everything else -- the
-// prefetch of C, m_c, m_d (cp.async, kPf columns ahead, vector copies), their
-// loads and partial sums -- is done before the wait.
+// The column step is a chain of dependent instructions (the warp's own m_a
+// feeds the next column), so the loop body is kept short and compact (one
+// copy of it, hot in the instruction cache): C, m_c, m_d are staged kPf
+// columns ahead into a shared-memory ring by cp.async from running pointers,
+// the output addresses advance by one add per column, and the back-pressure
+// check loads the consumer's counter only when the cached value is too old.
+// What waits for the row above is: two adds, the halving, the min search M
+// and the hand-off of m_b.
 //
-//  - m_b from the row above: a shared-memory mailbox ring inside the block
-//    (release / acquire counters, bounded spins), and between blocks a
-//    "value + tag" 8-byte record per label in global memory that the
-//    consumer polls until every tag equals this pass's tag (no fence on the
-//    path).  Global message stores are issued after the hand-off.
+//  - m_b from the row above: inside the block a shared-memory mailbox ring
+//    of "value + tag" 8-byte records (tag = column + 1; one 64-bit access
+//    per record, so a tag that matches carries its value), polled until
+//    every tag of the column matches, with a consumed-column counter for
+//    back-pressure; between blocks the same records in global memory, one
+//    per column and label, tagged with the launch.  No fence is on the path:
+//    a release would also wait for this warp's earlier global stores.
+//    Global message stores are issued after the hand-off.
 //  - M of the truncated linear prior: per-lane forward / backward sweeps
 //    (Eq. L_dec3, Eq. L_dec5), carries from the lanes within distance < g
 //    (farther labels cost at least the clip value), the vector minimum by
@@ -29,19 +36,29 @@
 namespace edp {
 
 namespace {
-constexpr int kPf = 7;   // prefetch distance in columns (ring of kPf + 1)
+constexpr int kPf = 7;   // prefetch distance in columns (ring of kPf + 1 slots)
 constexpr int kMb = 8;   // mailbox ring depth between rows of a block
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ int redux_min(int v) { return __reduce_min_sync(kFull, v); }
 
-__device__ __forceinline__ int ld_acq_shared(const int *p) {
+// tagged mailbox records in shared memory: {value, tag} as one 64-bit access
+__device__ __forceinline__ int2 lds_rec(const int2 *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.cta.shared.b64 %0, [%1];" : "=l"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return make_int2((int)(unsigned)v, (int)(unsigned)(v >> 32));
+}
+__device__ __forceinline__ void sts_rec(int2 *p, int value, int tag) {
+    const unsigned long long v = (unsigned long long)(unsigned)value | ((unsigned long long)(unsigned)tag << 32);
+    asm volatile("st.relaxed.cta.shared.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_shared(const int *p) {
     int v;
-    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    asm volatile("ld.relaxed.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_rel_shared(int *p, int v) {
-    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_shared(int *p, int v) {
+    asm volatile("st.relaxed.cta.shared.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
 __device__ __forceinline__ int2 ld_rec(const int2 *p) {
     int2 r;
@@ -51,15 +68,61 @@ __device__ __forceinline__ int2 ld_rec(const int2 *p) {
 __device__ __forceinline__ void st_rec(int2 *p, int v, int tag) {
     asm volatile("st.relaxed.gpu.global.v2.s32 [%0], {%1, %2};" ::"l"(p), "r"(v), "r"(tag) : "memory");
 }
-__device__ __forceinline__ void cp_async_bytes(int *dst, const int *src, int bytes, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const int n = valid ? bytes : 0;
-    if (bytes == 16)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
-    else if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+// cp.async of a lane's E consecutive ints in chunks of V ints (V divides E);
+// chunks at or past Q labels are not copied, all are zero-filled when !ok.
+template <int E, int V>
+__device__ __forceinline__ void cp_chunks(unsigned dst, const int *src, int q0, int Q, bool ok) {
+    const int n = ok ? 4 * V : 0;
+#pragma unroll
+    for (int i = 0; i < E; i += V) {
+        if (q0 + i < Q) {
+            if constexpr (V == 4)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst + 4 * i), "l"(src + i), "r"(n) : "memory");
+            else if constexpr (V == 2)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst + 4 * i), "l"(src + i), "r"(n) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * i), "l"(src + i), "r"(n) : "memory");
+        }
+    }
+}
+// widest chunk that divides E (message vectors: 16-byte aligned pixel
+// vectors, so a lane's E-aligned run of labels is E * 4-byte aligned)
+template <int E>
+constexpr int msg_chunk() { return E % 4 == 0 ? 4 : (E % 2 == 0 ? 2 : 1); }
+// vector shared-memory load of a lane's E consecutive ints
+template <int E>
+__device__ __forceinline__ void lds_vec(unsigned a, int (&v)[E]) {
+    constexpr int V = msg_chunk<E>();
+#pragma unroll
+    for (int i = 0; i < E; i += V) {
+        if constexpr (V == 4) {
+            asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(v[i]), "=r"(v[i + 1]), "=r"(v[i + 2]), "=r"(v[i + 3]) : "r"(a + 4 * i));
+        } else if constexpr (V == 2) {
+            asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(v[i]), "=r"(v[i + 1]) : "r"(a + 4 * i));
+        } else {
+            asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v[i]) : "r"(a + 4 * i));
+        }
+    }
+}
+
+// store of a lane's E message values (message vectors have stride Qm, a
+// multiple of 4, so E-aligned chunks of a lane that starts below Q stay
+// inside its pixel's vector)
+template <int E>
+__device__ __forceinline__ void stg_vec(int *p, const int (&v)[E], int q0, int Q) {
+    constexpr int V = E % 4 == 0 ? 4 : (E % 2 == 0 ? 2 : 1);
+#pragma unroll
+    for (int i = 0; i < E; i += V) {
+        if (q0 + i < Q) {
+            if constexpr (V == 4)
+                *reinterpret_cast<int4 *>(p + i) = make_int4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            else if constexpr (V == 2)
+                *reinterpret_cast<int2 *>(p + i) = make_int2(v[i], v[i + 1]);
+            else
+                p[i] = v[i];
+        }
+    }
 }
 
 // Truncated L1 distance transform of two row vectors a, b (E labels per
@@ -182,263 +245,238 @@ __device__ __forceinline__ void quad_pair(int (&a)[E], int (&b)[E], int lane, in
     }
 }
 
-// vector shared-memory load / store of a lane's E consecutive ints
-template <int E>
-__device__ __forceinline__ void lds_vec(const int *p, int (&v)[E]) {
-    if constexpr (E % 4 == 0) {
-#pragma unroll
-        for (int i = 0; i < E; i += 4) {
-            const int4 t = *reinterpret_cast<const int4 *>(p + i);
-            v[i] = t.x;
-            v[i + 1] = t.y;
-            v[i + 2] = t.z;
-            v[i + 3] = t.w;
-        }
-    } else if constexpr (E % 2 == 0) {
-#pragma unroll
-        for (int i = 0; i < E; i += 2) {
-            const int2 t = *reinterpret_cast<const int2 *>(p + i);
-            v[i] = t.x;
-            v[i + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < E; ++i) v[i] = p[i];
-    }
-}
-template <int E>
-__device__ __forceinline__ void sts_vec(int *p, const int (&v)[E]) {
-    if constexpr (E % 4 == 0) {
-#pragma unroll
-        for (int i = 0; i < E; i += 4) *reinterpret_cast<int4 *>(p + i) = make_int4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-    } else if constexpr (E % 2 == 0) {
-#pragma unroll
-        for (int i = 0; i < E; i += 2) *reinterpret_cast<int2 *>(p + i) = make_int2(v[i], v[i + 1]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < E; ++i) p[i] = v[i];
-    }
-}
 }  // namespace
 
-// One row band (NWR rows, one warp each) of one scan pass.  Every thread of
-// the block calls it with the same band; returns false when the pass was
-// aborted (a wait timed out).
+// One row band (NWR rows, one warp each) of one scan pass, or of two passes
+// that share the vertical direction (A.pair: P1 then P2, or P3 then P4).  A
+// paired sweep runs 2W columns per row: the first half is pass A.pass from
+// left to right, the second half pass A.pass + 1 from right to left.  This is
+// the same Gauss-Seidel order as two separate passes: pixel (x, y) of the
+// second pass reads m_{+x} of the first pass at (x - 1, y) (written by this
+// lane in its first half), its own pass at (x + 1, y) and (x, y -+ 1), and
+// m_{-+y} from the opposite vertical direction, which neither pass writes.
+// The wavefront of the pair is H + 2W columns long instead of 2 (H + W).
+// Every thread of the block calls it with the same band; returns false when
+// the pass was aborted (a wait timed out).
 // QUAD: the build for the truncated quadratic prior (l1 = 2).
 template <int E, bool QUAD = false>
 __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int *smem_i, volatile int *s_abort) {
-    const int Q = A.Q, W = A.W, H = A.H, NWR = A.NWR;
     constexpr int Qp = 32 * E;  // padded vector length in shared memory
+    constexpr int VM = msg_chunk<E>();
+    const int Q = A.Q, W = A.W, H = A.H, NWR = A.NWR, Qm = A.Qm;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    int *ring = smem_i + (size_t)w * (kPf + 1) * 3 * Qp;  // [kPf+1][3][Qp] per warp
-    int *mbox = smem_i + (size_t)NWR * (kPf + 1) * 3 * Qp;  // [NWR][kMb][Qp]
-    int *produced = mbox + (size_t)NWR * kMb * Qp;          // [NWR]
-    int *consumed = produced + NWR;                         // [NWR]
-    const bool incx = (A.pass == 0 || A.pass == 2);
+    // [NWR][kPf+1][3][Qp] staging ring, then [NWR][kMb][Qp] {value, tag} mailbox records
+    int *const ring = smem_i + (size_t)w * (kPf + 1) * 3 * Qp;
+    int2 *const mbox = reinterpret_cast<int2 *>(smem_i + (size_t)NWR * (kPf + 1) * 3 * Qp);
+    int *const consumed = reinterpret_cast<int *>(mbox + (size_t)NWR * kMb * Qp);  // [NWR]
     const bool incy = (A.pass < 2);
-    int *const Ma = incx ? A.M[0] : A.M[1];
+    const int ncol = A.pair ? 2 * W : W;
     int *const Mb = incy ? A.M[2] : A.M[3];
-    const int *const Mc = incx ? A.M[1] : A.M[0];
     const int *const Md = incy ? A.M[3] : A.M[2];
-    if (tid < NWR) {
-        produced[tid] = 0;
-        consumed[tid] = 0;
-    }
+    // no stale tag may match: records from an earlier band (or launch) are cleared
+    for (int i = tid; i < NWR * kMb * Qp; i += blockDim.x) mbox[i] = make_int2(0, 0);
+    if (tid < NWR) consumed[tid] = 0;
     __syncthreads();
     unsigned long long t_band0 = (A.trace && tid == 0) ? global_ns() : 0, t_wait = 0;
     const int r = band * NWR + w;
+    bool aborted = false;
     if (w < NWR && r < H) {
         const int y = incy ? r : H - 1 - r;
         const bool has_next = r + 1 < H;
-        const int y_next = incy ? y + 1 : y - 1;
+        const int y_next = has_next ? (incy ? y + 1 : y - 1) : y;
         const bool last_in_band = (w == NWR - 1);
         const bool d_ok = A.read_d && (incy ? y + 1 < H : y - 1 >= 0);
         const int q0 = lane * E;
-        const bool lane_on = q0 < Q;
-        const int vw = A.vw;          // ints per cp.async (1, 2 or 4)
-        // pixel pointers advance by +/-Q (cost) and +/-Qm (messages) per column
-        const int Qm = A.Qm;
-        const long long dq = incx ? Q : -Q, dqm = incx ? Qm : -Qm;
-        const int *pC = A.C + ((size_t)y * W + (incx ? 0 : W - 1)) * Q + q0;
-        const size_t m0 = ((size_t)y * W + (incx ? 0 : W - 1)) * Qm + q0;
-        const size_t mn = ((size_t)(has_next ? y_next : y) * W + (incx ? 0 : W - 1)) * Qm + q0;
-        const int *pc = Mc + m0;
-        const int *pd = Md + m0;
-        int *pa_out = Ma + m0;   // message into the column, written one column ahead
-        int *pb_out = Mb + mn;
-        const int2 *ll_in = A.ll + (size_t)(band - 1) * W * Q + q0;  // previous band's last row
-        int2 *ll_out = A.ll + (size_t)band * W * Q + q0;
-        const int mb_src = (w - 1) * kMb;
-
-        auto prefetch = [&](int s) {
-            if (s < W && lane_on) {
-                const long long off = (long long)s * dq, offm = (long long)s * dqm;
-                const int x = incx ? s : W - 1 - s;
-                const bool c_ok = A.read_c && (incx ? x + 1 < W : x - 1 >= 0);
-                int *dst = ring + (s % (kPf + 1)) * 3 * Qp + q0;
-#pragma unroll
-                for (int i = 0; i < E; i += 1) {
-                    // vw divides both E and Q: a vw-chunk is wholly inside or outside the vector
-                    if (i % vw || q0 + i >= Q) continue;
-                    cp_async_bytes(dst + i, pC + off + i, 4 * vw, true);
-                    cp_async_bytes(dst + Qp + i, pc + offm + i, 4 * vw, c_ok);
-                    cp_async_bytes(dst + 2 * Qp + i, pd + offm + i, 4 * vw, d_ok);
+        const int vw = A.vw;  // ints per C load (1, 2 or 4): divides E and Q, aligned
+        const int2 *const ll_in = A.ll + (size_t)(band - 1) * ncol * Q + q0;  // previous band's last row
+        int2 *const ll_out = A.ll + (size_t)band * ncol * Q + q0;
+        const int2 *const mb_in = mbox + (size_t)(w - 1) * kMb * Qp + q0;  // used when w > 0
+        int2 *const mb_out = mbox + (size_t)w * kMb * Qp + q0;
+        const int *const Crow = A.C + (size_t)y * W * Q + q0;
+        const size_t mrow = (size_t)y * W * Qm + q0;
+        const int *const Mdrow = Md + mrow;
+        int *const Mbrow = Mb + (size_t)y_next * W * Qm + q0;
+        int cons_seen = 0;  // the consumer's progress as last read (producer side)
+        const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring + q0);
+        constexpr unsigned kSlot = 3 * Qp * 4;  // bytes per ring slot
+        for (int h = 0; h < (A.pair ? 2 : 1) && !aborted; ++h) {
+            // half h: pass A.pass + h, pixel x = incx ? xs : W - 1 - xs at column xs
+            const bool incx = ((A.pass + h) & 1) == 0;
+            const bool read_c = h ? A.read_c2 : A.read_c;
+            const bool write_a = h ? A.write_a2 : A.write_a;
+            const bool write_b = has_next && (h ? A.write_b2 : A.write_b);
+            const bool fin = h ? A.final2 : A.final_;
+            const int x0 = incx ? 0 : W - 1;
+            const int dC = incx ? Q : -Q, dM = incx ? Qm : -Qm;
+            // running source pointers of the prefetch (column xp of the half)
+            const int *pfC = Crow + (size_t)x0 * Q;
+            const int *pfc = (incx ? A.M[1] : A.M[0]) + mrow + (size_t)x0 * Qm;
+            const int *pfd = Mdrow + (size_t)x0 * Qm;
+            int xp = 0;
+            auto prefetch = [&]() {
+                if (xp < W && q0 < Q) {
+                    const unsigned dst = ring_s + (unsigned)((h * W + xp) % (kPf + 1)) * kSlot;
+                    if (vw == 4)
+                        cp_chunks<E, (E % 4 == 0 ? 4 : 1)>(dst, pfC, q0, Q, true);
+                    else if (vw == 2)
+                        cp_chunks<E, (E % 2 == 0 ? 2 : 1)>(dst, pfC, q0, Q, true);
+                    else
+                        cp_chunks<E, 1>(dst, pfC, q0, Q, true);
+                    cp_chunks<E, VM>(dst + Qp * 4, pfc, q0, Q, read_c && xp + 1 < W);
+                    cp_chunks<E, VM>(dst + 2 * Qp * 4, pfd, q0, Q, d_ok);
                 }
-            }
-            cp_async_commit();
-        };
-        for (int s = 0; s < kPf; ++s) prefetch(s);
-
-        int ma[E];
+                cp_async_commit();
+                ++xp;
+                pfC += dC;
+                pfc += dM;
+                pfd += dM;
+            };
+            for (int t = 0; t < kPf; ++t) prefetch();
+            // running output pointers: m_a into the next pixel, m_b into the next row
+            int *pa_out = (incx ? A.M[0] : A.M[1]) + mrow + (long long)(x0 + (incx ? 1 : -1)) * Qm;
+            int *pb_out = Mbrow + (size_t)x0 * Qm;
+            int ma[E];
 #pragma unroll
-        for (int i = 0; i < E; ++i) ma[i] = 0;
-        for (int s = 0; s < W; ++s) {
-            prefetch(s + kPf);
-            cp_async_wait_n<kPf>();
-            // ---- work that does not wait for the row above ----
-            const int *src = ring + (s % (kPf + 1)) * 3 * Qp + q0;
-            int cv[E], mc[E], md[E], pa[E], pb[E], po[E];
-            lds_vec<E>(src, cv);
-            lds_vec<E>(src + Qp, mc);
-            lds_vec<E>(src + 2 * Qp, md);
+            for (int i = 0; i < E; ++i) ma[i] = 0;
+#pragma unroll 1
+            for (int xs = 0; xs < W; ++xs) {
+                const int s = h * W + xs;  // column of the launch (ring slots, mailbox tags, records)
+                prefetch();
+                cp_async_wait_n<kPf>();
+                // ---- work that does not wait for the row above ----
+                const unsigned src = ring_s + (unsigned)(s % (kPf + 1)) * kSlot;
+                int cv[E], mc[E], md[E], pa[E], pb[E];
+                lds_vec<E>(src, cv);
+                lds_vec<E>(src + Qp * 4, mc);
+                lds_vec<E>(src + 2 * Qp * 4, md);
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-                pa[i] = cv[i] + ma[i] + md[i] - mc[i];
-                pb[i] = cv[i] + ma[i] + mc[i] - md[i];
-                po[i] = cv[i] + ma[i] + mc[i] + md[i];
-            }
-            // ---- m_b from the row above ----
-            int mb[E];
+                for (int i = 0; i < E; ++i) {
+                    pa[i] = cv[i] + ma[i] + md[i] - mc[i];
+                    pb[i] = cv[i] + ma[i] + mc[i] - md[i];
+                }
+                // ---- m_b from the row above ----
+                int mb[E];
 #pragma unroll
-            for (int i = 0; i < E; ++i) mb[i] = 0;
-            if (r > 0) {
-                long long spins = 0;
-                if (w > 0) {
-                    while (true) {
-                        const bool ok = ld_acq_shared(produced + w - 1) >= s + 1;
-                        if (__all_sync(kFull, ok)) break;
-                        if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0)) {
-                            if (lane == 0) {
-                                atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
-                                *s_abort = 1;
-                            }
-                            break;
-                        }
-                    }
-                    lds_vec<E>(mbox + (mb_src + s % kMb) * Qp + q0, mb);
-                    __syncwarp();
-                    if (lane == 0) st_rel_shared(consumed + w, s + 1);
-                } else {
-                    const unsigned long long tw = A.trace ? global_ns() : 0;
-                    const int2 *p = ll_in + (size_t)s * Q;
+                for (int i = 0; i < E; ++i) mb[i] = 0;
+                if (r > 0) {
+                    long long spins = 0;
+                    bool bad = false;
+                    const int2 *p = (w > 0) ? mb_in + (s % kMb) * Qp : ll_in + (size_t)s * Q;
+                    const int want = (w > 0) ? s + 1 : A.tag;
+                    const unsigned long long tw = (A.trace && w == 0) ? global_ns() : 0;
                     while (true) {
                         bool ok = true;
 #pragma unroll
                         for (int i = 0; i < E; ++i) {
                             if (q0 + i < Q) {
-                                const int2 t = ld_rec(p + i);
+                                const int2 t = (w > 0) ? lds_rec(p + i) : ld_rec(p + i);
                                 mb[i] = t.x;
-                                ok = ok && (t.y == A.tag);
+                                ok = ok && (t.y == want);
                             }
                         }
                         if (__all_sync(kFull, ok)) break;
                         if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0 ||
-                                                  *(volatile int *)A.status != 0)) {
-                            if (lane == 0) {
-                                atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
-                                *s_abort = 1;
-                            }
+                                                  (w == 0 && *(volatile int *)A.status != 0))) {
+                            bad = true;
                             break;
                         }
-                        __nanosleep(20);
+                        if (w == 0) __nanosleep(20);
                     }
-                    if (A.trace) t_wait += global_ns() - tw;
+                    if (tw) t_wait += global_ns() - tw;
+                    if (bad) {
+                        if (lane == 0) {
+                            atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
+                            *s_abort = 1;
+                        }
+                        aborted = true;
+                        break;
+                    }
+                    // issued after the vote on every lane's loaded tags: the
+                    // loads of the slot have returned before the producer can
+                    // see this count and overwrite it
+                    if (w > 0 && lane == 0) st_relaxed_shared(consumed + w, s + 1);
                 }
-                if (__any_sync(kFull, *s_abort != 0)) break;
-            }
-            // ---- sums (Eq. DP_2D_base), halving, min search M ----
-            int ha[E], hb[E];
-            int la = kBig, lb = kBig;
+                // ---- sums (Eq. DP_2D_base), halving, min search M ----
+                int ha[E], hb[E];
+                int la = kBig, lb = kBig;
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-                const bool on = q0 + i < Q;
-                ha[i] = on ? floor_half(pa[i] + mb[i]) : kBig;
-                hb[i] = on ? floor_half(pb[i] + mb[i]) : kBig;
-                la = min(la, ha[i]);
-                lb = min(lb, hb[i]);
-            }
-            const int ga = redux_min(la), gb = redux_min(lb);
-            if constexpr (QUAD)
-                quad_pair<E>(ha, hb, lane, A.lam, A.g);
-            else
-                dt_pair<E>(ha, hb, lane, A.lam, A.kc);
-            const int clipa = ga + A.capv, clipb = gb + A.capv;
+                for (int i = 0; i < E; ++i) {
+                    const bool on = q0 + i < Q;
+                    ha[i] = on ? floor_half(pa[i] + mb[i]) : kBig;
+                    hb[i] = on ? floor_half(pb[i] + mb[i]) : kBig;
+                    la = min(la, ha[i]);
+                    lb = min(lb, hb[i]);
+                }
+                const int ga = redux_min(la), gb = redux_min(lb);
+                if constexpr (QUAD)
+                    quad_pair<E>(ha, hb, lane, A.lam, A.g);
+                else
+                    dt_pair<E>(ha, hb, lane, A.lam, A.kc);
+                const int clipa = ga + A.capv, clipb = gb + A.capv;
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-                ha[i] = min(ha[i], clipa);
-                hb[i] = min(hb[i], clipb);
-            }
-            // ---- hand-off of m_b to the row below, then the global stores ----
-            if (has_next) {
-                if (!last_in_band) {
-                    if (s >= kMb) {
-                        long long spins = 0;
-                        while (true) {
-                            const bool ok = ld_acq_shared(consumed + w + 1) >= s - kMb + 1;
-                            if (__all_sync(kFull, ok)) break;
-                            if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0)) {
+                for (int i = 0; i < E; ++i) {
+                    ha[i] = min(ha[i], clipa);
+                    hb[i] = min(hb[i], clipb);
+                }
+                // ---- hand-off of m_b to the row below, then the global stores ----
+                if (has_next) {
+                    if (!last_in_band) {
+                        const int need = s - kMb + 1;  // the slot's previous column was read
+                        if (cons_seen < need) {
+                            long long spins = 0;
+                            bool bad = false;
+                            while (true) {
+                                cons_seen = ld_relaxed_shared(consumed + w + 1);
+                                if (__all_sync(kFull, cons_seen >= need)) break;
+                                if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0)) {
+                                    bad = true;
+                                    break;
+                                }
+                            }
+                            if (bad) {
                                 if (lane == 0) {
                                     atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
                                     *s_abort = 1;
                                 }
+                                aborted = true;
                                 break;
                             }
                         }
+                        int2 *p = mb_out + (s % kMb) * Qp;
+#pragma unroll
+                        for (int i = 0; i < E; ++i)
+                            if (q0 + i < Q) sts_rec(p + i, hb[i], s + 1);
+                    } else {
+                        int2 *p = ll_out + (size_t)s * Q;
+#pragma unroll
+                        for (int i = 0; i < E; ++i)
+                            if (q0 + i < Q) st_rec(p + i, hb[i], A.tag);
                     }
-                    sts_vec<E>(mbox + (w * kMb + s % kMb) * Qp + q0, hb);
-                    __syncwarp();
-                    if (lane == 0) st_rel_shared(produced + w, s + 1);
-                } else {
-                    int2 *p = ll_out + (size_t)s * Q;
-#pragma unroll
-                    for (int i = 0; i < E; ++i)
-                        if (q0 + i < Q) st_rec(p + i, hb[i], A.tag);
+                    if (write_b) stg_vec<E>(pb_out, hb, q0, Q);
                 }
-                if (A.write_b) {
-                    int *p = pb_out + (long long)s * dqm;
+                if (write_a && xs + 1 < W) stg_vec<E>(pa_out, ha, q0, Q);
+                pa_out += dM;
+                pb_out += dM;
+                if (fin) {
+                    // marginal S_Omega = C + all four messages, lowest-index argmin
+                    int sv = kBig, sq = 0x7fffffff;
 #pragma unroll
-                    for (int i = 0; i < E; ++i)
-                        if (q0 + i < Q) p[i] = hb[i];
-                }
-            }
-            if (A.write_a && s + 1 < W) {
-                int *p = pa_out + (long long)(s + 1) * dqm;
-#pragma unroll
-                for (int i = 0; i < E; ++i)
-                    if (q0 + i < Q) p[i] = ha[i];
-            }
-            if (A.final_) {
-                // marginal S_Omega = C + all four messages, lowest-index argmin
-                int sv = kBig, sq = 0x7fffffff;
-#pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    const int v = po[i] + mb[i];
-                    if (q0 + i < Q && v < sv) {
-                        sv = v;
-                        sq = q0 + i;
+                    for (int i = 0; i < E; ++i) {
+                        const int v = cv[i] + ma[i] + mc[i] + md[i] + mb[i];
+                        if (q0 + i < Q && v < sv) {
+                            sv = v;
+                            sq = q0 + i;
+                        }
                     }
+                    const int vbest = redux_min(sv);
+                    const int qbest = redux_min(sv == vbest ? sq : 0x7fffffff);
+                    if (lane == 0) A.labels[(size_t)y * W + (incx ? xs : W - 1 - xs)] = qbest;
                 }
-                const int vbest = redux_min(sv);
-                const int qbest = redux_min(sv == vbest ? sq : 0x7fffffff);
-                if (lane == 0) {
-                    const int x = incx ? s : W - 1 - s;
-                    A.labels[(size_t)y * W + x] = qbest;
-                }
-            }
 #pragma unroll
-            for (int i = 0; i < E; ++i) ma[i] = ha[i];
+                for (int i = 0; i < E; ++i) ma[i] = ha[i];
+            }
+            cp_async_wait_0();
         }
-        cp_async_wait_0();
     }
     if (A.trace && tid == 0) {
         A.trace[band * 4 + 0] = t_band0;

@@ -330,6 +330,7 @@ __device__ __forceinline__ int lean_phase0(unsigned aC, unsigned aCc, unsigned a
 // the messages.
 struct LeanOut {
     unsigned aMa, aBox;    // shared: m_a of the next column, mailbox slot of the next row (0: none)
+    bool zero_a;           // no next column in this sweep direction: m_a of the next column is zero
     int *pMa, *pMb;        // global M[a], M[b] (null: not written)
     int2 *pRec;            // record ring slot (null: none)
     int tag;
@@ -353,7 +354,7 @@ __device__ __forceinline__ void lean_phase_r(unsigned aX, int qb, int st, bool l
     } else if (vsel == 0) {
         const unsigned om = O.aMa + 4u * (unsigned)qb;
 #pragma unroll
-        for (int i = 0; i < L; ++i) team::sts(om + i * st4, h[i]);
+        for (int i = 0; i < L; ++i) team::sts(om + i * st4, O.zero_a ? 0 : h[i]);
         if (O.pMa) {
 #pragma unroll
             for (int i = 0; i < L; ++i) O.pMa[qb + i * st] = h[i];
@@ -413,11 +414,12 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
 
     const int r = band * NT + tm;
     if (tm < NT && r < H) {
-        const bool incx = (A.pass == 0 || A.pass == 2);
+        // A.pair: passes A.pass (left to right) and A.pass + 1 (right to left)
+        // as one sweep of 2W columns per row (half h = column / W)
+        const int ncol = A.pair ? 2 * W : W;
+        auto incx_of = [&](int h) { return ((A.pass + h) & 1) == 0; };
         const bool incy = (A.pass < 2);
-        int *const Ma = incx ? A.M[0] : A.M[1];
         int *const Mb = incy ? A.M[2] : A.M[3];
-        const int *const Mc = incx ? A.M[1] : A.M[0];
         const int *const Md = incy ? A.M[3] : A.M[2];
         const int y = incy ? r : H - 1 - r;
         const bool has_next = r + 1 < H;
@@ -454,11 +456,15 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             return X.stride == 1 ? li * X.L : (li % X.stride) + (li / X.stride) * X.stride * X.L;
         };
 
-        auto prefetch = [&](int s) {
-            if (s < W) {
-                const int x = incx ? s : W - 1 - s;
+        // column xt of the half sweeping in direction incx (column s of the
+        // launch); its m_c source Mc, read only where read_c.  In the second
+        // half of a pair, Mc holds the first half's m_a outputs (ordered
+        // before this by the team barriers).
+        auto prefetch = [&](int xt, int s, bool incx, const int *Mc, bool read_c) {
+            if (xt < W) {
+                const int x = incx ? xt : W - 1 - xt;
                 const size_t pix = (size_t)y * W + x;
-                const bool c_ok = A.read_c && (incx ? x + 1 < W : x - 1 >= 0);
+                const bool c_ok = read_c && (incx ? x + 1 < W : x - 1 >= 0);
                 int *dst = stg + (size_t)(s % nbuf) * SS;
                 const size_t e0 = pix * Q + cshift, e1 = e0 + Q, eend = NQ + cshift;
                 const size_t c0 = e0 >> 2, c1 = (e1 + 3) >> 2;
@@ -475,19 +481,29 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                     // box centres of this pixel, of the next pixel of the row and of
                     // the same column in the next row (zero where there is none)
                     const int which = tl / R, r_ = tl - which * R;
-                    const bool ok = which == 0 || (which == 1 ? s + 1 < W : has_next);
+                    const bool ok = which == 0 || (which == 1 ? xt + 1 < W : has_next);
                     const size_t p2 = which == 0 ? pix : (which == 1 ? pix + (incx ? 1 : -1) : (size_t)y_next * W + x);
                     cp_async4(dst + 3 * Qs + tl, A.centre + (ok ? p2 : pix) * R + r_, ok);
                 }
             }
             cp_async_commit();
         };
-        for (int s = 0; s < nbuf - 1; ++s) prefetch(s);
-
         unsigned cons_seen = 0;     // consumer progress seen by this producer (lane tl == 0)
         int mb_cons_seen = 0;       // same, for the mailbox consumer
-        for (int s = 0; s < W; ++s) {
-            prefetch(s + nbuf - 1);
+        bool aborted = false;
+        for (int h = 0; h < (A.pair ? 2 : 1) && !aborted; ++h) {
+        // half h of the sweep: pass A.pass + h, direction and flags
+        const bool incx = incx_of(h);
+        const bool fin = h ? A.final2 : A.final_;     // marginal and labels (last pass)
+        const bool read_c = h ? A.read_c2 : A.read_c;
+        const bool write_a = h ? A.write_a2 : A.write_a;
+        const bool write_b = h ? A.write_b2 : A.write_b;
+        int *const Ma = incx ? A.M[0] : A.M[1];
+        const int *const Mc = incx ? A.M[1] : A.M[0];
+        for (int t = 0; t < nbuf - 1; ++t) prefetch(t, h * W + t, incx, Mc, read_c);
+        for (int xs = 0; xs < W; ++xs) {
+            const int s = h * W + xs;  // column of the launch (ring slots, tags, counters)
+            prefetch(xs + nbuf - 1, s + nbuf - 1, incx, Mc, read_c);
             wait_groups(nbuf - 1);
             bool bad = false;
             // ---- m_b of this column from the row above ----
@@ -507,21 +523,34 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 const int2 *p = ll_in + (size_t)(s % ring) * Qm;
                 const int tag = A.tag0 + s / ring;
                 int *dst = mbox + (s % kmb) * Qm;
-                for (int q = 2 * tl; q < Q; q += 2 * NL) {
-                    long long spins = 0;
-                    int4 v;
-                    while (true) {
-                        v = ld_rec2(p + q);
-                        if (v.y == tag && (q + 1 >= Q || v.w == tag)) break;
-                        if (++spins > A.spin_limit ||
-                            ((spins & 63) == 0 && (*s_abort || *(volatile int *)A.status != 0))) {
-                            bad = true;
-                            break;
-                        }
+                // kRecBatch record pairs per lane in flight: the first loads of a
+                // batch are independent, so a column costs about one L2 round
+                // trip per batch rather than one per record pair
+                constexpr int kRecBatch = 8;
+                for (int q0 = 2 * tl; q0 < Q && !bad; q0 += 2 * NL * kRecBatch) {
+                    int4 v[kRecBatch];
+#pragma unroll
+                    for (int u = 0; u < kRecBatch; ++u) {
+                        const int q = q0 + 2 * NL * u;
+                        if (q < Q) v[u] = ld_rec2(p + q);
                     }
-                    if (bad) break;
-                    dst[q] = v.x;
-                    if (q + 1 < Q) dst[q + 1] = v.z;
+#pragma unroll
+                    for (int u = 0; u < kRecBatch; ++u) {
+                        const int q = q0 + 2 * NL * u;
+                        if (q >= Q || bad) continue;
+                        long long spins = 0;
+                        while (!(v[u].y == tag && (q + 1 >= Q || v[u].w == tag))) {
+                            if (++spins > A.spin_limit ||
+                                ((spins & 63) == 0 && (*s_abort || *(volatile int *)A.status != 0))) {
+                                bad = true;
+                                break;
+                            }
+                            v[u] = ld_rec2(p + q);
+                        }
+                        if (bad) break;
+                        dst[q] = v[u].x;
+                        if (q + 1 < Q) dst[q + 1] = v[u].z;
+                    }
                 }
             }
             // producer side: room in the consumer's mailbox / record ring
@@ -555,26 +584,30 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
                 *s_abort = 1;
             }
-            if (sync_or(tm, T, bad || *s_abort)) break;  // barrier 1
+            if (sync_or(tm, T, bad || *s_abort)) {  // barrier 1
+                aborted = true;
+                break;
+            }
 
             // ---- column s: inputs in shared memory, outputs ----
+            const int x = incx ? xs : W - 1 - xs;
             const int *sb = stg + (size_t)(s % nbuf) * SS;
-            const int *sC = sb + (int)((((size_t)y * W + (incx ? s : W - 1 - s)) * Q + cshift) & 3);
+            const int *sC = sb + (int)((((size_t)y * W + x) * Q + cshift) & 3);
             const int *sc = sb + Qs, *sd = sb + 2 * Qs;
             const int *mbv = (r > 0) ? mbox + (s % kmb) * Qm : nullptr;
-            const bool has_ma = s > 0;
+            const bool has_ma = xs > 0;       // a previous pixel in this direction
+            const bool nxt = xs + 1 < W;      // a next pixel in this direction
             unsigned long long key = ~0ull;           // final pass: (S_Omega, q) minimum
-            const int x = incx ? s : W - 1 - s;
             const int xn = incx ? x + 1 : x - 1;
-            const bool a_out = A.write_a && s + 1 < W;
+            const bool a_out = write_a && nxt;
             const int tag_out = A.tag0 + s / ring;
             int *const pMa = a_out ? Ma + ((size_t)y * W + xn) * Qm : nullptr;
-            int *const pMb = (has_next && A.write_b) ? Mb + ((size_t)y_next * W + x) * Qm : nullptr;
+            int *const pMb = (has_next && write_b) ? Mb + ((size_t)y_next * W + x) * Qm : nullptr;
             int *const pBox = to_mbox ? nx_mbox + (s % kmb) * Qm : nullptr;
             int2 *const pRec = to_ring ? ll_out + (size_t)(s % ring) * Qm : nullptr;
             // message into the next column of the row (m_a) and into the next row (m_b)
             auto emit_a = [&](int q, int oa) {
-                maS[q] = oa;
+                maS[q] = nxt ? oa : 0;  // the first pixel of a sweep direction gets a zero m_a
                 if (pMa) pMa[q] = oa;
             };
             auto emit_b = [&](int q, int ob) {
@@ -593,7 +626,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             auto barrier2 = [&](int ja, int jb) -> bool {
                 ja = __reduce_min_sync(kAllLanes, ja);
                 jb = __reduce_min_sync(kAllLanes, jb);
-                if (A.final_) {
+                if (fin) {
                     const unsigned hi = __reduce_min_sync(kAllLanes, (unsigned)(key >> 32));
                     const unsigned lo =
                         __reduce_min_sync(kAllLanes, (unsigned)(key >> 32) == hi ? (unsigned)key : 0xffffffffu);
@@ -602,7 +635,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 if (lane == 0) {
                     wmin[2 * wt] = ja;
                     wmin[2 * wt + 1] = jb;
-                    if (A.final_) wkey[wt] = key;
+                    if (fin) wkey[wt] = key;
                 }
                 if (sync_or(tm, T, *s_abort != 0)) return false;  // barrier 2
                 // every lane of the team is done with this column's m_b
@@ -610,8 +643,8 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                     if (from_mbox) st_rel_cta(misc + 16, s + 1);
                     // the consumer's record loads above have returned (their values
                     // went through shared memory and a barrier) before this store
-                    if (from_ring && ((s & 3) == 3 || s + 1 == W)) st_relaxed_gpu(A.cons + band - 1, (unsigned)(s + 1));
-                    if (A.final_) {
+                    if (from_ring && ((s & 3) == 3 || s + 1 == ncol)) st_relaxed_gpu(A.cons + band - 1, (unsigned)(s + 1));
+                    if (fin) {
                         unsigned long long best = wkey[0];
                         for (int w = 1; w < T; ++w) best = min(best, wkey[w]);
                         int q = (int)(best & 0xffffffffu);
@@ -641,7 +674,6 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             const int *cs = sb + 3 * Qs;
             auto origin = [&](int c, int Qr) { return min(max(c, hN), Qr - 1 - hN) - hN; };
             const int lo0 = origin(cs[0], A.Q0w), lo1 = R == 2 ? origin(cs[1], A.Q1w) : 0;
-            const bool nxt = s + 1 < W;
             const int la0 = nxt ? origin(cs[R], A.Q0w) : lo0;
             const int la1 = R == 2 ? (nxt ? origin(cs[R + 1], A.Q1w) : lo1) : 0;
             const int lb0 = has_next ? origin(cs[2 * R], A.Q0w) : lo0;
@@ -651,7 +683,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             // old messages no pass has written yet come from sums that are still
             // zero: M(0) between the boxes (the c neighbour is the next pixel of
             // the row, the d neighbour the same column of the next row)
-            const bool c_m0 = !A.read_c && nxt, d_m0 = !A.read_d && has_next;
+            const bool c_m0 = !read_c && nxt, d_m0 = !A.read_d && has_next;
             const int v = R == 2 ? (lane < N ? 0 : (lane < 2 * N ? 1 : -1)) : (lane < 2 ? lane : -1);
             const int l = R == 2 ? lane - (v > 0 ? N : 0) : 0;
             const int d0 = (v == 1 ? lb0 : la0) - lo0, d1 = (v == 1 ? lb1 : la1) - lo1;
@@ -686,7 +718,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                         const int t = lds(aC + o4) + lds(aMa + o4) + lds(aMb + o4);
                         const int c = c_m0 ? m0(i, l, la0, la1) : lds(aCc + o4);
                         const int d = d_m0 ? m0(i, l, lb0, lb1) : lds(aCd + o4);
-                        if (A.final_ && v == 0)
+                        if (fin && v == 0)
                             key = min(key, ((unsigned long long)((unsigned)(t + c + d) ^ 0x80000000u) << 32) | (unsigned)q);
                         hv[i] = floor_half(v ? t + c - d : t + d - c);
                         lmin0 = min(lmin0, hv[i]);
@@ -815,7 +847,10 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             case 13: ok = body(std::integral_constant<int, 13>()); break;
             default: ok = body(std::integral_constant<int, 15>()); break;
             }
-            if (!ok) break;
+            if (!ok) {
+                aborted = true;
+                break;
+            }
             } else if constexpr (LEAN) {
             // Lean form (two or more axes): lane lv of vector v (warps
             // [v*Tv, v*Tv + Tv)) owns whole lines; the backward sweep goes to the
@@ -829,7 +864,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             const unsigned aC = saddr(sC), aCc = saddr(sc), aCd = saddr(sd);
             const unsigned aMa = saddr(maS), aMb = saddr(mbox + (s % kmb) * Qm);
             const int lam = A.lam;
-            const bool final_a = A.final_ && vsel == 0;
+            const bool final_a = fin && vsel == 0;
             int vmin = kBig;                           // minimum of this vector's halved sums
             {
                 const int L = A.ax[0].L, nl = A.ax[0].nlines;
@@ -847,13 +882,17 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                     vmin = min(vmin, lm);
                 }
             }
-            if (!barrier2(vsel ? kBig : vmin, vsel ? vmin : kBig)) break;
+            if (!barrier2(vsel ? kBig : vmin, vsel ? vmin : kBig)) {
+                aborted = true;
+                break;
+            }
             {
                 int gv = kBig;
                 if (!per_axis)
                     for (int w = vsel * Tv; w < vsel * Tv + Tv; ++w) gv = min(gv, wmin[2 * w + vsel]);
                 LeanOut O;
                 O.aMa = aMa;
+                O.zero_a = !nxt;
                 O.aBox = pBox ? saddr(pBox) : 0u;
                 O.pMa = pMa;
                 O.pMb = pMb;
@@ -903,7 +942,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                             if (mbv) t += mbv[q];
                             ha[i] = floor_half(t + d - c);
                             hb[i] = floor_half(t + c - d);
-                            if (A.final_) {
+                            if (fin) {
                                 const int so = t + c + d;
                                 key = min(key, ((unsigned long long)((unsigned)so ^ 0x80000000u) << 32) | (unsigned)q);
                             }
@@ -938,7 +977,10 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                     }
                 }
             }
-            if (!barrier2(ja, jb)) break;
+            if (!barrier2(ja, jb)) {
+                aborted = true;
+                break;
+            }
             // ---- phases 1 .. R-1: sweeps of the other axes, clip, emit ----
             if (R >= 2) {
                 int ga = kBig, gb = kBig;
@@ -996,6 +1038,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 __syncwarp();
                 if (lane == 0) st_rel_cta(produced + wt, s + 1);
             }
+        }
         }
         cp_async_wait_0();
     }

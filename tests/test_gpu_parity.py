@@ -32,8 +32,10 @@ def host(t):
 @pytest.fixture(autouse=True)
 def reset_tuning(edp_lib):
     edp_lib.set_tuning(0, 0, False)
+    edp_lib.set_pass_pairs(True)
     yield
     edp_lib.set_tuning(0, 0, False)
+    edp_lib.set_pass_pairs(True)
 
 
 # --------------------------------------------------------------------------
@@ -254,6 +256,64 @@ def test_edp_one_axis_rows_per_block(edp_lib, rows):
     edp_lib.set_tuning(rows, 0, False)
     got = host(edp_lib.solve(dev(C), sp((64,)), prior, iters=2))
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+@pytest.mark.parametrize("Q,W,H,rows", [(64, 41, 37, 2), (64, 41, 37, 8), (7, 5, 23, 3), (33, 1, 9, 2),
+                                        (100, 9, 1, 2), (130, 30, 17, 5)])
+@pytest.mark.parametrize("iters", [1, 3])
+def test_edp_pass_schedule(edp_lib, pairs, Q, W, H, rows, iters):
+    """Paired sweeps (P1 + P2, P3 + P4 in one launch each) and one launch per
+    pass give the oracle's labels: the schedule never changes a value."""
+    rng = np.random.default_rng(Q * 7 + W + H + iters)
+    C = rng.integers(0, 21, size=(H, W, Q)).astype(np.int32)
+    prior = {"lam": int(rng.integers(1, 25)), "g": 4, "l1": 1, "mode": "joint"}
+    want = oracle.edp(C, sp((Q,)), prior, iters=iters, tier=1)
+    edp_lib.set_pass_pairs(pairs)
+    edp_lib.set_tuning(rows, 0, False)
+    assert edp_lib.pass_launches(sp((Q,)), iters) == (2 if pairs else 4) * iters
+    got = host(edp_lib.solve(dev(C), sp((Q,)), prior, iters=iters))
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+@pytest.mark.parametrize("Q,mode,form", [((9, 9), "per_axis", 0), ((33, 33), "joint", 0), ((17, 9), "per_axis", 0),
+                                         ((5, 4), "per_axis", 2), ((17, 17, 9), "joint", 0),
+                                         ((5, 5, 3), "per_axis", 2), ((16,), "joint", 1)])
+@pytest.mark.parametrize("iters", [1, 3])
+def test_edp_pass_schedule_multi_axis(edp_lib, pairs, Q, mode, form, iters):
+    """The multi-axis kernel (whole-line form 0, lane-group form 2, one-axis
+    spaces on it with form 1) under both schedules, with bands spanning
+    several blocks and teams (2 rows per block)."""
+    rng = np.random.default_rng(sum(Q) * 11 + form + iters)
+    n = int(np.prod(Q))
+    H, W = (11, 13) if n > 500 else (19, 25)
+    C = rng.integers(0, 21, size=(H, W, n)).astype(np.int32)
+    prior = {"lam": int(rng.integers(1, 12)), "g": int(rng.integers(1, 5)), "l1": 1, "mode": mode}
+    want = oracle.edp(C, sp(Q), prior, iters=iters, tier=1)
+    edp_lib.set_pass_pairs(pairs)
+    edp_lib.set_tuning(2, 0, form)
+    got = host(edp_lib.solve(dev(C), sp(Q), prior, iters=iters))
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+@pytest.mark.parametrize("Q,win,l1", [((13, 13), 5, 1), ((11,), 7, 1), ((13, 13), 5, 2)])
+def test_windowed_pass_schedule(edp_lib, pairs, Q, win, l1):
+    rng = np.random.default_rng(sum(Q) + win + l1)
+    H, W = 13, 19
+    R = len(Q)
+    space = sp(Q, [-(q // 2) for q in Q], [1] * R)
+    I0 = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+    I1 = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+    centre = np.stack([rng.integers(-2, q + 2, size=(H, W)) for q in Q], axis=-1).astype(np.int32)
+    prior = {"lam": int(rng.integers(2, 9)), "g": 3, "l1": l1, "mode": "per_axis"}
+    Cw = oracle.cost_window(I0, I1, None, space, 1, 30, centre, win)
+    want = oracle.edp_windowed(Cw, centre, space, prior, win, iters=2)
+    edp_lib.set_pass_pairs(pairs)
+    edp_lib.set_tuning(3, 0, 0)
+    got = edp_lib.solve_windowed(dev(Cw), dev(centre), win, space, prior, iters=2)
+    assert np.array_equal(host(got), want)
 
 
 @pytest.mark.parametrize("form", [1, 2])
