@@ -364,7 +364,29 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                     const int2 *p = (w > 0) ? mb_in + (s % kMb) * Qp : ll_in + (size_t)s * Q;
                     const int want = (w > 0) ? s + 1 : A.tag;
                     const unsigned long long tw = (A.trace && w == 0) ? global_ns() : 0;
-                    while (true) {
+                    // first look straight-line (the record is usually there), then the
+                    // bounded spin
+                    bool ok0 = true;
+                    if (w > 0) {
+#pragma unroll
+                        for (int i = 0; i < E; ++i) {
+                            if (q0 + i < Q) {
+                                const int2 t = lds_rec(p + i);
+                                mb[i] = t.x;
+                                ok0 = ok0 && (t.y == want);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < E; ++i) {
+                            if (q0 + i < Q) {
+                                const int2 t = ld_rec(p + i);
+                                mb[i] = t.x;
+                                ok0 = ok0 && (t.y == want);
+                            }
+                        }
+                    }
+                    if (!__all_sync(kFull, ok0)) while (true) {
                         bool ok = true;
 #pragma unroll
                         for (int i = 0; i < E; ++i) {
