@@ -336,10 +336,10 @@ def time_solve_rows(edp, synth, torch):
     H, W, Q = C.shape
     ws = edp.workspace(edp.OP_SOLVE, W, H, w["space"], w["prior"], 1)
     lab = torch.empty((H, W), dtype=torch.int32, device="cuda")
-    nl = edp.pass_launches(w["space"], 1)
-    evs = [ev() for _ in range(2 * nl)]
+    evs = [ev() for _ in range(8)]
     edp.set_profile_events(evs)
     ms = timed(lambda: edp.solve(C, w["space"], w["prior"], iters=1, ws=ws, labels=lab), reps=10)
+    nl = edp.last_pass_launches()
     pass_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(nl)]
     edp.set_profile_events(None)
     nbytes = sum(launch_bytes(nl, W, H, Q, 1))
@@ -482,8 +482,7 @@ def run_gpu(args, world, rank, local):
     labels = torch.empty((H, W), dtype=torch.int32, device=dev)
     energy4 = torch.empty(4, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
-    npass = edp.pass_launches(space, j)  # scan-pass launches per solve
-    pev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * npass)]
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(8 * j)]
 
     def step():
         edp.solve_images(I0, I1, None, space, prior, w["l2"], w["cmax"], iters=j, ws=ws, labels=labels,
@@ -492,6 +491,7 @@ def run_gpu(args, world, rank, local):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    npass = edp.last_pass_launches()  # scan-pass launches per solve (2 per iteration for paired sweeps)
     launches_per_step = 1 + npass + 1  # cost volume, scan passes, energy
 
     def timed_region():

@@ -135,21 +135,27 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
  * Not thread-safe with concurrent solves. */
 int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, int general_kernel);
 
-/* Pass schedule of edp_solve, edp_solve_images and edp_solve_windowed
- * (Sec. 4.2: P1..P4 per iteration).  on = 1 (the default): P1 and P2, and
- * P3 and P4, which share their vertical direction, run as one paired sweep
- * each (two launches per iteration; each row sweeps left to right, then
- * right to left, so the second pass starts on a row as soon as the first has
- * finished it).  on = 0: one launch per pass.  Results never depend on it
- * (edp_solve_batched always runs one pass per work item).  Returns
- * EDP_ERR_INVALID_ARG unless on is 0 or 1.  Not thread-safe with concurrent
- * solves. */
-int edp_set_pass_pairs(int on);
+/* Pass schedule of edp_solve, edp_solve_images, edp_solve_windowed and
+ * edp_solve_batched (Sec. 4.2: P1..P4 per iteration).  P1 and P2, and P3 and
+ * P4, share their vertical direction and can run as one paired sweep each:
+ * every row sweeps left to right, then right to left, so the second pass
+ * starts on a row as soon as the first has finished it (two launches per
+ * iteration instead of four).
+ *   mode 0: one launch per pass;
+ *   mode 1: paired sweeps always;
+ *   mode 2 (the default): paired sweeps when every row band of the problem
+ *           has a block at once (a paired band holds its block twice as long,
+ *           which costs more than it saves when bands wait for blocks);
+ *           edp_solve_batched pairs in modes 1 and 2.
+ * Results never depend on it.  Returns EDP_ERR_INVALID_ARG unless mode is 0,
+ * 1 or 2.  Not thread-safe with concurrent solves. */
+int edp_set_pass_pairs(int mode);
 
-/* Number of scan-pass launches edp_solve makes for `iters` iterations on a
- * label space of R axes and Q labels under the current schedule: 2 * iters
- * for paired sweeps, else 4 * iters (0 if iters, R or Q is below 1). */
-int edp_pass_launches(int R, int Q, int iters);
+/* Scan-pass launches of the most recent edp_solve, edp_solve_images or
+ * edp_solve_windowed call in this process (2 per iteration for paired
+ * sweeps, else 4; 0 before the first solve).  The launches are counted as by
+ * edp_set_profile_events.  Not thread-safe with concurrent solves. */
+int edp_last_pass_launches(void);
 
 /* Per-launch timing hook: while set, edp_solve (and edp_solve_images) record
  * events[2*i] / events[2*i + 1] (cudaEvent_t handles created by the caller)

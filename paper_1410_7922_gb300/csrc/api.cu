@@ -23,7 +23,8 @@ int g_tune_e = 0;        // labels per lane target override, scanline DP (0 = au
 int g_tune_t = 0;        // warps per row override, multi-axis scan pass (0 = automatic)
 int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass kernel
 int g_generic_team = 0;  // 1: multi-axis problems take the generic team body (tests)
-int g_pass_pairs = 1;    // 1: P1 + P2 and P3 + P4 run as paired sweeps (one launch each)
+int g_pass_pairs = 2;    // P1 + P2 and P3 + P4 as paired sweeps: 0 never, 1 always, 2 when every band is resident
+int g_last_launches = 0; // scan-pass launches of the most recent solve
 void *const *g_prof_events = nullptr;  // optional per-pass events (profiling hook)
 int g_prof_n = 0;
 unsigned long long *g_trace = nullptr;  // optional per-band trace buffer (device)
@@ -299,11 +300,9 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
     if (P->r1) {
         const int E = (g.Q + 31) / 32;
         int NWR = fixed_threads ? fixed_threads / 32 : (g_tune_rb > 0 ? g_tune_rb : 8);
-        if (!fixed_threads) NWR = std::max(kMinRowsR1, std::min(NWR, std::min(8, H)));  // kernel built for <= 256 threads
-        // the batched kernel (fixed_threads) runs the staged body
-        auto smem_of = [&](int n) { return fixed_threads ? pass_r1_staged_smem(n, E) : pass_r1_smem(n, E); };
-        while (!fixed_threads && NWR > kMinRowsR1 && smem_of(NWR) > (size_t)kMaxSmem) --NWR;
-        P->smem = smem_of(NWR);
+        if (!fixed_threads) NWR = std::max(kMinRowsR1, std::min(NWR, std::min(pass_r1_max_rows(E, p->l1), H)));
+        while (!fixed_threads && NWR > kMinRowsR1 && pass_r1_smem(NWR, E) > (size_t)kMaxSmem) --NWR;
+        P->smem = pass_r1_smem(NWR, E);
         if (P->smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
         PassR1Args &a = P->o;
         a.C = C;
@@ -453,6 +452,8 @@ size_t control_bytes(const SolvePlan &P, int W, int Q) {
     return P.r1 ? P.L.ll + (size_t)P.nbands * 2 * W * Q * 8 : P.L.ll + (size_t)P.nbands * P.ta.ring * P.L.Qm * 8;
 }
 
+bool pairs_for(bool resident) { return g_pass_pairs == 1 || (g_pass_pairs == 2 && resident); }
+
 // Launch k of iteration `it`: one pass (k = 0..3), or with paired sweeps the
 // pair k = 0 (P1 + P2) or 1 (P3 + P4).  Sets the first pass and the flags of
 // both passes of the launch.
@@ -481,19 +482,25 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     int rc = plan_solve(C, W, H, g, p, labels, ws, &P);
     if (rc) return rc;
     if ((rc = cuda_status(cudaMemsetAsync(ws, 0, control_bytes(P, W, g.Q), st)))) return rc;
-    int grid_t = 1;
+    int grid_t = 1, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    bool resident;  // every row band has a block at once
     if (!P.r1) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int occ = std::max(1, edp_pass_team_occupancy(P.em, P.ta.lean, 0, P.threads, P.smem));
         grid_t = std::min(P.nbands, occ * sms);
         // a smaller resident set than the ring was sized for could stall the back-pressure
         if (grid_t < P.nbands && team_ring(2 * W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
+        resident = grid_t >= P.nbands;
+    } else {
+        resident = P.nbands <= std::max(1, edp_pass_r1_occupancy(P.o.E, P.o.l1, P.threads, P.smem)) * sms;
     }
-    // paired sweeps: two launches per iteration (P1 + P2, P3 + P4)
-    const bool pairs = g_pass_pairs;
+    // paired sweeps: two launches per iteration (P1 + P2, P3 + P4).  They
+    // shorten the wavefront when every band runs at once; when bands wait for
+    // a free block, a paired band holds its block twice as long.
+    const bool pairs = pairs_for(resident);
     const int per_it = pairs ? 2 : 4;
+    g_last_launches = per_it * p->iters;
     for (int it = 0; it < p->iters; ++it) {
         for (int k = 0; k < per_it; ++k) {
             const int launch = it * per_it + k;
@@ -628,16 +635,13 @@ int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, i
     return EDP_OK;
 }
 
-int edp_set_pass_pairs(int on) {
-    if (on != 0 && on != 1) return EDP_ERR_INVALID_ARG;
-    g_pass_pairs = on;
+int edp_set_pass_pairs(int mode) {
+    if (mode < 0 || mode > 2) return EDP_ERR_INVALID_ARG;
+    g_pass_pairs = mode;
     return EDP_OK;
 }
 
-int edp_pass_launches(int R, int Q, int iters) {
-    if (iters < 1 || R < 1 || Q < 1) return 0;
-    return (g_pass_pairs ? 2 : 4) * iters;
-}
+int edp_last_pass_launches(void) { return g_last_launches; }
 
 int edp_set_profile_events(void *const *events, int n_events) {
     if (n_events < 0 || (n_events > 0 && !events)) return EDP_ERR_INVALID_ARG;
@@ -920,7 +924,8 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     static BatchArgs B;  // too large for the stack of some callers; filled and copied into the launch
     memset(&B, 0, sizeof B);
     B.n = n;
-    B.slots = 4 * iters;
+    B.pairs = g_pass_pairs != 0;  // the wave's bands share the blocks: the pair halves the slots
+    B.slots = (B.pairs ? 2 : 4) * iters;
     B.queue = reinterpret_cast<unsigned *>(ws + kHeader);
     B.done = reinterpret_cast<unsigned *>(ws + kHeader + 256);
     B.status = status;
@@ -971,7 +976,7 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
         int32_t *C = reinterpret_cast<int32_t *>(pws + L.end);
         const SolvePlan &P = plans[k];
         off += problem_bytes(pr, g);
-        if (!P.r1 && team_ring(pr.W, occ * sms) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
+        if (!P.r1 && team_ring(B.pairs ? 2 * pr.W : pr.W, occ * sms) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
         BatchProblem &bp = B.p[slot_of[k]];
         bp.r1 = P.r1;
         bp.nbands = P.nbands;
@@ -1198,8 +1203,9 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
     a.grid = std::min(a.nbands, occ * sms);
     if (a.grid < a.nbands && team_ring(2 * W, a.grid) > a.ring) return EDP_ERR_UNSUPPORTED;
     if ((rc = cuda_status(cudaMemsetAsync(w, 0, L.ll + (size_t)a.nbands * a.ring * L.Qm * 8, st)))) return rc;
-    const bool pairs = g_pass_pairs;
+    const bool pairs = pairs_for(a.grid >= a.nbands);
     const int per_it = pairs ? 2 : 4;
+    g_last_launches = per_it * params->iters;
     for (int it = 0; it < params->iters; ++it)
         for (int k = 0; k < per_it; ++k) {
             const int launch = it * per_it + k;

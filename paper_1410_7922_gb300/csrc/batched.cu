@@ -14,7 +14,6 @@
 // kernel's parameter block (no host tables, so the launch can be captured in
 // a CUDA graph).
 #include "pass_r1.cuh"
-#include "pass_r1_staged.cuh"
 #include "pass_team.cuh"
 
 namespace edp {
@@ -56,8 +55,13 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
         }
         __syncthreads();
         if (s_abort) return;
-        const int it = slot / 4, pass = slot % 4;
+        // slot: one pass, or with B.pairs one paired sweep (P1 + P2, P3 + P4)
+        const int per_it = B.pairs ? 2 : 4;
+        const int it = slot / per_it, kk = slot % per_it;
+        const int pass = B.pairs ? 2 * kk : kk;
+        const int pslot = it * 4 + pass;  // the first pass's slot: record tags, consumed counters
         const PassFlags f = pass_flags(it, pass, P.iters);
+        const PassFlags f2 = pass_flags(it, B.pairs ? pass + 1 : pass, P.iters);
         bool ok;
         if (P.r1) {
             PassR1Args a = P.o;
@@ -67,14 +71,19 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
             a.write_a = f.write_a;
             a.write_b = f.write_b;
             a.final_ = f.final_;
-            a.tag = slot + 1;
+            a.pair = B.pairs;
+            a.read_c2 = f2.read_c;
+            a.write_a2 = f2.write_a;
+            a.write_b2 = f2.write_b;
+            a.final2 = f2.final_;
+            a.tag = pslot + 1;
             if (QUAD && a.l1 == 2)
                 ok = r1_dispatch(a.E, [&](auto e) {
-                    return staged::r1_band_staged<decltype(e)::value, QUAD>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+                    return r1_band<decltype(e)::value, QUAD>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
                 });
             else
                 ok = r1_dispatch(a.E, [&](auto e) {
-                    return staged::r1_band_staged<decltype(e)::value, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+                    return r1_band<decltype(e)::value, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
                 });
         } else {
             TeamArgs a = P.t;
@@ -84,8 +93,13 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
             a.write_a = f.write_a;
             a.write_b = f.write_b;
             a.final_ = f.final_;
-            a.cons = P.cons + (size_t)slot * P.nbands;
-            a.tag0 = 1 + slot * P.laps;
+            a.pair = B.pairs;
+            a.read_c2 = f2.read_c;
+            a.write_a2 = f2.write_a;
+            a.write_b2 = f2.write_b;
+            a.final2 = f2.final_;
+            a.cons = P.cons + (size_t)pslot * P.nbands;
+            a.tag0 = 1 + pslot * P.laps;
             if (QUAD && a.lean && a.l1 == 2)
                 ok = team_band<QUAD ? 2 : LM, true>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
             else if (a.lean)
@@ -116,13 +130,6 @@ static void *batched_kernel_for(int lm, int gen) {
     // dispatches on the line lengths itself otherwise)
     if (lm == 2) return gen ? batched_kernel<33, true, true>() : batched_kernel<33, false, true>();
     return gen ? batched_kernel<33, true, false>() : batched_kernel<33, false, false>();
-}
-
-// shared memory of the staged one-axis body: per warp a (kPf + 1)-column
-// ring of C, m_c, m_d; the mailbox ring and the produced / consumed counters
-size_t pass_r1_staged_smem(int NWR, int E) {
-    const size_t Qp = 32 * (size_t)E;
-    return ((size_t)NWR * (staged::kPf + 1) * 3 * Qp + (size_t)NWR * staged::kMb * Qp + 2 * (size_t)NWR) * 4;
 }
 
 int edp_batched_occupancy(int lm, int gen, int threads, size_t smem) {

@@ -4,8 +4,13 @@
 
 namespace edp {
 
+// rows (warps) per block the build allows: 16 where the registers fit 512
+// threads (E <= 4, linear prior), else 8
 template <int E, bool QUAD>
-__global__ void __launch_bounds__(256, 1) edp_pass_r1_kernel(PassR1Args A) {
+constexpr int r1_max_rows() { return (E <= 4 && !QUAD) ? 16 : 8; }
+
+template <int E, bool QUAD>
+__global__ void __launch_bounds__(32 * r1_max_rows<E, QUAD>(), 1) edp_pass_r1_kernel(PassR1Args A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
     __shared__ volatile int s_abort;
@@ -37,10 +42,20 @@ R1Kernel r1_kernel_for(int E) {
     }
 }
 
+int pass_r1_max_rows(int E, int l1) { return (E <= 4 && l1 != 2) ? 16 : 8; }
+
 size_t pass_r1_smem(int NWR, int E) {
     const size_t Qp = 32 * (size_t)E;
     // staging rings, mailbox records, consumed counters
     return ((size_t)NWR * (kPf + 1) * 3 * Qp + 2 * (size_t)NWR * kMb * Qp + (size_t)NWR) * 4;
+}
+
+int edp_pass_r1_occupancy(int E, int l1, int threads, size_t smem) {
+    const R1Kernel k = l1 == 2 ? r1_kernel_for<true>(E) : r1_kernel_for<false>(E);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem) != cudaSuccess) return 0;
+    return occ;
 }
 
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st) {

@@ -91,8 +91,9 @@ struct PassR1Args {
     unsigned long long *trace;
 };
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st);
+int edp_pass_r1_occupancy(int E, int l1, int threads, size_t smem);
 size_t pass_r1_smem(int NWR, int E);
-size_t pass_r1_staged_smem(int NWR, int E);  // the batched kernel's one-axis body (batched.cu)
+int pass_r1_max_rows(int E, int l1);  // rows per block the one-axis build for E labels per lane allows
 
 // batched solve: up to kMaxBatch problems of one wave, passed by value
 constexpr int kMaxBatch = 64;
@@ -109,7 +110,8 @@ struct BatchProblem {
 };
 struct BatchArgs {
     int n;
-    int slots;            // 4 * iters (shared by the wave)
+    int pairs;            // 1: a slot is a paired sweep (P1 + P2 or P3 + P4)
+    int slots;            // 4 * iters, or 2 * iters with pairs (shared by the wave)
     int per_slot;         // sum of nbands over the wave
     int prefix[kMaxBatch + 1];
     unsigned *queue;      // work-item counter

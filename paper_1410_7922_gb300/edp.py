@@ -68,7 +68,7 @@ def load() -> ctypes.CDLL:
         "edp_set_tuning": ([I, I, I, I], I),
         "edp_set_profile_events": ([P, I], I),
         "edp_set_pass_pairs": ([I], I),
-        "edp_pass_launches": ([I, I, I], I),
+        "edp_last_pass_launches": ([], I),
         "edp_set_trace": ([P, SZ], I),
         "edp_cost_volume": ([P, P, P, I, I, I, LS, PR, P, P], I),
         "edp_scanline_dp": ([P, I, I, LS, PR, P, P, P, SZ, P], I),
@@ -114,7 +114,7 @@ def exported_symbols() -> list[str]:
             "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_forward", "edp_net_backward",
             "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc", "edp_coarse_labels",
             "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_scanline_marginals",
-            "edp_set_pass_pairs", "edp_pass_launches"]
+            "edp_set_pass_pairs", "edp_last_pass_launches"]
 
 
 def status_string(code: int) -> str:
@@ -192,18 +192,21 @@ def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0, general_kernel
 _prof_keep = None
 
 
-def set_pass_pairs(on: bool) -> None:
-    """Paired sweeps P1 + P2, P3 + P4 (default on) or one launch per pass."""
-    _check(load().edp_set_pass_pairs(1 if on else 0), "set_pass_pairs")
+PAIRS_OFF, PAIRS_ON, PAIRS_AUTO = 0, 1, 2
 
 
-def pass_launches(space: dict, iters: int) -> int:
-    """Scan-pass launches of one solve under the current schedule."""
-    Qr = [q for q in space["Q"][:space["R"]] if q > 1]
-    Q = 1
-    for q in Qr:
-        Q *= q
-    return int(load().edp_pass_launches(max(1, len(Qr)), Q, iters))
+def set_pass_pairs(mode) -> None:
+    """Pass schedule: PAIRS_OFF (one launch per pass), PAIRS_ON (paired sweeps
+    P1 + P2, P3 + P4) or PAIRS_AUTO (paired when every row band is resident;
+    the default).  A bool selects PAIRS_ON / PAIRS_OFF."""
+    if isinstance(mode, bool):
+        mode = PAIRS_ON if mode else PAIRS_OFF
+    _check(load().edp_set_pass_pairs(int(mode)), "set_pass_pairs")
+
+
+def last_pass_launches() -> int:
+    """Scan-pass launches of the most recent solve in this process."""
+    return int(load().edp_last_pass_launches())
 
 
 def set_profile_events(events) -> None:

@@ -32,10 +32,10 @@ def host(t):
 @pytest.fixture(autouse=True)
 def reset_tuning(edp_lib):
     edp_lib.set_tuning(0, 0, False)
-    edp_lib.set_pass_pairs(True)
+    edp_lib.set_pass_pairs(edp_lib.PAIRS_AUTO)
     yield
     edp_lib.set_tuning(0, 0, False)
-    edp_lib.set_pass_pairs(True)
+    edp_lib.set_pass_pairs(edp_lib.PAIRS_AUTO)
 
 
 # --------------------------------------------------------------------------
@@ -271,8 +271,8 @@ def test_edp_pass_schedule(edp_lib, pairs, Q, W, H, rows, iters):
     want = oracle.edp(C, sp((Q,)), prior, iters=iters, tier=1)
     edp_lib.set_pass_pairs(pairs)
     edp_lib.set_tuning(rows, 0, False)
-    assert edp_lib.pass_launches(sp((Q,)), iters) == (2 if pairs else 4) * iters
     got = host(edp_lib.solve(dev(C), sp((Q,)), prior, iters=iters))
+    assert edp_lib.last_pass_launches() == (2 if pairs else 4) * iters
     assert np.array_equal(got, want)
 
 
@@ -441,8 +441,11 @@ def _oracle_problem(w, iters):
     return lab, oracle.energy(C, lab, w["space"], w["prior"])
 
 
+@pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("iters", [1, 2])
-def test_batched_matches_oracle(edp_lib, iters):
+def test_batched_matches_oracle(edp_lib, iters, pairs):
+    """Every body of the batched kernel, one pass per work item or paired sweeps."""
+    edp_lib.set_pass_pairs(pairs)
     items = _batch_items(edp_lib, iters=iters)
     probs = edp_lib.make_problems(items)
     ws = torch.empty(edp_lib.batch_workspace_size(probs), dtype=torch.uint8, device="cuda")
