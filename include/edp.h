@@ -146,7 +146,8 @@ int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, i
  *   mode 2 (the default): paired sweeps when every row band of the problem
  *           has a block at once (a paired band holds its block twice as long,
  *           which costs more than it saves when bands wait for blocks);
- *           edp_solve_batched pairs in modes 1 and 2.
+ *           edp_solve_batched pairs only in mode 1 (its bands share the
+ *           blocks).
  * Results never depend on it.  Returns EDP_ERR_INVALID_ARG unless mode is 0,
  * 1 or 2.  Not thread-safe with concurrent solves. */
 int edp_set_pass_pairs(int mode);

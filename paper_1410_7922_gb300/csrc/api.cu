@@ -924,7 +924,10 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     static BatchArgs B;  // too large for the stack of some callers; filled and copied into the launch
     memset(&B, 0, sizeof B);
     B.n = n;
-    B.pairs = g_pass_pairs != 0;  // the wave's bands share the blocks: the pair halves the slots
+    // the wave's bands share the blocks, so a paired band holding its block twice
+    // as long costs more than the shorter wavefront saves (measured on the
+    // 64-problem batch): pairs only when asked for explicitly
+    B.pairs = g_pass_pairs == 1;
     B.slots = (B.pairs ? 2 : 4) * iters;
     B.queue = reinterpret_cast<unsigned *>(ws + kHeader);
     B.done = reinterpret_cast<unsigned *>(ws + kHeader + 256);
