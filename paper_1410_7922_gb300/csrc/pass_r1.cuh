@@ -36,8 +36,9 @@
 namespace edp {
 
 namespace {
-constexpr int kPf = 7;   // prefetch distance in columns (ring of kPf + 1 slots)
-constexpr int kMb = 8;   // mailbox ring depth between rows of a block
+constexpr int kPf = 7;   // prefetch distance in columns (ring of kPf + 1 slots, a power of two)
+constexpr int kMb = 8;   // mailbox ring depth between rows of a block (a power of two)
+static_assert(((kPf + 1) & kPf) == 0 && (kMb & (kMb - 1)) == 0, "ring sizes must be powers of two");
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ int redux_min(int v) { return __reduce_min_sync(kFull, v); }
@@ -315,7 +316,7 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
             int xp = 0;
             auto prefetch = [&]() {
                 if (xp < W && q0 < Q) {
-                    const unsigned dst = ring_s + (unsigned)((h * W + xp) % (kPf + 1)) * kSlot;
+                    const unsigned dst = ring_s + ((unsigned)(h * W + xp) & kPf) * kSlot;
                     if (vw == 4)
                         cp_chunks<E, (E % 4 == 0 ? 4 : 1)>(dst, pfC, q0, Q, true);
                     else if (vw == 2)
@@ -344,7 +345,7 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                 prefetch();
                 cp_async_wait_n<kPf>();
                 // ---- work that does not wait for the row above ----
-                const unsigned src = ring_s + (unsigned)(s % (kPf + 1)) * kSlot;
+                const unsigned src = ring_s + ((unsigned)s & kPf) * kSlot;
                 int cv[E], mc[E], md[E], pa[E], pb[E];
                 lds_vec<E>(src, cv);
                 lds_vec<E>(src + Qp * 4, mc);
@@ -361,7 +362,7 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                 if (r > 0) {
                     long long spins = 0;
                     bool bad = false;
-                    const int2 *p = (w > 0) ? mb_in + (s % kMb) * Qp : ll_in + (size_t)s * Q;
+                    const int2 *p = (w > 0) ? mb_in + (s & (kMb - 1)) * Qp : ll_in + (size_t)s * Q;
                     const int want = (w > 0) ? s + 1 : A.tag;
                     const unsigned long long tw = (A.trace && w == 0) ? global_ns() : 0;
                     // first look straight-line (the record is usually there), then the
@@ -416,7 +417,8 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                     // issued after the vote on every lane's loaded tags: the
                     // loads of the slot have returned before the producer can
                     // see this count and overwrite it
-                    if (w > 0 && lane == 0) st_relaxed_shared(consumed + w, s + 1);
+                    // (every lane stores the same count: no divergent branch)
+                    if (w > 0) st_relaxed_shared(consumed + w, s + 1);
                 }
                 // ---- sums (Eq. DP_2D_base), halving, min search M ----
                 int ha[E], hb[E];
@@ -464,7 +466,7 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                                 break;
                             }
                         }
-                        int2 *p = mb_out + (s % kMb) * Qp;
+                        int2 *p = mb_out + (s & (kMb - 1)) * Qp;
 #pragma unroll
                         for (int i = 0; i < E; ++i)
                             if (q0 + i < Q) sts_rec(p + i, hb[i], s + 1);
