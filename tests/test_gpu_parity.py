@@ -297,6 +297,27 @@ def test_edp_pass_schedule_multi_axis(edp_lib, pairs, Q, mode, form, iters):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("Q,mode_prior", [((16,), "joint"), ((5, 4), "per_axis"), ((9, 9), "per_axis")])
+def test_edp_pass_schedule_many_bands(edp_lib, mode, Q, mode_prior):
+    """More row bands than blocks can be resident at once (12000 rows, 2 per
+    block, more than 152 SMs x 32 blocks): the automatic schedule falls back to
+    one launch per pass, a forced pairing holds each block for a paired band;
+    every schedule gives the oracle's labels."""
+    rng = np.random.default_rng(sum(Q) + mode)
+    H, W = 12000, 3
+    n = int(np.prod(Q))
+    C = rng.integers(0, 21, size=(H, W, n)).astype(np.int32)
+    prior = {"lam": int(rng.integers(1, 12)), "g": 3, "l1": 1, "mode": mode_prior}
+    want = oracle.edp(C, sp(Q), prior, iters=2, tier=1)
+    edp_lib.set_pass_pairs(mode)
+    edp_lib.set_tuning(2, 0, 0)
+    got = host(edp_lib.solve(dev(C), sp(Q), prior, iters=2))
+    launches = edp_lib.last_pass_launches()
+    assert np.array_equal(got, want)
+    assert launches == (4 if mode == 1 else 8)
+
+
 @pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("Q,win,l1", [((13, 13), 5, 1), ((11,), 7, 1), ((13, 13), 5, 2)])
 def test_windowed_pass_schedule(edp_lib, pairs, Q, win, l1):
