@@ -72,9 +72,13 @@ def _load():
         lib.oracle_edp.argtypes = [P, i32, i32, ctypes.POINTER(_Prior), i32, i32, P, P, P]
         lib.oracle_edp_windowed.argtypes = [P, P, i32, i32, ctypes.POINTER(_Prior), i32, i32, P]
         lib.oracle_energy.argtypes = [P, P, i32, i32, ctypes.POINTER(_Prior), P]
+        lib.oracle_edp_weighted.argtypes = [P, i32, i32, ctypes.POINTER(_Prior), i32, i32, P, P, P]
+        lib.oracle_energy_weighted.argtypes = [P, P, i32, i32, ctypes.POINTER(_Prior), P, P, P]
+        lib.oracle_edge_weights.argtypes = [P, i32, i32, i32, i32, i32, P, P]
         for f in ("oracle_cost_volume", "oracle_cost_window", "oracle_message",
                   "oracle_scanline_dp", "oracle_min_marginals", "oracle_edp",
-                  "oracle_edp_windowed", "oracle_energy"):
+                  "oracle_edp_windowed", "oracle_energy", "oracle_edp_weighted",
+                  "oracle_energy_weighted", "oracle_edge_weights"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -232,4 +236,46 @@ def energy(C, labels, space: dict, prior: dict) -> tuple[int, int, int, int]:
     p = make_prior(space, prior)
     _check(_load().oracle_energy(_ptr(Cc), _ptr(labels), W, H, ctypes.byref(p), _ptr(out)),
            "energy")
+    return tuple(int(v) for v in out)
+
+
+def edge_weights(I, thresh: int = 10, factor: int = 2):
+    """Per-edge prior multipliers of the locally adaptive lambda (text below
+    Eq. Smooth_value_t): (wh, wv) uint8 [H][W]; an edge whose intensity step
+    is below `thresh` gets `factor`, every other edge 1."""
+    I = np.ascontiguousarray(I, dtype=np.uint8)
+    H, W = I.shape
+    wh = np.empty((H, W), dtype=np.uint8)
+    wv = np.empty((H, W), dtype=np.uint8)
+    _check(_load().oracle_edge_weights(_ptr(I), W, H, W, int(thresh), int(factor), _ptr(wh), _ptr(wv)),
+           "edge_weights")
+    return wh, wv
+
+
+def edp_weighted(C, space: dict, prior: dict, wh, wv, iters: int = 1, tier: int = 1):
+    """EDP with per-edge prior multipliers: the prior of edge (x, y)-(x+1, y)
+    is wh[y][x] * lambda * f, of (x, y)-(x, y+1) wv[y][x] * lambda * f."""
+    C = np.ascontiguousarray(C, dtype=np.int32)
+    H, W, Q = C.shape
+    wh = np.ascontiguousarray(wh, dtype=np.uint8)
+    wv = np.ascontiguousarray(wv, dtype=np.uint8)
+    assert wh.shape == (H, W) and wv.shape == (H, W)
+    labels = np.empty((H, W), dtype=np.int32)
+    p = make_prior(space, prior)
+    _check(_load().oracle_edp_weighted(_ptr(C), W, H, ctypes.byref(p), int(iters), int(tier), _ptr(wh),
+                                       _ptr(wv), _ptr(labels)), "edp_weighted")
+    return labels
+
+
+def energy_weighted(C, labels, space: dict, prior: dict, wh, wv) -> tuple[int, int, int, int]:
+    """Eq. GE_objective_function with per-edge prior multipliers."""
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    H, W = labels.shape
+    Cc = None if C is None else np.ascontiguousarray(C, dtype=np.int32)
+    wh = np.ascontiguousarray(wh, dtype=np.uint8)
+    wv = np.ascontiguousarray(wv, dtype=np.uint8)
+    out = np.zeros(4, dtype=np.int64)
+    p = make_prior(space, prior)
+    _check(_load().oracle_energy_weighted(_ptr(Cc), _ptr(labels), W, H, ctypes.byref(p), _ptr(wh), _ptr(wv),
+                                          _ptr(out)), "energy_weighted")
     return tuple(int(v) for v in out)

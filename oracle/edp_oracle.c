@@ -495,6 +495,9 @@ typedef struct {
     grid_t g;
     int32_t *S; /* [4][H][W][Q] */
     int64_t *h;
+    /* optional per-edge prior multipliers (locally adaptive lambda):
+     * wh[y][x] for the edge (x, y)-(x+1, y), wv[y][x] for (x, y)-(x, y+1) */
+    const uint8_t *wh, *wv;
 } full_ctx;
 
 static int neighbour(int k, int x, int y, int *xn, int *yn) {
@@ -519,7 +522,14 @@ static int full_msg(void *vctx, int k, int x, int y, int64_t *out) {
     }
     const int32_t *s = c->S + (((int64_t)k * c->g.H + yn) * c->g.W + xn) * c->g.Q;
     for (int64_t q = 0; q < c->g.Q; ++q) c->h[q] = floor_half(s[q]);
-    int rc = message(c->p, c->tier, c->h, out);
+    oracle_prior_t pe = *c->p;
+    if (c->wh) {
+        /* the prior of this edge: lambda times the edge's multiplier */
+        const int w = (k == KPX || k == KMX) ? c->wh[(int64_t)y * c->g.W + (x < xn ? x : xn)]
+                                             : c->wv[(int64_t)(y < yn ? y : yn) * c->g.W + x];
+        pe.lambda = c->p->lambda * w;
+    }
+    int rc = message(&pe, c->tier, c->h, out);
     if (rc) return rc;
     for (int64_t q = 0; q < c->g.Q; ++q)
         if (!fits32(out[q])) return ORACLE_ERR_RANGE;
@@ -606,13 +616,16 @@ out:
 
 /* Full-label EDP.  S_out (optional) receives the final sums [4][H][W][Q]
  * (k order +x, -x, +y, -y); S_omega (optional) the marginal estimate. */
-int oracle_edp(const int32_t *C, int W, int H, const oracle_prior_t *p, int iters, int tier,
-               int32_t *labels, int32_t *S_out, int64_t *S_omega) {
+static int edp_full(const int32_t *C, int W, int H, const oracle_prior_t *p, int iters, int tier,
+                    const uint8_t *wh, const uint8_t *wv, int32_t *labels, int32_t *S_out, int64_t *S_omega) {
     int rc = check_prior(p);
     if (rc) return rc;
     if (W < 1 || H < 1 || iters < 0) return ORACLE_ERR_ARG;
+    if ((wh == NULL) != (wv == NULL)) return ORACLE_ERR_ARG;
     full_ctx c;
     c.p = p;
+    c.wh = wh;
+    c.wv = wv;
     c.tier = tier;
     c.g.W = W;
     c.g.H = H;
@@ -629,6 +642,46 @@ int oracle_edp(const int32_t *C, int W, int H, const oracle_prior_t *p, int iter
     if (!S_out) free(S);
     free(c.h);
     return rc;
+}
+
+int oracle_edp(const int32_t *C, int W, int H, const oracle_prior_t *p, int iters, int tier,
+               int32_t *labels, int32_t *S_out, int64_t *S_omega) {
+    return edp_full(C, W, H, p, iters, tier, NULL, NULL, labels, S_out, S_omega);
+}
+
+/* EDP with a locally adaptive prior (the text below Eq. Smooth_value_t):
+ * the prior of every grid edge is lambda times the edge's multiplier,
+ * wh[y][x] for (x, y)-(x+1, y) and wv[y][x] for (x, y)-(x, y+1) (uint8,
+ * [H][W]; the last column of wh and the last row of wv are not read). */
+int oracle_edp_weighted(const int32_t *C, int W, int H, const oracle_prior_t *p, int iters, int tier,
+                        const uint8_t *wh, const uint8_t *wv, int32_t *labels) {
+    if (!wh || !wv) return ORACLE_ERR_ARG;
+    return edp_full(C, W, H, p, iters, tier, wh, wv, labels, NULL, NULL);
+}
+
+/* The paper's adaptive rule, read as per-edge multipliers: an edge whose
+ * intensity step |I(x') - I(x)| is below `thresh` gets `factor` (the paper:
+ * 2 lambda where the local gradient of I_t is below 10), every other edge 1.
+ * Entries without an edge (last column of wh, last row of wv) are 1. */
+int oracle_edge_weights(const uint8_t *I, int W, int H, int pitch, int thresh, int factor, uint8_t *wh,
+                        uint8_t *wv) {
+    if (!I || !wh || !wv || W < 1 || H < 1 || pitch < W || factor < 0 || factor > 255) return ORACLE_ERR_ARG;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int v = I[(int64_t)y * pitch + x];
+            int h = 1, u = 1;
+            if (x + 1 < W) {
+                const int d = I[(int64_t)y * pitch + x + 1] - v;
+                h = (d < 0 ? -d : d) < thresh ? factor : 1;
+            }
+            if (y + 1 < H) {
+                const int d = I[(int64_t)(y + 1) * pitch + x] - v;
+                u = (d < 0 ? -d : d) < thresh ? factor : 1;
+            }
+            wh[(int64_t)y * W + x] = (uint8_t)h;
+            wv[(int64_t)y * W + x] = (uint8_t)u;
+        }
+    return ORACLE_OK;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -713,8 +766,8 @@ int oracle_edp_windowed(const int32_t *Cw, const int32_t *centre, int W, int H,
 /* data term + right-neighbour edges + down-neighbour edges.                */
 /* ------------------------------------------------------------------------ */
 
-int oracle_energy(const int32_t *C, const int32_t *labels, int W, int H, const oracle_prior_t *p,
-                  int64_t *out4) {
+static int energy_full(const int32_t *C, const int32_t *labels, int W, int H, const oracle_prior_t *p,
+                       const uint8_t *wh, const uint8_t *wv, int64_t *out4) {
     int rc = check_prior(p);
     if (rc) return rc;
     int64_t Q = total_labels(p);
@@ -724,12 +777,26 @@ int oracle_energy(const int32_t *C, const int32_t *labels, int W, int H, const o
             int64_t l = labels[(int64_t)y * W + x];
             if (l < 0 || l >= Q) return ORACLE_ERR_ARG;
             if (C) data += C[((int64_t)y * W + x) * Q + l];
-            if (x + 1 < W) sh += oracle_prior(p, l, labels[(int64_t)y * W + x + 1]);
-            if (y + 1 < H) sv += oracle_prior(p, l, labels[(int64_t)(y + 1) * W + x]);
+            const int64_t i = (int64_t)y * W + x;
+            if (x + 1 < W) sh += (wh ? wh[i] : 1) * oracle_prior(p, l, labels[i + 1]);
+            if (y + 1 < H) sv += (wv ? wv[i] : 1) * oracle_prior(p, l, labels[i + W]);
         }
     out4[0] = data;
     out4[1] = sh;
     out4[2] = sv;
     out4[3] = data + sh + sv;
     return ORACLE_OK;
+}
+
+int oracle_energy(const int32_t *C, const int32_t *labels, int W, int H, const oracle_prior_t *p,
+                  int64_t *out4) {
+    return energy_full(C, labels, W, H, p, NULL, NULL, out4);
+}
+
+/* Eq. GE_objective_function with per-edge multipliers of the prior (see
+ * oracle_edp_weighted). */
+int oracle_energy_weighted(const int32_t *C, const int32_t *labels, int W, int H, const oracle_prior_t *p,
+                           const uint8_t *wh, const uint8_t *wv, int64_t *out4) {
+    if (!wh || !wv) return ORACLE_ERR_ARG;
+    return energy_full(C, labels, W, H, p, wh, wv, out4);
 }
