@@ -232,6 +232,37 @@ int edp_energy(const int32_t *C, const int32_t *labels, int W, int H,
                const edp_label_space *space, const edp_params *params, int64_t *out4,
                edp_stream_t stream);
 
+/* Locally adaptive prior (the text below Eq. Smooth_value_t: lambda(x) =
+ * 2 lambda where the local gradient of the image is below 10, lambda
+ * elsewhere), read as one multiplier per grid edge: the prior of the edge
+ * (x, y)-(x+1, y) is wh[y][x] * lambda * f, that of (x, y)-(x, y+1) is
+ * wv[y][x] * lambda * f.  (The paper's printed rule gives 2 lambda on both
+ * branches; the second is read as lambda.)
+ *
+ * edp_edge_weights: the multipliers of that rule from an image I (uint8
+ * [H][pitch]): an edge whose intensity step |I(x') - I(x)| is below
+ * `threshold` gets `factor` (0..255), every other edge 1; entries without an
+ * edge (last column of wh, last row of wv) are 1.  wh, wv: uint8 [H][W],
+ * device memory. */
+int edp_edge_weights(const uint8_t *I, int W, int H, int pitch, int threshold, int factor, uint8_t *wh,
+                     uint8_t *wv, edp_stream_t stream);
+
+/* edp_solve with the per-edge multipliers wh, wv (uint8 [H][W], device
+ * memory, every entry in 0..max_weight): the message from a pixel into its
+ * neighbour is the min search M with the prior of the edge between them.
+ * One-axis label spaces with Q <= 256 only (EDP_ERR_UNSUPPORTED otherwise).
+ * ws: >= edp_workspace_size(EDP_OP_SOLVE, ...).  The range check of
+ * edp_solve applies with lambda * max_weight. */
+int edp_solve_weighted(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,
+                       const uint8_t *wh, const uint8_t *wv, int max_weight, int32_t *labels, void *ws,
+                       size_t ws_bytes, edp_stream_t stream);
+
+/* edp_energy with the per-edge multipliers: out4[1] = sum over horizontal
+ * edges of wh * V, out4[2] = sum over vertical edges of wv * V. */
+int edp_energy_weighted(const int32_t *C, const int32_t *labels, int W, int H, const edp_label_space *space,
+                        const edp_params *params, const uint8_t *wh, const uint8_t *wv, int64_t *out4,
+                        edp_stream_t stream);
+
 /* Images to labels on the device: edp_cost_volume into the workspace,
  * edp_solve, edp_energy.  labels: int32 [H][W]; energy4: int64 [4] or NULL. */
 int edp_solve_images(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int H,

@@ -476,11 +476,15 @@ int set_launch(Args &a, int it, int k, int iters, bool pairs) {
     return pass;
 }
 
+// wh / wv: optional per-edge prior multipliers (one-axis kernel only)
 int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
-              unsigned char *ws, cudaStream_t st) {
+              unsigned char *ws, cudaStream_t st, const uint8_t *wh = nullptr, const uint8_t *wv = nullptr) {
     SolvePlan P;
     int rc = plan_solve(C, W, H, g, p, labels, ws, &P);
     if (rc) return rc;
+    if (wh && !P.r1) return EDP_ERR_UNSUPPORTED;
+    P.o.wh = wh;
+    P.o.wv = wv;
     if ((rc = cuda_status(cudaMemsetAsync(ws, 0, control_bytes(P, W, g.Q), st)))) return rc;
     int grid_t = 1, dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -585,9 +589,12 @@ int run_cost(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int
 }
 
 int run_energy(const int32_t *C, const int32_t *labels, int W, int H, const edp_label_space *s,
-               const edp_params *p, int Q, int64_t *out4, cudaStream_t st) {
+               const edp_params *p, int Q, int64_t *out4, cudaStream_t st, const uint8_t *wh = nullptr,
+               const uint8_t *wv = nullptr) {
     EnergyArgs a;
     memset(&a, 0, sizeof a);
+    a.wh = wh;
+    a.wv = wv;
     a.C = C;
     a.labels = labels;
     a.W = W;
@@ -826,6 +833,44 @@ int edp_solve(const int32_t *C, int W, int H, const edp_label_space *space, cons
     if (ws_bytes < edp_workspace_size(EDP_OP_SOLVE, W, H, space, params)) return EDP_ERR_WORKSPACE;
     if ((rc = check_range(W, H, g, params))) return rc;
     return run_solve(C, W, H, g, params, labels, static_cast<unsigned char *>(ws), (cudaStream_t)stream);
+}
+
+int edp_edge_weights(const uint8_t *I, int W, int H, int pitch, int threshold, int factor, uint8_t *wh, uint8_t *wv,
+                     edp_stream_t stream) {
+    if (!I || !wh || !wv || W < 1 || H < 1 || pitch < W) return EDP_ERR_INVALID_ARG;
+    if (factor < 0 || factor > 255 || threshold < 0) return EDP_ERR_INVALID_ARG;
+    return launch_edge_weights(I, W, H, pitch, threshold, factor, wh, wv, (cudaStream_t)stream) ? EDP_ERR_CUDA
+                                                                                                 : EDP_OK;
+}
+
+int edp_solve_weighted(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,
+                       const uint8_t *wh, const uint8_t *wv, int max_weight, int32_t *labels, void *ws,
+                       size_t ws_bytes, edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if (!C || !wh || !wv || !labels || !ws || W < 1 || H < 1 || params->iters < 1) return EDP_ERR_INVALID_ARG;
+    if (max_weight < 0 || max_weight > 255) return EDP_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
+    if (ws_bytes < edp_workspace_size(EDP_OP_SOLVE, W, H, space, params)) return EDP_ERR_WORKSPACE;
+    if ((rc = check_range(W, H, g, params))) return rc;
+    // the int32 range bound of the heaviest edge: lambda times the largest multiplier
+    edp_params pw = *params;
+    pw.lambda = params->lambda * std::max(1, max_weight);
+    if ((rc = check_range(W, H, g, &pw))) return rc;
+    return run_solve(C, W, H, g, params, labels, static_cast<unsigned char *>(ws), (cudaStream_t)stream, wh, wv);
+}
+
+int edp_energy_weighted(const int32_t *C, const int32_t *labels, int W, int H, const edp_label_space *space,
+                        const edp_params *params, const uint8_t *wh, const uint8_t *wv, int64_t *out4,
+                        edp_stream_t stream) {
+    Geometry g;
+    int rc = check_space(space, &g);
+    if (rc) return rc;
+    if ((rc = check_prior(params))) return rc;
+    if (!labels || !out4 || !wh || !wv || W < 1 || H < 1) return EDP_ERR_INVALID_ARG;
+    return run_energy(C, labels, W, H, space, params, g.Q, out4, (cudaStream_t)stream, wh, wv);
 }
 
 int edp_energy(const int32_t *C, const int32_t *labels, int W, int H, const edp_label_space *space,

@@ -129,8 +129,9 @@ __device__ __forceinline__ void energy_body(const EnergyArgs &A) {
         // labels outside [0, Q) are clamped so that every read stays in bounds
         const int l = min(max(A.labels[i], 0), A.Q - 1);
         if (A.C) e[0] += A.C[i * A.Q + l];
-        if (x + 1 < A.W) e[1] += prior_v(l, min(max(A.labels[i + 1], 0), A.Q - 1), A);
-        if (y + 1 < A.H) e[2] += prior_v(l, min(max(A.labels[i + A.W], 0), A.Q - 1), A);
+        // per-edge multipliers of the locally adaptive prior (null: all 1)
+        if (x + 1 < A.W) e[1] += (A.wh ? A.wh[i] : 1) * prior_v(l, min(max(A.labels[i + 1], 0), A.Q - 1), A);
+        if (y + 1 < A.H) e[2] += (A.wv ? A.wv[i] : 1) * prior_v(l, min(max(A.labels[i + A.W], 0), A.Q - 1), A);
     }
     __shared__ long long red[3][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -179,6 +180,31 @@ __global__ void zero_batched_kernel(const __grid_constant__ ZeroBatch Z) {
 int launch_zero_batched(const ZeroBatch &a, cudaStream_t st) {
     if (a.n == 0) return 0;
     zero_batched_kernel<<<dim3(64, a.n), 256, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+// Per-edge multipliers of the locally adaptive prior (the text below Eq.
+// Smooth_value_t: 2 lambda where the local image gradient is below 10), read
+// per grid edge: an edge whose intensity step is below `thresh` gets
+// `factor`, every other edge 1; entries without an edge are 1.
+__global__ void edge_weights_kernel(const uint8_t *I, int W, int H, int pitch, int thresh, int factor, uint8_t *wh,
+                                    uint8_t *wv) {
+    const long long n = (long long)W * H;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W), y = (int)(i / W);
+        const uint8_t *p = I + (size_t)y * pitch + x;
+        const int v = *p;
+        wh[i] = (uint8_t)((x + 1 < W && abs((int)p[1] - v) < thresh) ? factor : 1);
+        wv[i] = (uint8_t)((y + 1 < H && abs((int)p[pitch] - v) < thresh) ? factor : 1);
+    }
+}
+
+int launch_edge_weights(const uint8_t *I, int W, int H, int pitch, int thresh, int factor, uint8_t *wh, uint8_t *wv,
+                        cudaStream_t st) {
+    const long long n = (long long)W * H;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    edge_weights_kernel<<<(unsigned)blocks, 256, 0, st>>>(I, W, H, pitch, thresh, factor, wh, wv);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

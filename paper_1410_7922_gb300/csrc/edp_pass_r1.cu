@@ -9,7 +9,7 @@ namespace edp {
 template <int E, bool QUAD>
 constexpr int r1_max_rows() { return (E <= 4 && !QUAD) ? 16 : 8; }
 
-template <int E, bool QUAD>
+template <int E, bool QUAD, bool WT>
 __global__ void __launch_bounds__(32 * r1_max_rows<E, QUAD>(), 1) edp_pass_r1_kernel(PassR1Args A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
@@ -22,24 +22,28 @@ __global__ void __launch_bounds__(32 * r1_max_rows<E, QUAD>(), 1) edp_pass_r1_ke
         __syncthreads();
         const int band = s_band;
         if (band >= A.nbands) break;
-        if (!r1_band<E, QUAD>(A, band, smem_i, &s_abort)) return;
+        if (!r1_band<E, QUAD, WT>(A, band, smem_i, &s_abort)) return;
     }
 }
 
 // one build per labels-per-lane count (each allocates its own registers)
 using R1Kernel = void (*)(PassR1Args);
-template <bool QUAD>
+template <bool QUAD, bool WT>
 R1Kernel r1_kernel_for(int E) {
     switch (E) {
-    case 1: return edp_pass_r1_kernel<1, QUAD>;
-    case 2: return edp_pass_r1_kernel<2, QUAD>;
-    case 3: return edp_pass_r1_kernel<3, QUAD>;
-    case 4: return edp_pass_r1_kernel<4, QUAD>;
-    case 5: return edp_pass_r1_kernel<5, QUAD>;
-    case 6: return edp_pass_r1_kernel<6, QUAD>;
-    case 7: return edp_pass_r1_kernel<7, QUAD>;
-    default: return edp_pass_r1_kernel<8, QUAD>;
+    case 1: return edp_pass_r1_kernel<1, QUAD, WT>;
+    case 2: return edp_pass_r1_kernel<2, QUAD, WT>;
+    case 3: return edp_pass_r1_kernel<3, QUAD, WT>;
+    case 4: return edp_pass_r1_kernel<4, QUAD, WT>;
+    case 5: return edp_pass_r1_kernel<5, QUAD, WT>;
+    case 6: return edp_pass_r1_kernel<6, QUAD, WT>;
+    case 7: return edp_pass_r1_kernel<7, QUAD, WT>;
+    default: return edp_pass_r1_kernel<8, QUAD, WT>;
     }
+}
+R1Kernel r1_kernel_of(int E, int l1, bool wt) {
+    if (wt) return l1 == 2 ? r1_kernel_for<true, true>(E) : r1_kernel_for<false, true>(E);
+    return l1 == 2 ? r1_kernel_for<true, false>(E) : r1_kernel_for<false, false>(E);
 }
 
 int pass_r1_max_rows(int E, int l1) { return (E <= 4 && l1 != 2) ? 16 : 8; }
@@ -51,7 +55,7 @@ size_t pass_r1_smem(int NWR, int E) {
 }
 
 int edp_pass_r1_occupancy(int E, int l1, int threads, size_t smem) {
-    const R1Kernel k = l1 == 2 ? r1_kernel_for<true>(E) : r1_kernel_for<false>(E);
+    const R1Kernel k = r1_kernel_of(E, l1, false);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem) != cudaSuccess) return 0;
@@ -59,7 +63,7 @@ int edp_pass_r1_occupancy(int E, int l1, int threads, size_t smem) {
 }
 
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st) {
-    const R1Kernel k = a.l1 == 2 ? r1_kernel_for<true>(a.E) : r1_kernel_for<false>(a.E);
+    const R1Kernel k = r1_kernel_of(a.E, a.l1, a.wh != nullptr);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<a.grid, threads, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;

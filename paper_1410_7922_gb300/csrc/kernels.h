@@ -85,6 +85,7 @@ struct PassR1Args {
     int pass, read_c, read_d, write_a, write_b, final_;
     int pair;               // 1: passes pass and pass + 1 (pass 0 or 2) as one sweep of 2W columns per row
     int read_c2, write_a2, write_b2, final2;  // flags of the second pass of a pair (read_d is shared)
+    const uint8_t *wh, *wv; // optional [H][W] prior multipliers of the edges (x,y)-(x+1,y) and (x,y)-(x,y+1)
     int NWR;                // rows (warps) per block
     int nbands, grid, tag;
     long long spin_limit;
@@ -165,9 +166,12 @@ struct EnergyArgs {
     const int *labels;
     int W, H, Q, R, Q0, Q1;
     int lam, g, l1, mode;
+    const uint8_t *wh, *wv;  // optional per-edge prior multipliers (null: all 1)
     long long *out4;
 };
 int launch_energy(const EnergyArgs &a, cudaStream_t st);
+int launch_edge_weights(const uint8_t *I, int W, int H, int pitch, int thresh, int factor, uint8_t *wh, uint8_t *wv,
+                        cudaStream_t st);
 
 struct CostBatch {
     int n;

@@ -127,23 +127,24 @@ __device__ __forceinline__ void stg_vec(int *p, const int (&v)[E], int q0, int Q
 }
 
 // Truncated L1 distance transform of two row vectors a, b (E labels per
-// lane), carries from kc <= 4 lanes on each side (full lane scan otherwise).
+// lane) with slopes la, lb (the prior of each vector's edge), carries from
+// kc <= 4 lanes on each side (full lane scan otherwise).
 template <int E>
-__device__ __forceinline__ void dt_pair(int (&a)[E], int (&b)[E], int lane, int lam, int kc) {
+__device__ __forceinline__ void dt_pair(int (&a)[E], int (&b)[E], int lane, int la, int lb, int kc) {
     int fa[E], ba[E], fb[E], bb[E];
     fa[0] = a[0];
     fb[0] = b[0];
 #pragma unroll
     for (int i = 1; i < E; ++i) {
-        fa[i] = min(a[i], fa[i - 1] + lam);
-        fb[i] = min(b[i], fb[i - 1] + lam);
+        fa[i] = min(a[i], fa[i - 1] + la);
+        fb[i] = min(b[i], fb[i - 1] + lb);
     }
     ba[E - 1] = a[E - 1];
     bb[E - 1] = b[E - 1];
 #pragma unroll
     for (int i = E - 2; i >= 0; --i) {
-        ba[i] = min(a[i], ba[i + 1] + lam);
-        bb[i] = min(b[i], bb[i + 1] + lam);
+        ba[i] = min(a[i], ba[i + 1] + la);
+        bb[i] = min(b[i], bb[i + 1] + lb);
     }
     int cfa = kBig, cba = kBig, cfb = kBig, cbb = kBig;
     if (kc <= 4) {
@@ -154,20 +155,20 @@ __device__ __forceinline__ void dt_pair(int (&a)[E], int (&b)[E], int lane, int 
             const int t1 = __shfl_up_sync(kFull, fb[E - 1], d);
             const int t2 = __shfl_down_sync(kFull, ba[0], d);
             const int t3 = __shfl_down_sync(kFull, bb[0], d);
-            const int gap = lam * ((d - 1) * E + 1);
+            const int gapa = la * ((d - 1) * E + 1), gapb = lb * ((d - 1) * E + 1);
             if (lane >= d) {
-                cfa = min(cfa, t0 + gap);
-                cfb = min(cfb, t1 + gap);
+                cfa = min(cfa, t0 + gapa);
+                cfb = min(cfb, t1 + gapb);
             }
             if (lane + d < 32) {
-                cba = min(cba, t2 + gap);
-                cbb = min(cbb, t3 + gap);
+                cba = min(cba, t2 + gapa);
+                cbb = min(cbb, t3 + gapb);
             }
         }
     } else {
         // min-plus prefix / suffix scans over all lanes
-        int pa = fa[E - 1] - lam * E * lane, pb = fb[E - 1] - lam * E * lane;
-        int sa = ba[0] + lam * E * lane, sb = bb[0] + lam * E * lane;
+        int pa = fa[E - 1] - la * E * lane, pb = fb[E - 1] - lb * E * lane;
+        int sa = ba[0] + la * E * lane, sb = bb[0] + lb * E * lane;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int t0 = __shfl_up_sync(kFull, pa, d), t1 = __shfl_up_sync(kFull, pb, d);
@@ -184,29 +185,29 @@ __device__ __forceinline__ void dt_pair(int (&a)[E], int (&b)[E], int lane, int 
         const int xa = __shfl_up_sync(kFull, pa, 1), xb = __shfl_up_sync(kFull, pb, 1);
         const int ya = __shfl_down_sync(kFull, sa, 1), yb = __shfl_down_sync(kFull, sb, 1);
         if (lane > 0) {
-            cfa = xa + lam * (E * (lane - 1) + 1);
-            cfb = xb + lam * (E * (lane - 1) + 1);
+            cfa = xa + la * (E * (lane - 1) + 1);
+            cfb = xb + lb * (E * (lane - 1) + 1);
         }
         if (lane < 31) {
-            cba = ya - lam * (lane * E + E - 1);
-            cbb = yb - lam * (lane * E + E - 1);
+            cba = ya - la * (lane * E + E - 1);
+            cbb = yb - lb * (lane * E + E - 1);
         }
     }
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-        a[i] = min(min(fa[i], cfa + lam * i), min(ba[i], cba + lam * (E - 1 - i)));
-        b[i] = min(min(fb[i], cfb + lam * i), min(bb[i], cbb + lam * (E - 1 - i)));
+        a[i] = min(min(fa[i], cfa + la * i), min(ba[i], cba + la * (E - 1 - i)));
+        b[i] = min(min(fb[i], cfb + lb * i), min(bb[i], cbb + lb * (E - 1 - i)));
     }
 }
 
 // Truncated quadratic prior (l1 = 2, Eq. M_decmp: the generalized RMS): the
-// min-convolution of two row vectors a, b with lambda d^2 over the taps
+// min-convolution of two row vectors a, b with la d^2, lb d^2 over the taps
 // |d| < g (farther sources cost at least the clip value lambda g^2 applied
 // afterwards).  The window slides one label per tap: every lane shifts its E
 // values and takes the boundary value from its neighbour lane.  Positions
 // past the vector hold kBig.
 template <int E>
-__device__ __forceinline__ void quad_pair(int (&a)[E], int (&b)[E], int lane, int lam, int g) {
+__device__ __forceinline__ void quad_pair(int (&a)[E], int (&b)[E], int lane, int la, int lb, int g) {
     int oa[E], ob[E], ua[E], ub[E], da[E], db[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -232,11 +233,11 @@ __device__ __forceinline__ void quad_pair(int (&a)[E], int (&b)[E], int lane, in
         }
         da[0] = lane > 0 ? pa : kBig;
         db[0] = lane > 0 ? pb : kBig;
-        const int w = lam * d * d;
+        const int wa = la * d * d, wb = lb * d * d;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-            oa[i] = min(oa[i], min(ua[i], da[i]) + w);
-            ob[i] = min(ob[i], min(ub[i], db[i]) + w);
+            oa[i] = min(oa[i], min(ua[i], da[i]) + wa);
+            ob[i] = min(ob[i], min(ub[i], db[i]) + wb);
         }
     }
 #pragma unroll
@@ -259,8 +260,11 @@ __device__ __forceinline__ void quad_pair(int (&a)[E], int (&b)[E], int lane, in
 // The wavefront of the pair is H + 2W columns long instead of 2 (H + W).
 // Every thread of the block calls it with the same band; returns false when
 // the pass was aborted (a wait timed out).
-// QUAD: the build for the truncated quadratic prior (l1 = 2).
-template <int E, bool QUAD = false>
+// QUAD: the build for the truncated quadratic prior (l1 = 2).  WT: the build
+// for per-edge prior multipliers A.wh / A.wv (the locally adaptive prior):
+// the message into the next pixel of the row uses its horizontal edge, the
+// message into the next row its vertical edge.
+template <int E, bool QUAD = false, bool WT = false>
 __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int *smem_i, volatile int *s_abort) {
     constexpr int Qp = 32 * E;  // padded vector length in shared memory
     constexpr int VM = msg_chunk<E>();
@@ -355,6 +359,15 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                     pa[i] = cv[i] + ma[i] + md[i] - mc[i];
                     pb[i] = cv[i] + ma[i] + mc[i] - md[i];
                 }
+                // multipliers of this column's two outgoing edges: into the next
+                // pixel of the sweep (x, x +- 1) and into the next row (y, y -+ 1)
+                int wgt_a = 1, wgt_b = 1;
+                if constexpr (WT) {
+                    const int x = incx ? xs : W - 1 - xs;
+                    const int xe = (xs + 1 < W) ? (incx ? x : x - 1) : 0;  // left pixel of the edge
+                    wgt_a = __ldg(A.wh + (size_t)y * W + xe);
+                    wgt_b = has_next ? __ldg(A.wv + (size_t)(incy ? y : y - 1) * W + x) : 1;
+                }
                 // ---- m_b from the row above ----
                 int mb[E];
 #pragma unroll
@@ -432,11 +445,12 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                     lb = min(lb, hb[i]);
                 }
                 const int ga = redux_min(la), gb = redux_min(lb);
+                const int lam_a = WT ? A.lam * wgt_a : A.lam, lam_b = WT ? A.lam * wgt_b : A.lam;
                 if constexpr (QUAD)
-                    quad_pair<E>(ha, hb, lane, A.lam, A.g);
+                    quad_pair<E>(ha, hb, lane, lam_a, lam_b, A.g);
                 else
-                    dt_pair<E>(ha, hb, lane, A.lam, A.kc);
-                const int clipa = ga + A.capv, clipb = gb + A.capv;
+                    dt_pair<E>(ha, hb, lane, lam_a, lam_b, A.kc);
+                const int clipa = ga + (WT ? A.capv * wgt_a : A.capv), clipb = gb + (WT ? A.capv * wgt_b : A.capv);
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
                     ha[i] = min(ha[i], clipa);

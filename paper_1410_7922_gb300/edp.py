@@ -75,6 +75,9 @@ def load() -> ctypes.CDLL:
         "edp_solve": ([P, I, I, LS, PR, P, P, SZ, P], I),
         "edp_scanline_marginals": ([P, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_energy": ([P, P, I, I, LS, PR, P, P], I),
+        "edp_edge_weights": ([P, I, I, I, I, I, P, P, P], I),
+        "edp_solve_weighted": ([P, I, I, LS, PR, P, P, I, P, P, SZ, P], I),
+        "edp_energy_weighted": ([P, P, I, I, LS, PR, P, P, P, P], I),
         "edp_solve_images": ([P, P, P, I, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_solve_images_host": ([P, P, P, I, I, LS, PR, P, P, P, SZ, P], I),
         "edp_get_device_status": ([P, SZ, ctypes.POINTER(I), P], I),
@@ -114,7 +117,8 @@ def exported_symbols() -> list[str]:
             "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_forward", "edp_net_backward",
             "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc", "edp_coarse_labels",
             "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_scanline_marginals",
-            "edp_set_pass_pairs", "edp_last_pass_launches"]
+            "edp_set_pass_pairs", "edp_last_pass_launches", "edp_edge_weights", "edp_solve_weighted",
+            "edp_energy_weighted"]
 
 
 def status_string(code: int) -> str:
@@ -320,6 +324,50 @@ def energy(C, labels, space: dict, prior: dict, out=None, stream=None):
     rc = load().edp_energy(_dev(C, torch.int32, "C"), _dev(labels, torch.int32, "labels"), W, H,
                            ctypes.byref(ls), ctypes.byref(pr), _dev(out, torch.int64, "out4"), _stream(stream))
     _check(rc, "energy")
+    return out
+
+
+def edge_weights(I, threshold: int = 10, factor: int = 2, wh=None, wv=None, stream=None):
+    """edp_edge_weights: per-edge prior multipliers (wh, wv) uint8 [H][W] of
+    the locally adaptive prior from a device image."""
+    H, W = I.shape
+    if wh is None:
+        wh = torch.empty((H, W), dtype=torch.uint8, device=I.device)
+    if wv is None:
+        wv = torch.empty((H, W), dtype=torch.uint8, device=I.device)
+    rc = load().edp_edge_weights(_dev(I, torch.uint8, "I"), W, H, I.stride(0), int(threshold), int(factor),
+                                 _dev(wh, torch.uint8, "wh"), _dev(wv, torch.uint8, "wv"), _stream(stream))
+    _check(rc, "edge_weights")
+    return wh, wv
+
+
+def solve_weighted(C, space: dict, prior: dict, wh, wv, max_weight: int, iters: int = 1, ws=None, labels=None,
+                   stream=None):
+    """edp_solve_weighted: EDP with per-edge prior multipliers (one-axis spaces)."""
+    H, W, _ = C.shape
+    if ws is None:
+        ws = workspace(OP_SOLVE, W, H, space, prior, iters, device=C.device)
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=C.device)
+    ls, pr = label_space(space), params(prior, iters=iters)
+    rc = load().edp_solve_weighted(_dev(C, torch.int32, "C"), W, H, ctypes.byref(ls), ctypes.byref(pr),
+                                   _dev(wh, torch.uint8, "wh"), _dev(wv, torch.uint8, "wv"), int(max_weight),
+                                   _dev(labels, torch.int32, "labels"), _dev(ws, torch.uint8, "ws"), ws.numel(),
+                                   _stream(stream))
+    _check(rc, "solve_weighted")
+    return labels
+
+
+def energy_weighted(C, labels, space: dict, prior: dict, wh, wv, out=None, stream=None):
+    """edp_energy_weighted: int64 [4] with per-edge prior multipliers."""
+    H, W = labels.shape
+    if out is None:
+        out = torch.empty(4, dtype=torch.int64, device=labels.device)
+    ls, pr = label_space(space), params(prior)
+    rc = load().edp_energy_weighted(_dev(C, torch.int32, "C"), _dev(labels, torch.int32, "labels"), W, H,
+                                    ctypes.byref(ls), ctypes.byref(pr), _dev(wh, torch.uint8, "wh"),
+                                    _dev(wv, torch.uint8, "wv"), _dev(out, torch.int64, "out4"), _stream(stream))
+    _check(rc, "energy_weighted")
     return out
 
 
