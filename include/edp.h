@@ -250,7 +250,9 @@ int edp_edge_weights(const uint8_t *I, int W, int H, int pitch, int threshold, i
 /* edp_solve with the per-edge multipliers wh, wv (uint8 [H][W], device
  * memory, every entry in 0..max_weight): the message from a pixel into its
  * neighbour is the min search M with the prior of the edge between them.
- * One-axis label spaces with Q <= 256 only (EDP_ERR_UNSUPPORTED otherwise).
+ * One-axis label spaces with Q <= 256, and multi-axis spaces whose lines all
+ * hold 9, 17 or 33 labels, or all 65 (the whole-line form of the multi-axis
+ * kernel); EDP_ERR_UNSUPPORTED otherwise.
  * ws: >= edp_workspace_size(EDP_OP_SOLVE, ...).  The range check of
  * edp_solve applies with lambda * max_weight. */
 int edp_solve_weighted(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,

@@ -482,9 +482,9 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     SolvePlan P;
     int rc = plan_solve(C, W, H, g, p, labels, ws, &P);
     if (rc) return rc;
-    if (wh && !P.r1) return EDP_ERR_UNSUPPORTED;
-    P.o.wh = wh;
-    P.o.wv = wv;
+    if (wh && !P.r1 && !P.ta.lean) return EDP_ERR_UNSUPPORTED;  // one-axis kernel, or the whole-line form
+    P.o.wh = P.ta.wh = wh;
+    P.o.wv = P.ta.wv = wv;
     if ((rc = cuda_status(cudaMemsetAsync(ws, 0, control_bytes(P, W, g.Q), st)))) return rc;
     int grid_t = 1, dev = 0, sms = 0;
     cudaGetDevice(&dev);

@@ -50,6 +50,7 @@ struct TeamArgs {
     int W, H, Q, Qm, R;     // Qm: message stride, Q rounded up to a multiple of 4
     TeamAxis ax[3];
     int lam, capv, mode;    // mode 0 joint, 1 per axis truncation
+    const uint8_t *wh, *wv; // optional [H][W] prior multipliers of the edges (x,y)-(x+1,y), (x,y)-(x,y+1) (lean form)
     int l1, g;              // prior power (1: linear sweeps, 2: quadratic taps, lean / windowed forms) and truncation
     int pass, read_c, read_d, write_a, write_b, final_;
     int pair;               // 1: passes pass and pass + 1 (pass 0 or 2) as one sweep of 2W columns per row

@@ -382,7 +382,8 @@ __host__ __device__ inline bool lean_length(int L) { return L == 9 || L == 17 ||
 // serves 9/17/33, 65 serves 65, 2 is the quadratic-prior build for all).
 // WIN: EDP on per-pixel label boxes (windowed form, one warp per row); EM is
 // then the prior power l1 of the build (1 linear sweeps, 2 quadratic taps).
-template <int EM, bool LEAN, bool WIN = false>
+// WT (whole-line form): per-edge multipliers of the prior, A.wh / A.wv.
+template <int EM, bool LEAN, bool WIN = false, bool WT = false>
 __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int *smem, volatile int *s_abort) {
     using namespace team;
     const int Q = A.Q, Qm = A.Qm, W = A.W, H = A.H, T = A.T, NT = A.NT, R = A.R;
@@ -863,7 +864,20 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             const unsigned aX = saddr(vsel ? tB : tA);
             const unsigned aC = saddr(sC), aCc = saddr(sc), aCd = saddr(sd);
             const unsigned aMa = saddr(maS), aMb = saddr(mbox + (s % kmb) * Qm);
-            const int lam = A.lam;
+            // the prior of this vector's outgoing edge: per-edge multipliers of
+            // the locally adaptive prior (into the next pixel of the sweep, or
+            // into the next row), 1 without them
+            int wsel = 1;
+            if constexpr (WT) {
+                if (vsel == 0)
+                    wsel = nxt ? __ldg(A.wh + (size_t)y * W + (incx ? x : x - 1)) : 1;
+                else
+                    wsel = has_next ? __ldg(A.wv + (size_t)(incy ? y : y - 1) * W + x) : 1;
+            }
+            // (the build without multipliers reads lambda f(g) from the
+            // parameter block, as an operand, not from a register)
+            const int lam = WT ? A.lam * wsel : A.lam;
+            const int capw = WT ? A.capv * wsel : 0;
             const bool final_a = fin && vsel == 0;
             int vmin = kBig;                           // minimum of this vector's halved sums
             {
@@ -872,13 +886,13 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 for (int li = lv; li < nl; li += NLV) {
                     int lm;
                     if (EM >= 65 || (EM == 2 && L == 65)) {
-                        lm = lean_phase0<65, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 65, vsel, final_a, per_axis, lam, A.capv, key, A.g);
+                        lm = lean_phase0<65, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 65, vsel, final_a, per_axis, lam, WT ? capw : A.capv, key, A.g);
                     } else if (L == 33)
-                        lm = lean_phase0<33, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 33, vsel, final_a, per_axis, lam, A.capv, key, A.g);
+                        lm = lean_phase0<33, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 33, vsel, final_a, per_axis, lam, WT ? capw : A.capv, key, A.g);
                     else if (L == 17)
-                        lm = lean_phase0<17, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 17, vsel, final_a, per_axis, lam, A.capv, key, A.g);
+                        lm = lean_phase0<17, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 17, vsel, final_a, per_axis, lam, WT ? capw : A.capv, key, A.g);
                     else
-                        lm = lean_phase0<9, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 9, vsel, final_a, per_axis, lam, A.capv, key, A.g);
+                        lm = lean_phase0<9, EM == 2>(aC, aCc, aCd, aMa, aMb, aX, li * 9, vsel, final_a, per_axis, lam, WT ? capw : A.capv, key, A.g);
                     vmin = min(vmin, lm);
                 }
             }
@@ -907,13 +921,13 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                     for (int li = lv; li < Xr.nlines; li += NLV) {
                         const int qb = line_first(Xr, li);
                         if (EM >= 65 || (EM == 2 && Xr.L == 65))
-                            lean_phase_r<65, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O, A.g);
+                            lean_phase_r<65, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, WT ? capw : A.capv, gv, O, A.g);
                         else if (Xr.L == 33)
-                            lean_phase_r<33, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O, A.g);
+                            lean_phase_r<33, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, WT ? capw : A.capv, gv, O, A.g);
                         else if (Xr.L == 17)
-                            lean_phase_r<17, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O, A.g);
+                            lean_phase_r<17, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, WT ? capw : A.capv, gv, O, A.g);
                         else
-                            lean_phase_r<9, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, A.capv, gv, O, A.g);
+                            lean_phase_r<9, EM == 2>(aX, qb, Xr.stride, last, vsel, per_axis, lam, WT ? capw : A.capv, gv, O, A.g);
                     }
                 }
             }

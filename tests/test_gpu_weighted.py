@@ -60,6 +60,25 @@ def test_weighted_edp_random(edp_lib, Q, iters, pairs):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("Q,mode", [((9, 9), "per_axis"), ((17, 9), "joint"), ((33, 33), "per_axis"),
+                                    ((65, 65), "joint"), ((17, 17, 9), "per_axis")])
+@pytest.mark.parametrize("pairs", [False, True])
+def test_weighted_edp_whole_line_form(edp_lib, Q, mode, pairs):
+    """Multi-axis spaces on the whole-line form of the multi-axis kernel."""
+    rng = np.random.default_rng(sum(Q) * 7 + pairs)
+    n = int(np.prod(Q))
+    H, W = (9, 13) if n > 1000 else (15, 19)
+    C = rng.integers(0, 21, size=(H, W, n)).astype(np.int32)
+    wh = rng.integers(0, 4, size=(H, W)).astype(np.uint8)
+    wv = rng.integers(0, 4, size=(H, W)).astype(np.uint8)
+    prior = {"lam": int(rng.integers(1, 9)), "g": int(rng.integers(1, 5)), "l1": 1, "mode": mode}
+    want = oracle.edp_weighted(C, sp(Q), prior, wh, wv, iters=2)
+    edp_lib.set_pass_pairs(pairs)
+    edp_lib.set_tuning(2, 0, 0)
+    got = host(edp_lib.solve_weighted(dev(C), sp(Q), prior, dev(wh), dev(wv), 3, iters=2))
+    assert np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("Q,g", [(16, 3), (64, 5)])
 def test_weighted_edp_quadratic_prior(edp_lib, Q, g):
     rng = np.random.default_rng(Q + g)
@@ -104,6 +123,7 @@ def test_weighted_energy(edp_lib, Q, mode):
 
 
 def test_weighted_unsupported_and_invalid(edp_lib):
+    """The lane-group form of the multi-axis kernel (a 5x4 space) takes no weights."""
     C = torch.zeros((4, 5, 20), dtype=torch.int32, device="cuda")
     w = torch.ones((4, 5), dtype=torch.uint8, device="cuda")
     prior = {"lam": 2, "g": 2, "l1": 1, "mode": "per_axis"}
