@@ -1,7 +1,7 @@
 // pass_r1.cuh -- one row band of an EDP scan pass for one label axis (Q <= 256).
 //
-// Same arithmetic as pass_gen.cuh (Sec. 4.2, Eq. DP_2D_base with the data
-// term, messages M(floor(S_k / 2)) stored at the receiving pixel), with a
+// Sec. 4.2, Eq. DP_2D_base with the data term, messages M(floor(S_k / 2))
+// stored at the receiving pixel (the arithmetic of pass_team.cuh), with a
 // schedule built for the latency of the pass's wavefront: one warp owns one
 // image row and keeps the message into its next pixel (m_a) in registers;
 // lane j holds the E labels j*E .. j*E+E-1 of the row's current pixel.
