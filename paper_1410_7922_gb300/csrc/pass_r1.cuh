@@ -301,220 +301,231 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
         const size_t mrow = (size_t)y * W * Qm + q0;
         const int *const Mdrow = Md + mrow;
         int *const Mbrow = Mb + (size_t)y_next * W * Qm + q0;
-        int cons_seen = 0;  // the consumer's progress as last read (producer side)
-        const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring + q0);
-        constexpr unsigned kSlot = 3 * Qp * 4;  // bytes per ring slot
-        for (int h = 0; h < (A.pair ? 2 : 1) && !aborted; ++h) {
-            // half h: pass A.pass + h, pixel x = incx ? xs : W - 1 - xs at column xs
-            const bool incx = ((A.pass + h) & 1) == 0;
-            const bool read_c = h ? A.read_c2 : A.read_c;
-            const bool write_a = h ? A.write_a2 : A.write_a;
-            const bool write_b = has_next && (h ? A.write_b2 : A.write_b);
-            const bool fin = h ? A.final2 : A.final_;
-            const int x0 = incx ? 0 : W - 1;
-            const int dC = incx ? Q : -Q, dM = incx ? Qm : -Qm;
-            // running source pointers of the prefetch (column xp of the half)
-            const int *pfC = Crow + (size_t)x0 * Q;
-            const int *pfc = (incx ? A.M[1] : A.M[0]) + mrow + (size_t)x0 * Qm;
-            const int *pfd = Mdrow + (size_t)x0 * Qm;
-            int xp = 0;
-            auto prefetch = [&]() {
-                if (xp < W && q0 < Q) {
-                    const unsigned dst = ring_s + ((unsigned)(h * W + xp) & kPf) * kSlot;
-                    if (vw == 4)
-                        cp_chunks<E, (E % 4 == 0 ? 4 : 1)>(dst, pfC, q0, Q, true);
-                    else if (vw == 2)
-                        cp_chunks<E, (E % 2 == 0 ? 2 : 1)>(dst, pfC, q0, Q, true);
-                    else
-                        cp_chunks<E, 1>(dst, pfC, q0, Q, true);
-                    cp_chunks<E, VM>(dst + Qp * 4, pfc, q0, Q, read_c && xp + 1 < W);
-                    cp_chunks<E, VM>(dst + 2 * Qp * 4, pfd, q0, Q, d_ok);
-                }
-                cp_async_commit();
-                ++xp;
-                pfC += dC;
-                pfc += dM;
-                pfd += dM;
-            };
-            for (int t = 0; t < kPf; ++t) prefetch();
-            // running output pointers: m_a into the next pixel, m_b into the next row
-            int *pa_out = (incx ? A.M[0] : A.M[1]) + mrow + (long long)(x0 + (incx ? 1 : -1)) * Qm;
-            int *pb_out = Mbrow + (size_t)x0 * Qm;
-            int ma[E];
-#pragma unroll
-            for (int i = 0; i < E; ++i) ma[i] = 0;
-#pragma unroll 1
-            for (int xs = 0; xs < W; ++xs) {
-                const int s = h * W + xs;  // column of the launch (ring slots, mailbox tags, records)
-                prefetch();
-                cp_async_wait_n<kPf>();
-                // ---- work that does not wait for the row above ----
-                const unsigned src = ring_s + ((unsigned)s & kPf) * kSlot;
-                int cv[E], mc[E], md[E], pa[E], pb[E];
-                lds_vec<E>(src, cv);
-                lds_vec<E>(src + Qp * 4, mc);
-                lds_vec<E>(src + 2 * Qp * 4, md);
-#pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    pa[i] = cv[i] + ma[i] + md[i] - mc[i];
-                    pb[i] = cv[i] + ma[i] + mc[i] - md[i];
-                }
-                // multipliers of this column's two outgoing edges: into the next
-                // pixel of the sweep (x, x +- 1) and into the next row (y, y -+ 1)
-                int wgt_a = 1, wgt_b = 1;
-                if constexpr (WT) {
-                    const int x = incx ? xs : W - 1 - xs;
-                    const int xe = (xs + 1 < W) ? (incx ? x : x - 1) : 0;  // left pixel of the edge
-                    wgt_a = __ldg(A.wh + (size_t)y * W + xe);
-                    wgt_b = has_next ? __ldg(A.wv + (size_t)(incy ? y : y - 1) * W + x) : 1;
-                }
-                // ---- m_b from the row above ----
-                int mb[E];
-#pragma unroll
-                for (int i = 0; i < E; ++i) mb[i] = 0;
-                if (r > 0) {
-                    long long spins = 0;
-                    bool bad = false;
-                    const int2 *p = (w > 0) ? mb_in + (s & (kMb - 1)) * Qp : ll_in + (size_t)s * Q;
-                    const int want = (w > 0) ? s + 1 : A.tag;
-                    const unsigned long long tw = (A.trace && w == 0) ? global_ns() : 0;
-                    // first look straight-line (the record is usually there), then the
-                    // bounded spin
-                    bool ok0 = true;
-                    if (w > 0) {
-#pragma unroll
-                        for (int i = 0; i < E; ++i) {
-                            if (q0 + i < Q) {
-                                const int2 t = lds_rec(p + i);
-                                mb[i] = t.x;
-                                ok0 = ok0 && (t.y == want);
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < E; ++i) {
-                            if (q0 + i < Q) {
-                                const int2 t = ld_rec(p + i);
-                                mb[i] = t.x;
-                                ok0 = ok0 && (t.y == want);
-                            }
-                        }
+        // The row's role is fixed for the band: FAST is the common one (a row
+        // inside a block with rows above and below it, both hand-offs through
+        // the shared-memory mailbox), built without the role branches.
+        const bool fast_role = r > 0 && w > 0 && has_next && !last_in_band;
+        auto run_row = [&](auto fast_c) {
+            constexpr bool FAST = decltype(fast_c)::value;
+            int cons_seen = 0;  // the consumer's progress as last read (producer side)
+            const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring + q0);
+            constexpr unsigned kSlot = 3 * Qp * 4;  // bytes per ring slot
+            for (int h = 0; h < (A.pair ? 2 : 1) && !aborted; ++h) {
+                // half h: pass A.pass + h, pixel x = incx ? xs : W - 1 - xs at column xs
+                const bool incx = ((A.pass + h) & 1) == 0;
+                const bool read_c = h ? A.read_c2 : A.read_c;
+                const bool write_a = h ? A.write_a2 : A.write_a;
+                const bool write_b = (FAST || has_next) && (h ? A.write_b2 : A.write_b);
+                const bool fin = h ? A.final2 : A.final_;
+                const int x0 = incx ? 0 : W - 1;
+                const int dC = incx ? Q : -Q, dM = incx ? Qm : -Qm;
+                // running source pointers of the prefetch (column xp of the half)
+                const int *pfC = Crow + (size_t)x0 * Q;
+                const int *pfc = (incx ? A.M[1] : A.M[0]) + mrow + (size_t)x0 * Qm;
+                const int *pfd = Mdrow + (size_t)x0 * Qm;
+                int xp = 0;
+                auto prefetch = [&]() {
+                    if (xp < W && q0 < Q) {
+                        const unsigned dst = ring_s + ((unsigned)(h * W + xp) & kPf) * kSlot;
+                        if (vw == 4)
+                            cp_chunks<E, (E % 4 == 0 ? 4 : 1)>(dst, pfC, q0, Q, true);
+                        else if (vw == 2)
+                            cp_chunks<E, (E % 2 == 0 ? 2 : 1)>(dst, pfC, q0, Q, true);
+                        else
+                            cp_chunks<E, 1>(dst, pfC, q0, Q, true);
+                        cp_chunks<E, VM>(dst + Qp * 4, pfc, q0, Q, read_c && xp + 1 < W);
+                        cp_chunks<E, VM>(dst + 2 * Qp * 4, pfd, q0, Q, d_ok);
                     }
-                    if (!__all_sync(kFull, ok0)) while (true) {
-                        bool ok = true;
-#pragma unroll
-                        for (int i = 0; i < E; ++i) {
-                            if (q0 + i < Q) {
-                                const int2 t = (w > 0) ? lds_rec(p + i) : ld_rec(p + i);
-                                mb[i] = t.x;
-                                ok = ok && (t.y == want);
+                    cp_async_commit();
+                    ++xp;
+                    pfC += dC;
+                    pfc += dM;
+                    pfd += dM;
+                };
+                for (int t = 0; t < kPf; ++t) prefetch();
+                // running output pointers: m_a into the next pixel, m_b into the next row
+                int *pa_out = (incx ? A.M[0] : A.M[1]) + mrow + (long long)(x0 + (incx ? 1 : -1)) * Qm;
+                int *pb_out = Mbrow + (size_t)x0 * Qm;
+                int ma[E];
+    #pragma unroll
+                for (int i = 0; i < E; ++i) ma[i] = 0;
+    #pragma unroll 1
+                for (int xs = 0; xs < W; ++xs) {
+                    const int s = h * W + xs;  // column of the launch (ring slots, mailbox tags, records)
+                    prefetch();
+                    cp_async_wait_n<kPf>();
+                    // ---- work that does not wait for the row above ----
+                    const unsigned src = ring_s + ((unsigned)s & kPf) * kSlot;
+                    int cv[E], mc[E], md[E], pa[E], pb[E];
+                    lds_vec<E>(src, cv);
+                    lds_vec<E>(src + Qp * 4, mc);
+                    lds_vec<E>(src + 2 * Qp * 4, md);
+    #pragma unroll
+                    for (int i = 0; i < E; ++i) {
+                        pa[i] = cv[i] + ma[i] + md[i] - mc[i];
+                        pb[i] = cv[i] + ma[i] + mc[i] - md[i];
+                    }
+                    // multipliers of this column's two outgoing edges: into the next
+                    // pixel of the sweep (x, x +- 1) and into the next row (y, y -+ 1)
+                    int wgt_a = 1, wgt_b = 1;
+                    if constexpr (WT) {
+                        const int x = incx ? xs : W - 1 - xs;
+                        const int xe = (xs + 1 < W) ? (incx ? x : x - 1) : 0;  // left pixel of the edge
+                        wgt_a = __ldg(A.wh + (size_t)y * W + xe);
+                        wgt_b = has_next ? __ldg(A.wv + (size_t)(incy ? y : y - 1) * W + x) : 1;
+                    }
+                    // ---- m_b from the row above ----
+                    int mb[E];
+    #pragma unroll
+                    for (int i = 0; i < E; ++i) mb[i] = 0;
+                    if (FAST || r > 0) {
+                        long long spins = 0;
+                        bool bad = false;
+                        const int2 *p = (FAST || w > 0) ? mb_in + (s & (kMb - 1)) * Qp : ll_in + (size_t)s * Q;
+                        const int want = (FAST || w > 0) ? s + 1 : A.tag;
+                        const unsigned long long tw = (!FAST && A.trace && w == 0) ? global_ns() : 0;
+                        // first look straight-line (the record is usually there), then the
+                        // bounded spin
+                        bool ok0 = true;
+                        if (FAST || w > 0) {
+    #pragma unroll
+                            for (int i = 0; i < E; ++i) {
+                                if (q0 + i < Q) {
+                                    const int2 t = lds_rec(p + i);
+                                    mb[i] = t.x;
+                                    ok0 = ok0 && (t.y == want);
+                                }
+                            }
+                        } else {
+    #pragma unroll
+                            for (int i = 0; i < E; ++i) {
+                                if (q0 + i < Q) {
+                                    const int2 t = ld_rec(p + i);
+                                    mb[i] = t.x;
+                                    ok0 = ok0 && (t.y == want);
+                                }
                             }
                         }
-                        if (__all_sync(kFull, ok)) break;
-                        if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0 ||
-                                                  (w == 0 && *(volatile int *)A.status != 0))) {
-                            bad = true;
+                        if (!__all_sync(kFull, ok0)) while (true) {
+                            bool ok = true;
+    #pragma unroll
+                            for (int i = 0; i < E; ++i) {
+                                if (q0 + i < Q) {
+                                    const int2 t = (FAST || w > 0) ? lds_rec(p + i) : ld_rec(p + i);
+                                    mb[i] = t.x;
+                                    ok = ok && (t.y == want);
+                                }
+                            }
+                            if (__all_sync(kFull, ok)) break;
+                            if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0 ||
+                                                      (w == 0 && *(volatile int *)A.status != 0))) {
+                                bad = true;
+                                break;
+                            }
+                            if (w == 0) __nanosleep(20);
+                        }
+                        if (tw) t_wait += global_ns() - tw;
+                        if (bad) {
+                            if (lane == 0) {
+                                atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
+                                *s_abort = 1;
+                            }
+                            aborted = true;
                             break;
                         }
-                        if (w == 0) __nanosleep(20);
+                        // issued after the vote on every lane's loaded tags: the
+                        // loads of the slot have returned before the producer can
+                        // see this count and overwrite it
+                        // (every lane stores the same count: no divergent branch)
+                        if (FAST || w > 0) st_relaxed_shared(consumed + w, s + 1);
                     }
-                    if (tw) t_wait += global_ns() - tw;
-                    if (bad) {
-                        if (lane == 0) {
-                            atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
-                            *s_abort = 1;
-                        }
-                        aborted = true;
-                        break;
+                    // ---- sums (Eq. DP_2D_base), halving, min search M ----
+                    int ha[E], hb[E];
+                    int la = kBig, lb = kBig;
+    #pragma unroll
+                    for (int i = 0; i < E; ++i) {
+                        const bool on = q0 + i < Q;
+                        ha[i] = on ? floor_half(pa[i] + mb[i]) : kBig;
+                        hb[i] = on ? floor_half(pb[i] + mb[i]) : kBig;
+                        la = min(la, ha[i]);
+                        lb = min(lb, hb[i]);
                     }
-                    // issued after the vote on every lane's loaded tags: the
-                    // loads of the slot have returned before the producer can
-                    // see this count and overwrite it
-                    // (every lane stores the same count: no divergent branch)
-                    if (w > 0) st_relaxed_shared(consumed + w, s + 1);
-                }
-                // ---- sums (Eq. DP_2D_base), halving, min search M ----
-                int ha[E], hb[E];
-                int la = kBig, lb = kBig;
-#pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    const bool on = q0 + i < Q;
-                    ha[i] = on ? floor_half(pa[i] + mb[i]) : kBig;
-                    hb[i] = on ? floor_half(pb[i] + mb[i]) : kBig;
-                    la = min(la, ha[i]);
-                    lb = min(lb, hb[i]);
-                }
-                const int ga = redux_min(la), gb = redux_min(lb);
-                const int lam_a = WT ? A.lam * wgt_a : A.lam, lam_b = WT ? A.lam * wgt_b : A.lam;
-                if constexpr (QUAD)
-                    quad_pair<E>(ha, hb, lane, lam_a, lam_b, A.g);
-                else
-                    dt_pair<E>(ha, hb, lane, lam_a, lam_b, A.kc);
-                const int clipa = ga + (WT ? A.capv * wgt_a : A.capv), clipb = gb + (WT ? A.capv * wgt_b : A.capv);
-#pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    ha[i] = min(ha[i], clipa);
-                    hb[i] = min(hb[i], clipb);
-                }
-                // ---- hand-off of m_b to the row below, then the global stores ----
-                if (has_next) {
-                    if (!last_in_band) {
-                        const int need = s - kMb + 1;  // the slot's previous column was read
-                        if (cons_seen < need) {
-                            long long spins = 0;
-                            bool bad = false;
-                            while (true) {
-                                cons_seen = ld_relaxed_shared(consumed + w + 1);
-                                if (__all_sync(kFull, cons_seen >= need)) break;
-                                if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0)) {
-                                    bad = true;
+                    const int ga = redux_min(la), gb = redux_min(lb);
+                    const int lam_a = WT ? A.lam * wgt_a : A.lam, lam_b = WT ? A.lam * wgt_b : A.lam;
+                    if constexpr (QUAD)
+                        quad_pair<E>(ha, hb, lane, lam_a, lam_b, A.g);
+                    else
+                        dt_pair<E>(ha, hb, lane, lam_a, lam_b, A.kc);
+                    const int clipa = ga + (WT ? A.capv * wgt_a : A.capv), clipb = gb + (WT ? A.capv * wgt_b : A.capv);
+    #pragma unroll
+                    for (int i = 0; i < E; ++i) {
+                        ha[i] = min(ha[i], clipa);
+                        hb[i] = min(hb[i], clipb);
+                    }
+                    // ---- hand-off of m_b to the row below, then the global stores ----
+                    if (FAST || has_next) {
+                        if (FAST || !last_in_band) {
+                            const int need = s - kMb + 1;  // the slot's previous column was read
+                            if (cons_seen < need) {
+                                long long spins = 0;
+                                bool bad = false;
+                                while (true) {
+                                    cons_seen = ld_relaxed_shared(consumed + w + 1);
+                                    if (__all_sync(kFull, cons_seen >= need)) break;
+                                    if (__any_sync(kFull, ++spins > A.spin_limit || *s_abort != 0)) {
+                                        bad = true;
+                                        break;
+                                    }
+                                }
+                                if (bad) {
+                                    if (lane == 0) {
+                                        atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
+                                        *s_abort = 1;
+                                    }
+                                    aborted = true;
                                     break;
                                 }
                             }
-                            if (bad) {
-                                if (lane == 0) {
-                                    atomicCAS(A.status, 0, EDP_ERR_TIMEOUT_CODE);
-                                    *s_abort = 1;
-                                }
-                                aborted = true;
-                                break;
+                            int2 *p = mb_out + (s & (kMb - 1)) * Qp;
+    #pragma unroll
+                            for (int i = 0; i < E; ++i)
+                                if (q0 + i < Q) sts_rec(p + i, hb[i], s + 1);
+                        } else {
+                            int2 *p = ll_out + (size_t)s * Q;
+    #pragma unroll
+                            for (int i = 0; i < E; ++i)
+                                if (q0 + i < Q) st_rec(p + i, hb[i], A.tag);
+                        }
+                        if (write_b) stg_vec<E>(pb_out, hb, q0, Q);
+                    }
+                    if (write_a && xs + 1 < W) stg_vec<E>(pa_out, ha, q0, Q);
+                    pa_out += dM;
+                    pb_out += dM;
+                    if (fin) {
+                        // marginal S_Omega = C + all four messages, lowest-index argmin
+                        int sv = kBig, sq = 0x7fffffff;
+    #pragma unroll
+                        for (int i = 0; i < E; ++i) {
+                            const int v = cv[i] + ma[i] + mc[i] + md[i] + mb[i];
+                            if (q0 + i < Q && v < sv) {
+                                sv = v;
+                                sq = q0 + i;
                             }
                         }
-                        int2 *p = mb_out + (s & (kMb - 1)) * Qp;
-#pragma unroll
-                        for (int i = 0; i < E; ++i)
-                            if (q0 + i < Q) sts_rec(p + i, hb[i], s + 1);
-                    } else {
-                        int2 *p = ll_out + (size_t)s * Q;
-#pragma unroll
-                        for (int i = 0; i < E; ++i)
-                            if (q0 + i < Q) st_rec(p + i, hb[i], A.tag);
+                        const int vbest = redux_min(sv);
+                        const int qbest = redux_min(sv == vbest ? sq : 0x7fffffff);
+                        if (lane == 0) A.labels[(size_t)y * W + (incx ? xs : W - 1 - xs)] = qbest;
                     }
-                    if (write_b) stg_vec<E>(pb_out, hb, q0, Q);
+    #pragma unroll
+                    for (int i = 0; i < E; ++i) ma[i] = ha[i];
                 }
-                if (write_a && xs + 1 < W) stg_vec<E>(pa_out, ha, q0, Q);
-                pa_out += dM;
-                pb_out += dM;
-                if (fin) {
-                    // marginal S_Omega = C + all four messages, lowest-index argmin
-                    int sv = kBig, sq = 0x7fffffff;
-#pragma unroll
-                    for (int i = 0; i < E; ++i) {
-                        const int v = cv[i] + ma[i] + mc[i] + md[i] + mb[i];
-                        if (q0 + i < Q && v < sv) {
-                            sv = v;
-                            sq = q0 + i;
-                        }
-                    }
-                    const int vbest = redux_min(sv);
-                    const int qbest = redux_min(sv == vbest ? sq : 0x7fffffff);
-                    if (lane == 0) A.labels[(size_t)y * W + (incx ? xs : W - 1 - xs)] = qbest;
-                }
-#pragma unroll
-                for (int i = 0; i < E; ++i) ma[i] = ha[i];
+                cp_async_wait_0();
             }
-            cp_async_wait_0();
-        }
+        };
+        if (fast_role)
+            run_row(std::true_type());
+        else
+            run_row(std::false_type());
     }
     if (A.trace && tid == 0) {
         A.trace[band * 4 + 0] = t_band0;
