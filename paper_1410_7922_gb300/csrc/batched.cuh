@@ -68,11 +68,11 @@ __global__ void __launch_bounds__(256) edp_batched_kernel(const __grid_constant_
             a.tag = pslot + 1;
             if (QUAD && a.l1 == 2)
                 ok = r1_dispatch(a.E, [&](auto e) {
-                    return r1_band<decltype(e)::value, QUAD, false, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+                    return r1_band<decltype(e)::value, QUAD>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
                 });
             else
                 ok = r1_dispatch(a.E, [&](auto e) {
-                    return r1_band<decltype(e)::value, false, false, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
+                    return r1_band<decltype(e)::value, false>(a, band, reinterpret_cast<int *>(smem_raw), &s_abort);
                 });
         } else {
             TeamArgs a = P.t;

@@ -263,10 +263,8 @@ __device__ __forceinline__ void quad_pair(int (&a)[E], int (&b)[E], int lane, in
 // QUAD: the build for the truncated quadratic prior (l1 = 2).  WT: the build
 // for per-edge prior multipliers A.wh / A.wv (the locally adaptive prior):
 // the message into the next pixel of the row uses its horizontal edge, the
-// message into the next row its vertical edge.  ROLES: a second build of the
-// row loop for the common hand-off role (off in the batched kernel, where
-// every body shares one kernel's registers and instruction cache).
-template <int E, bool QUAD = false, bool WT = false, bool ROLES = true>
+// message into the next row its vertical edge.
+template <int E, bool QUAD = false, bool WT = false>
 __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int *smem_i, volatile int *s_abort) {
     constexpr int Qp = 32 * E;  // padded vector length in shared memory
     constexpr int VM = msg_chunk<E>();
@@ -524,14 +522,10 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                 cp_async_wait_0();
             }
         };
-        if constexpr (ROLES) {
-            if (fast_role)
-                run_row(std::true_type());
-            else
-                run_row(std::false_type());
-        } else {
+        if (fast_role)
+            run_row(std::true_type());
+        else
             run_row(std::false_type());
-        }
     }
     if (A.trace && tid == 0) {
         A.trace[band * 4 + 0] = t_band0;
