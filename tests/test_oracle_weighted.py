@@ -128,3 +128,18 @@ def test_weighted_tiers_agree():
         p = _prior(lam=2, g=2, mode=mode)
         assert np.array_equal(oracle.edp_weighted(C, sp, p, wh, wv, iters=2, tier=0),
                               oracle.edp_weighted(C, sp, p, wh, wv, iters=2, tier=1))
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_weighted_quadratic_prior(k):
+    """The same identities for the truncated quadratic prior (l1 = 2): a
+    uniform multiplier k is the prior k lambda min(d^2, g^2), in both tiers."""
+    rng = np.random.default_rng(90 + k)
+    C = rng.integers(0, 40, size=(5, 6, 7)).astype(np.int32)
+    sp = {"R": 1, "Q": (7, 1, 1), "vmin": (0, 0, 0), "step": (1, 1, 1)}
+    w = np.full((5, 6), k, dtype=np.uint8)
+    for tier in (0, 1):
+        got = oracle.edp_weighted(C, sp, _prior(lam=2, g=3, l1=2), w, w, iters=2, tier=tier)
+        want = oracle.edp(C, sp, _prior(lam=2 * k, g=3, l1=2), iters=2, tier=tier)
+        assert np.array_equal(got, want)
+
