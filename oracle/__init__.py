@@ -70,7 +70,7 @@ def _load():
         lib.oracle_scanline_dp.argtypes = [P, i32, i32, ctypes.POINTER(_Prior), i32, P, P]
         lib.oracle_min_marginals.argtypes = [P, i32, i32, ctypes.POINTER(_Prior), i32, P]
         lib.oracle_edp.argtypes = [P, i32, i32, ctypes.POINTER(_Prior), i32, i32, P, P, P]
-        lib.oracle_edp_windowed.argtypes = [P, P, i32, i32, ctypes.POINTER(_Prior), i32, i32, P]
+        lib.oracle_edp_windowed.argtypes = [P, P, i32, i32, ctypes.POINTER(_Prior), i32, i32, P, P]
         lib.oracle_energy.argtypes = [P, P, i32, i32, ctypes.POINTER(_Prior), P]
         lib.oracle_edp_weighted.argtypes = [P, i32, i32, ctypes.POINTER(_Prior), i32, i32, P, P, P]
         lib.oracle_energy_weighted.argtypes = [P, P, i32, i32, ctypes.POINTER(_Prior), P, P, P]
@@ -214,17 +214,21 @@ def edp(C, space: dict, prior: dict, iters: int = 1, tier: int = 1, return_sums:
     return out[0] if len(out) == 1 else tuple(out)
 
 
-def edp_windowed(Cw, centre, space: dict, prior: dict, win: int, iters: int = 1) -> np.ndarray:
-    """EDP on per-pixel label boxes; labels are full-space linear indexes."""
+def edp_windowed(Cw, centre, space: dict, prior: dict, win: int, iters: int = 1, return_sums: bool = False):
+    """EDP on per-pixel label boxes; labels are full-space linear indexes.
+
+    Optionally also the final sums S_k [4][H][W][win^R] in box coordinates
+    (k = +x, -x, +y, -y)."""
     Cw = np.ascontiguousarray(Cw, dtype=np.int32)
-    H, W, _ = Cw.shape
+    H, W, QW = Cw.shape
     R = int(space["R"])
     centre = np.ascontiguousarray(centre, dtype=np.int32).reshape(H, W, R)
     labels = np.empty((H, W), dtype=np.int32)
+    S = np.empty((4, H, W, QW), dtype=np.int32) if return_sums else None
     p = make_prior(space, prior)
     _check(_load().oracle_edp_windowed(_ptr(Cw), _ptr(centre), W, H, ctypes.byref(p), int(win),
-                                       int(iters), _ptr(labels)), "edp_windowed")
-    return labels
+                                       int(iters), _ptr(labels), _ptr(S)), "edp_windowed")
+    return (labels, S) if return_sums else labels
 
 
 def energy(C, labels, space: dict, prior: dict) -> tuple[int, int, int, int]:

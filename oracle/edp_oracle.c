@@ -732,9 +732,11 @@ static int win_msg(void *vctx, int k, int x, int y, int64_t *out) {
     return ORACLE_OK;
 }
 
-/* labels receive full-space linear label indexes. */
+/* labels receive full-space linear label indexes.  S_out (optional)
+ * receives the final sums [4][H][W][win^R] in box coordinates (k order +x,
+ * -x, +y, -y). */
 int oracle_edp_windowed(const int32_t *Cw, const int32_t *centre, int W, int H,
-                        const oracle_prior_t *p, int win, int iters, int32_t *labels) {
+                        const oracle_prior_t *p, int win, int iters, int32_t *labels, int32_t *S_out) {
     int rc = check_prior(p);
     if (rc) return rc;
     if (W < 1 || H < 1 || iters < 0 || p->R > 2 || win < 1 || (win & 1) == 0)
@@ -748,7 +750,7 @@ int oracle_edp_windowed(const int32_t *Cw, const int32_t *centre, int W, int H,
     c.g.W = W;
     c.g.H = H;
     c.g.Q = p->R == 1 ? win : (int64_t)win * win;
-    c.S = malloc(sizeof(int32_t) * 4 * (size_t)W * H * c.g.Q);
+    c.S = S_out ? S_out : malloc(sizeof(int32_t) * 4 * (size_t)W * H * c.g.Q);
     if (!c.S) return ORACLE_ERR_NOMEM;
     rc = edp_drive(c.g, iters, Cw, c.S, win_msg, &c, labels, NULL);
     if (!rc)
@@ -757,7 +759,7 @@ int oracle_edp_windowed(const int32_t *Cw, const int32_t *centre, int W, int H,
             clamp_centre(p, win, centre + i * p->R, lo);
             labels[i] = (int32_t)box_label(p, lo, win, labels[i]);
         }
-    free(c.S);
+    if (!S_out) free(c.S);
     return rc;
 }
 

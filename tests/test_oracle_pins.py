@@ -417,3 +417,92 @@ def test_windowed_centre_clamped():
     a = oracle.cost_window(I0, I1, None, space, 1, 30, np.full((3, 4, 1), -5, np.int32), 3)
     b = oracle.cost_window(I0, I1, None, space, 1, 30, np.full((3, 4, 1), 1, np.int32), 3)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["horizontal 2x1, A left, B right", "vertical 1x2, A top, B bottom"])
+def test_windowed_distinct_boxes_handworked(name):
+    """Two pixels whose boxes differ: every sum and label worked by hand
+    (tests/golden/edp_window_2px_distinct_boxes_handworked.json)."""
+    gold = json.load(open(os.path.join(GOLDEN, "edp_window_2px_distinct_boxes_handworked.json")))
+    pr = {k: gold["prior"][k] for k in ("lam", "g", "l1", "mode")}
+    space = sp(gold["prior"]["Q"])
+    (c,) = [c for c in gold["cases"] if c["name"] == name]
+    Cw = np.array(c["Cw"], dtype=np.int32)
+    centre = np.array(c["centre"], dtype=np.int32)
+    labels, S = oracle.edp_windowed(Cw, centre, space, pr, gold["win"], iters=1, return_sums=True)
+    assert labels.tolist() == c["labels"]
+    for k, key in enumerate(["S_px", "S_mx", "S_py", "S_my"]):
+        assert S[k].tolist() == c[key], key
+
+
+def py_windowed_edp(Cw, centre, Q, pr, win, iters):
+    """Windowed Algorithm 1 restated in plain Python, independently of the
+    oracle: per-pixel boxes of win^R labels (centre clamped so the box fits),
+    messages by direct search over the source box evaluated on the target
+    box, passes P1..P4 of Sec. 4.2 in place, then Eq. DP_2D_1 / DP_2D_2 with
+    the lowest box index on ties.  Returns (full-space labels, sums)."""
+    H, W, R = len(Cw), len(Cw[0]), len(Q)
+    n = win ** R
+    half = (win - 1) // 2
+    lam, g, l1, mode = pr["lam"], pr["g"], pr["l1"], pr["mode"]
+
+    def lo(y, x):
+        return [min(max(centre[y][x][r], half), Q[r] - 1 - half) - half for r in range(R)]
+
+    def full(box_lo, w):
+        q = box_lo[0] + w % win
+        if R == 2:
+            q += Q[0] * (box_lo[1] + w // win)
+        return q
+
+    S = {k: [[[0] * n for _ in range(W)] for _ in range(H)] for k in ("+x", "-x", "+y", "-y")}
+    opp = {"+x": "-x", "-x": "+x", "+y": "-y", "-y": "+y"}
+    nb = {"+x": (-1, 0), "-x": (1, 0), "+y": (0, -1), "-y": (0, 1)}
+
+    def msg(k, x, y):
+        xn, yn = x + nb[k][0], y + nb[k][1]
+        if not (0 <= xn < W and 0 <= yn < H):
+            return [0] * n
+        ls, ld, src = lo(yn, xn), lo(y, x), S[k][yn][xn]
+        return [min(src[u] // 2 + V_def(full(ls, u), full(ld, v), Q, lam, g, l1, mode) for u in range(n))
+                for v in range(n)]
+
+    passes = [(("+x", "+y"), True, True), (("-x", "+y"), False, True),
+              (("+x", "-y"), True, False), (("-x", "-y"), False, False)]
+    for _ in range(iters):
+        for upd, incx, incy in passes:
+            for y in (range(H) if incy else range(H - 1, -1, -1)):
+                for x in (range(W) if incx else range(W - 1, -1, -1)):
+                    m = {k: msg(k, x, y) for k in S}
+                    new = {kp: [Cw[y][x][v] + sum(m[k][v] for k in S if k != opp[kp]) - m[opp[kp]][v]
+                                for v in range(n)] for kp in upd}
+                    for kp in upd:
+                        S[kp][y][x] = new[kp]
+    labels = [[0] * W for _ in range(H)]
+    for y in range(H):
+        for x in range(W):
+            m = {k: msg(k, x, y) for k in S}
+            tot = [Cw[y][x][v] + sum(m[k][v] for k in S) for v in range(n)]
+            labels[y][x] = full(lo(y, x), tot.index(min(tot)))
+    return labels, S
+
+
+@pytest.mark.parametrize("Q,win,mode,l1,iters", [((7,), 3, "joint", 1, 2), ((6, 5), 3, "per_axis", 1, 1),
+                                                  ((5, 6), 3, "joint", 1, 2), ((6, 6), 3, "per_axis", 2, 1),
+                                                  ((9,), 5, "joint", 2, 1)])
+def test_windowed_random_boxes_match_python_restatement(Q, win, mode, l1, iters):
+    """3x3 grids whose pixels all have different (random, partly clamped)
+    boxes: the oracle equals the independent Python restatement in every sum
+    and label."""
+    rng = np.random.default_rng(sum(Q) * 10 + win + l1)
+    R = len(Q)
+    n = win ** R
+    for trial in range(2):
+        Cw = rng.integers(0, 25, size=(3, 3, n)).astype(np.int32)
+        centre = np.stack([rng.integers(-1, Q[r] + 1, size=(3, 3)) for r in range(R)], axis=2).astype(np.int32)
+        pr = {"lam": int(rng.integers(1, 6)), "g": int(rng.integers(1, 4)), "l1": l1, "mode": mode}
+        want_lab, want_S = py_windowed_edp(Cw.tolist(), centre.tolist(), Q, pr, win, iters)
+        lab, S = oracle.edp_windowed(Cw, centre, sp(Q), pr, win, iters=iters, return_sums=True)
+        assert lab.tolist() == want_lab
+        for k, key in enumerate(["+x", "-x", "+y", "-y"]):
+            assert S[k].tolist() == want_S[key], key
