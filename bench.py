@@ -6,13 +6,23 @@ iterations (four scan passes each, Algorithm 1) with the marginal/argmin, and
 the energy -- one call of edp_solve_images.  Pixel-label updates per step =
 N * Q * (8 * j + 1): two sums written per pass, four passes per iteration,
 plus the marginal.  Workloads (--workload):
+  motion_edp_640x480_Q65x65  640x480 motion, the full 65x65 label space
+                             ([-32, 32]^2), cost min(|I1(x+o) - I0(x)|, 20),
+                             per-axis truncated-linear prior lambda = 15, K = 3
+                             (the default: the largest single-GPU workload);
+  motion_edp_320x240_Q33x33  320x240 motion, 33x33 labels, same prior;
   stereo_edp_450x375_Q64     450x375 stereo, 64 labels, cost min(|IL-IR|, 20),
-                             truncated-linear prior lambda = 20, K = 4 (default);
-  motion_edp_320x240_Q33x33  320x240 motion, 33x33 labels, per-axis lambda = 15, K = 3;
-  motion_edp_640x480_Q65x65  640x480 motion, full 65x65 labels, same prior.
+                             truncated-linear prior lambda = 20, K = 4.
+The other two workloads are also timed as side rows of the default line.
+
+Roofline: the scan pass is HBM-bound; its algorithmic bytes are those of the
+paper's sums form, 20 * Q bytes per pixel per pass (read C and the two old
+sums, write the two new sums), divided by the pass launches' CUDA-event time.
+The message form the kernels store moves fewer bytes; that count is reported
+beside it.
 
 Prints one JSON line (rank 0).  --impl reference runs the CPU oracle on the
-host cores instead (a bounded sample of the same workload).
+host cores instead (bounded samples of the same workload).
 """
 from __future__ import annotations
 
@@ -31,8 +41,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "EDP pixel-label updates/s"
 UNIT = "pixel-label updates/s"
-WORKLOAD = "stereo_edp_450x375_Q64"
-WORKLOADS = ("stereo_edp_450x375_Q64", "motion_edp_320x240_Q33x33", "motion_edp_640x480_Q65x65")
+WORKLOAD = "motion_edp_640x480_Q65x65"
+WORKLOADS = ("motion_edp_640x480_Q65x65", "motion_edp_320x240_Q33x33", "stereo_edp_450x375_Q64")
 
 
 def make_workload(name: str, pair: int = 0) -> dict:
@@ -129,6 +139,12 @@ def launch_bytes(nlaunch: int, W: int, H: int, Q: int, iters: int) -> list[int]:
             b += units * W * H * Q * 4 + (W * H * 4 if lab else 0)
         out.append(b)
     return out
+
+
+def sums_bytes_per_pass(W: int, H: int, Q: int) -> int:
+    """Algorithmic bytes of one scan pass in the paper's sums form: per pixel
+    read C(x, .) and the two old sums, write the two new sums, 20 * Q bytes."""
+    return 20 * Q * W * H
 
 
 def measured_peaks():
@@ -242,28 +258,70 @@ def bad_clocks(c) -> bool:
 # CPU oracle baseline
 # ---------------------------------------------------------------------------
 
-def cpu_oracle_sample(w, iters: int, min_seconds: float = 10.0, max_reps: int = 8):
-    """The oracle (as it is) on one host core, on the full frame, repeated
-    until about min_seconds of work."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_crop(job):
+    """The oracle, as it is, on rows [y0, y0 + rows) of a frame: cost volume,
+    EDP (RMS tier) and energy.  Returns the seconds it took."""
     import oracle
+    I0, I1, space, prior, l2, cmax, iters = job
+    t0 = time.perf_counter()
+    C = oracle.cost_volume(I0, I1, None, space, l2, cmax)
+    lab = oracle.edp(C, space, prior, iters=iters, tier=1)
+    oracle.energy(C, lab, space, prior)
+    return time.perf_counter() - t0
+
+
+def _crop_job(w, y0, rows, iters):
+    return (w["I0"][y0:y0 + rows].copy(), w["I1"][y0:y0 + rows].copy(), w["space"], w["prior"], w["l2"],
+            w["cmax"], iters)
+
+
+def crop_rows_for(w, iters, seconds: float) -> int:
+    """Image rows of a crop that takes about `seconds` of oracle work on one
+    host core (calibrated on a 2-row crop)."""
+    H = w["I0"].shape[0]
+    t2 = max(oracle_crop(_crop_job(w, 0, 2, iters)), 1e-4)
+    return max(2, min(H, int(2 * seconds / t2)))
+
+
+def oracle_pool(n: int):
+    """A process pool for the oracle, started with spawn (it may run after
+    the GPU has been initialised in this process)."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(n)
+
+
+def cpu_oracle_sample(w, iters: int, seconds: float = 8.0):
+    """The oracle as it is, timed on the host cores on bounded crops of the
+    frame: one crop on one core, then one crop per core on every core at
+    once (independent problems, one process each)."""
+    import oracle
+    oracle.build()
     H, W = w["I0"].shape
     Q = 1
     for r in range(w["space"]["R"]):
         Q *= w["space"]["Q"][r]
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
-        lab = oracle.edp(C, w["space"], w["prior"], iters=iters, tier=1)
-        oracle.energy(C, lab, w["space"], w["prior"])
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= min_seconds or reps >= max_reps:
-            break
-    updates = W * H * Q * (8 * iters + 1) * reps
-    return {"value": updates / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full {W}x{H} frame(s), j={iters}: oracle cost volume + EDP (RMS tier) + energy, "
-                      f"{el:.1f} s on 1 host core"}
+    rows = crop_rows_for(w, iters, seconds)
+    per_crop = W * rows * Q * (8 * iters + 1)
+    t1 = oracle_crop(_crop_job(w, 0, rows, iters))
+    n = host_cores()
+    jobs = [_crop_job(w, (k * rows) % max(1, H - rows + 1), rows, iters) for k in range(n)]
+    with oracle_pool(n) as pool:
+        pool.map(oracle_crop, jobs[:1])  # start-up of the workers
+        t0 = time.perf_counter()
+        pool.map(oracle_crop, jobs, chunksize=1)
+        tn = time.perf_counter() - t0
+    crop = f"{W}x{rows} crops of the {W}x{H} frame, j={iters}: oracle cost volume + EDP (RMS tier) + energy"
+    return {"value": n * per_crop / tn, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} {crop}, one process per host core, {tn:.1f} s wall",
+            "single_core": {"value": per_crop / t1, "unit": UNIT, "cores": 1,
+                            "sample": f"one {crop}, {t1:.1f} s on 1 host core"}}
 
 
 def run_reference(args, world, rank):
@@ -276,33 +334,27 @@ def run_reference(args, world, rank):
     Q = 1
     for r in range(w["space"]["R"]):
         Q *= w["space"]["Q"][r]
-
-    def frame(rows):
-        C = oracle.cost_volume(w["I0"][:rows], w["I1"][:rows], None, w["space"], w["l2"], w["cmax"])
-        lab = oracle.edp(C, w["space"], w["prior"], iters=args.iters, tier=1)
-        oracle.energy(C, lab, w["space"], w["prior"])
-
-    # each step: the first `rows` image rows of the frame, sized to about one
-    # second of oracle work on one host core (the whole frame when it fits)
-    t0 = time.perf_counter()
-    frame(2)
-    t2 = max(time.perf_counter() - t0, 1e-4)
-    rows = max(2, min(H, int(2 * 1.0 / t2)))
-    for _ in range(args.warmup):
-        frame(rows)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        frame(rows)
-    el = time.perf_counter() - t0
-    value = W * rows * Q * (8 * args.iters + 1) * args.steps / el
-    sample = (f"{W}x{rows} of the {W}x{H} frame per step (top rows), oracle cost volume + EDP (RMS tier) "
-              "+ energy on 1 host core")
+    # each step: one crop per host core, all at once, each about one second
+    # of oracle work (the whole frame when it fits)
+    rows = crop_rows_for(w, args.iters, 1.0)
+    n = host_cores()
+    jobs = [_crop_job(w, (k * rows) % max(1, H - rows + 1), rows, args.iters) for k in range(n)]
+    with oracle_pool(n) as pool:
+        for _ in range(args.warmup):
+            pool.map(oracle_crop, jobs, chunksize=1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(oracle_crop, jobs, chunksize=1)
+        el = time.perf_counter() - t0
+    value = n * W * rows * Q * (8 * args.iters + 1) * args.steps / el
+    sample = (f"{n} {W}x{rows} crops of the {W}x{H} frame per step, one process per host core: oracle cost "
+              "volume + EDP (RMS tier) + energy")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": args.workload, "W": W, "H": H, "Q": Q, "iters": args.iters},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -311,8 +363,20 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def time_solve_rows(edp, synth, torch):
-    """Side measurements of the other hot-path rows (device time, CUDA events)."""
+def pass_roofline(W: int, H: int, Q: int, iters: int, pass_ms: list[float], peak: float) -> dict:
+    """Roofline of the scan-pass launches of one solve: sums-form bytes (20 Q
+    per pixel per pass) over the launches' summed event time, and the
+    message-form bytes the kernels actually move."""
+    t = sum(pass_ms) * 1e-3
+    alg = 4 * iters * sums_bytes_per_pass(W, H, Q)
+    msg = sum(launch_bytes(len(pass_ms), W, H, Q, iters))
+    return {"achieved_gbs": alg / t / 1e9, "frac": alg / t / 1e9 / peak,
+            "message_form_gbs": msg / t / 1e9, "pass_ms": pass_ms}
+
+
+def time_solve_rows(edp, synth, torch, peak: float):
+    """Side measurements of the other workloads and hot-path rows (device
+    time, CUDA events; median of the repetitions)."""
     rows = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
@@ -339,23 +403,23 @@ def time_solve_rows(edp, synth, torch):
     re = torch.empty(48, dtype=torch.int64, device="cuda")
     ms = timed(lambda: edp.scanline_dp(C, w["space"], w["prior"], ws=ws, labels=lab, row_energy=re))
     rows["scanline_dp_64x48_Q16"] = {"ms": ms, "updates_per_s": 64 * 48 * 16 / (ms * 1e-3)}
-    # 2D motion EDP, 320x240, 33x33 labels
-    w = synth.workload_motion_320x240()
-    I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
-    C = edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"])
-    H, W, Q = C.shape
-    ws = edp.workspace(edp.OP_SOLVE, W, H, w["space"], w["prior"], 1)
-    lab = torch.empty((H, W), dtype=torch.int32, device="cuda")
-    evs = [ev() for _ in range(8)]
-    edp.set_profile_events(evs)
-    ms = timed(lambda: edp.solve(C, w["space"], w["prior"], iters=1, ws=ws, labels=lab), reps=10)
-    nl = edp.last_pass_launches()
-    pass_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(nl)]
-    edp.set_profile_events(None)
-    nbytes = sum(launch_bytes(nl, W, H, Q, 1))
-    rows["edp_motion_320x240_Q33x33"] = {
-        "ms": ms, "updates_per_s": W * H * Q * 9 / (ms * 1e-3), "pass_ms": pass_ms,
-        "pass_gbs": nbytes / (sum(pass_ms) * 1e-3) / 1e9}
+    # full EDP (j = 1) on the two smaller workloads: solve time and the
+    # roofline of its scan-pass launches
+    for name in ("motion_edp_320x240_Q33x33", "stereo_edp_450x375_Q64"):
+        w = make_workload(name)
+        I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
+        C = edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"])
+        H, W, Q = C.shape
+        ws = edp.workspace(edp.OP_SOLVE, W, H, w["space"], w["prior"], 1)
+        lab = torch.empty((H, W), dtype=torch.int32, device="cuda")
+        evs = [ev() for _ in range(8)]
+        edp.set_profile_events(evs)
+        ms = timed(lambda: edp.solve(C, w["space"], w["prior"], iters=1, ws=ws, labels=lab), reps=10)
+        nl = edp.last_pass_launches()
+        pass_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(nl)]
+        edp.set_profile_events(None)
+        rows[name] = {"ms_solve": ms, "updates_per_s": W * H * Q * 9 / (ms * 1e-3),
+                      "roofline": pass_roofline(W, H, Q, 1, pass_ms, peak)}
     # cost volume alone (write-bound), 450x375x64
     w = synth.workload_stereo_450x375()
     I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
@@ -543,16 +607,22 @@ def run_gpu(args, world, rank, local):
     updates = W * H * Q * (8 * j + 1)
     value = updates * world * args.steps / (total_ms * 1e-3)
 
-    # roofline of the dominant kernel (the scan pass): algorithmic bytes / time
-    nbytes = sum(launch_bytes(npass, W, H, Q, j))
+    # roofline of the dominant kernel (the scan pass): sums-form algorithmic
+    # bytes (20 Q per pixel per pass, four passes per iteration) / the pass
+    # launches' event time
     pass_total_s = sum(pass_ms) * 1e-3 / args.steps
+    nbytes = 4 * j * sums_bytes_per_pass(W, H, Q)
     achieved = nbytes / pass_total_s / 1e9
+    msg_bytes = sum(launch_bytes(npass, W, H, Q, j))
     peak, peak_kind = measured_peaks()
-    kernel = "edp_pass_r1_kernel" if (space["R"] == 1 and Q <= 256) else "edp_pass_team_kernel"
+    kernel = edp.last_pass_kernel()
     traffic = profiled_traffic(args.workload, kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
-                "bytes_per_launch_avg": nbytes / npass, "launch_ms_avg": sum(pass_ms) / args.steps / npass,
+                "bytes_per_launch_avg": nbytes / npass, "bytes_model": "20*Q per pixel per pass (sums form)",
+                "message_form_bytes_per_launch_avg": msg_bytes / npass,
+                "message_form_gbs": msg_bytes / pass_total_s / 1e9,
+                "launch_ms_avg": sum(pass_ms) / args.steps / npass,
                 "launches_per_solve": npass, "schedule": "paired sweeps" if npass == 2 * j else "one pass per launch",
                 "pass_ms": [p / args.steps for p in pass_ms]}
 
@@ -579,7 +649,7 @@ def run_gpu(args, world, rank, local):
 
     rows = None
     if not args.no_rows and rank == 0 and args.workload == WORKLOAD:
-        rows = time_solve_rows(edp, synth, torch)
+        rows = time_solve_rows(edp, synth, torch, peak)
     extra = {}
     if rank == 0:
         for name in [e for e in args.extra.split(",") if e]:

@@ -129,7 +129,11 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
  *   general_kernel   1: one-axis label spaces also take the multi-axis
  *                    scan-pass kernel instead of the warp-per-row one;
  *                    2: in addition, multi-axis spaces take its lane-group
- *                    form instead of the whole-line form.
+ *                    form instead of the whole-line form;
+ *                    3: two-axis spaces take the multi-axis kernel instead
+ *                    of the two-axis line kernel (which serves, by default,
+ *                    Q0 x Q1 = 17 x 17, 25 x 25, 33 x 33, 65 x 65 and
+ *                    27 x 15 with l1 = 1).
  * Used by the autotuner and the tests; results never depend on it.  A shape
  * the kernels cannot run makes the next solve return EDP_ERR_UNSUPPORTED.
  * Not thread-safe with concurrent solves. */
@@ -158,6 +162,11 @@ int edp_set_pass_pairs(int mode);
  * edp_set_profile_events.  Not thread-safe with concurrent solves. */
 int edp_last_pass_launches(void);
 
+/* Name of the scan-pass kernel the most recent edp_solve, edp_solve_images
+ * or edp_solve_windowed call in this process launched (static storage; ""
+ * before the first solve).  Not thread-safe with concurrent solves. */
+const char *edp_last_pass_kernel(void);
+
 /* Per-launch timing hook: while set, edp_solve (and edp_solve_images) record
  * events[2*i] / events[2*i + 1] (cudaEvent_t handles created by the caller)
  * on the solve's stream immediately before / after scan-pass launch i
@@ -167,6 +176,23 @@ int edp_last_pass_launches(void);
  * The library keeps the pointer, not a copy: the array must outlive the
  * solves that use it. */
 int edp_set_profile_events(void *const *events, int n_events);
+
+/* Bound of every wait between row bands of the scan-pass kernels (polls of
+ * the awaited flag or record before the wait gives up and the launch sets
+ * EDP_ERR_TIMEOUT in the device status word); 0 restores the default of
+ * 4,000,000.  Applies to the solves enqueued after the call.  Returns
+ * EDP_ERR_INVALID_ARG for a negative value.  Not thread-safe with
+ * concurrent solves. */
+int edp_set_spin_limit(long long polls);
+
+/* Test hook for the timeout path (0, the default, turns it off): in the
+ * solves enqueued after the call (edp_solve, edp_solve_images,
+ * edp_solve_weighted), the first row of row band `band` (> 0) waits for
+ * hand-off records of a tag no producer writes.  Its wait runs out after the
+ * spin limit, the launch sets EDP_ERR_TIMEOUT in the device status word and
+ * every kernel of the solve returns; the labels are then undefined.  Makes
+ * the wait expire without a fault.  Not thread-safe with concurrent solves. */
+int edp_test_hold_band(int band);
 
 /* Per-band trace of the scan passes (tracing hook): while set, scan-pass
  * launch i of a solve (counted as for edp_set_profile_events) writes, for
@@ -319,6 +345,11 @@ int edp_wta(const uint8_t *I0, const uint8_t *I1, int W, int H, int pitch, const
  * float32 [N][H][W][2], label coordinates relative to the space's middle. */
 long long edp_net_param_count(void);
 size_t edp_net_workspace_size(int N, int H, int W);
+/* Byte offset in the network workspace of the input of layer `layer` (0..5;
+ * layer 0's input is the feature tensor), which edp_net_forward leaves
+ * there for edp_net_backward: bf16 [N][H][W][C], C = 5, 32, 32, 32, 32, 32.
+ * (size_t)-1 for invalid arguments.  For inspection and tests. */
+size_t edp_net_activation_offset(int N, int H, int W, int layer);
 /* Forward pass; keeps the activations in ws for edp_net_backward. */
 int edp_net_forward(const float *params, const void *x, int N, int H, int W, float *out, void *ws, size_t ws_bytes,
                     edp_stream_t stream);
@@ -417,17 +448,26 @@ int edp_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stre
  * caller still passes C and labels (as for edp_solve); the scratch is a
  * static array of EDP_NOALLOC_SCRATCH_BYTES in the library's device memory,
  * which every GPU that loads the library holds until the process exits.
- * Problems whose edp_workspace_size(EDP_OP_SOLVE, ...) exceeds that size are
- * rejected with EDP_ERR_WORKSPACE before anything is enqueued.  The first
- * call on a device looks up the array's device address (once per device).
- * Every call shares the one array and it keeps the previous call's contents:
- * calls whose work overlaps on the GPU (other streams, other threads) race
- * and must be ordered by the caller.  The device status word is at the
- * start of the array; this entry point allocates nothing, so there is no
- * workspace pointer to pass to edp_get_device_status. */
+ * The call is edp_solve with that array as its workspace: the same argument
+ * checks in the same order and the same return codes, EDP_ERR_WORKSPACE for
+ * a problem whose edp_workspace_size(EDP_OP_SOLVE, ...) exceeds the array
+ * (nothing is enqueued then).  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  The address belongs to the
+ * device's primary context: after cudaDeviceReset of a device, do not call
+ * this entry point (or edp_noalloc_get_device_status) on it again in the
+ * same process.  Every call shares the one array and it keeps the previous
+ * call's contents: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be ordered by the caller. */
 #define EDP_NOALLOC_SCRATCH_BYTES (64u << 20)
 int edp_solve_noalloc(const int32_t *C, int W, int H, const edp_label_space *space,
                       const edp_params *params, int32_t *labels, edp_stream_t stream);
+
+/* Device status word of the most recent edp_solve_noalloc on the current
+ * device (EDP_ERR_TIMEOUT if a wait between row bands expired; the labels
+ * are then undefined), as edp_get_device_status reads it for a workspace.
+ * Synchronises `stream`. */
+int edp_noalloc_get_device_status(int *status, edp_stream_t stream);
 
 #ifdef __cplusplus
 }

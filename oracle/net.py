@@ -126,10 +126,14 @@ def smooth_l1(out: np.ndarray, target: np.ndarray) -> tuple[float, np.ndarray]:
     return float(loss.mean()), grad
 
 
-def backward(x: np.ndarray, params, target: np.ndarray, rounding=bf16):
-    """Loss and gradients [(dW, db)] with the precision contract above."""
+def backward(x: np.ndarray, params, target: np.ndarray, rounding=bf16, acts=None, out=None):
+    """Loss and gradients [(dW, db)] with the precision contract above.
+
+    acts / out: the stored layer inputs and the output of a forward pass to
+    differentiate (default: this reference's own forward pass of x)."""
     rnd = rounding or _exact
-    out, acts = forward(x, params, keep=True, rounding=rounding)
+    if acts is None:
+        out, acts = forward(x, params, keep=True, rounding=rounding)
     loss, g = smooth_l1(out, target)
     grads = [None] * len(params)
     for i in range(len(params) - 1, -1, -1):
@@ -140,6 +144,27 @@ def backward(x: np.ndarray, params, target: np.ndarray, rounding=bf16):
             gx = conv3x3_dgrad(gz, rnd(w))
             g = gx * (acts[i] > 0)  # ReLU of the previous layer
     return loss, grads
+
+
+def gradient_magnitudes(x: np.ndarray, params, target: np.ndarray, rounding=bf16, acts=None, out=None):
+    """Per parameter, the sum of the absolute values of the terms whose sum
+    is its gradient: sum |dL/dz| |input| for a weight, sum |dL/dz| for a
+    bias (same layout as the gradients of backward; acts / out as there).
+    Where bf16 rounding of an intermediate gradient can go either way, a
+    gradient moves by about one bf16 step of some of its terms, so these sums
+    scale the absolute error a gradient can carry from that rounding."""
+    rnd = rounding or _exact
+    if acts is None:
+        out, acts = forward(x, params, keep=True, rounding=rounding)
+    _, g = smooth_l1(out, target)
+    mags = [None] * len(params)
+    for i in range(len(params) - 1, -1, -1):
+        w, _ = params[i]
+        gz = rnd(g)
+        mags[i] = (conv3x3_wgrad(np.abs(gz), np.abs(acts[i])), np.abs(gz).sum(axis=(0, 2, 3)))
+        if i > 0:
+            g = conv3x3_dgrad(gz, rnd(w)) * (acts[i] > 0)
+    return mags
 
 
 def features(I0: np.ndarray, I1: np.ndarray, wta_flow: np.ndarray, wta_cost: np.ndarray,

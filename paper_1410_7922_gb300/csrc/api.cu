@@ -23,8 +23,13 @@ int g_tune_e = 0;        // labels per lane target override, scanline DP (0 = au
 int g_tune_t = 0;        // warps per row override, multi-axis scan pass (0 = automatic)
 int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass kernel
 int g_generic_team = 0;  // 1: multi-axis problems take the generic team body (tests)
+int g_line_off = 0;      // 1: two-axis problems take the team kernel instead of the line kernel (tests)
 int g_pass_pairs = 2;    // P1 + P2 and P3 + P4 as paired sweeps: 0 never, 1 always, 2 when every band is resident
 int g_last_launches = 0; // scan-pass launches of the most recent solve
+const char *g_last_kernel = "";  // scan-pass kernel of the most recent solve
+constexpr long long kSpinDefault = 4000000;
+long long g_spin_limit = kSpinDefault;  // polls before an inter-block wait gives up
+int g_hold_band = 0;     // test hook: the band whose first row waits for records never written
 void *const *g_prof_events = nullptr;  // optional per-pass events (profiling hook)
 int g_prof_n = 0;
 unsigned long long *g_trace = nullptr;  // optional per-band trace buffer (device)
@@ -177,7 +182,7 @@ int msg_stride(int Q) { return (Q + 3) / 4 * 4; }
 // (K - 1) * ring columns ahead of the last, which must cover the row
 int team_ring(int W, int resident) { return std::max(8, (W + resident - 2) / std::max(1, resident - 1) + 2); }
 struct SolveLayout {
-    size_t cons, counters, ll, ll_bytes, msg[4], end;
+    size_t cons, counters, lcons, lflag, ll, ll_bytes, msg[4], end;
     int Qm;
 };
 SolveLayout solve_layout(int W, int H, int Q, int R, int iters) {
@@ -186,7 +191,11 @@ SolveLayout solve_layout(int W, int H, int Q, int R, int iters) {
     L.Qm = msg_stride(Q);
     L.cons = kHeader;
     L.counters = align_up(L.cons + npass * H * 4);
-    L.ll = align_up(L.counters + npass * 4);
+    // two-axis line kernel: per-warp consumed columns and producer flags of
+    // the record ring, [4*iters][H][4] each
+    L.lcons = align_up(L.counters + npass * 4);
+    L.lflag = align_up(L.lcons + npass * H * 16);
+    L.ll = align_up(L.lflag + npass * H * 16);
     // one-axis kernel: a record per column of a paired sweep (2W) for every band boundary
     const size_t r1 = (R == 1 && Q <= 256) ? (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * 2 * W * Q * 8 : 0;
     const size_t tm = (size_t)H * team_ring(2 * W, kResidentMin) * L.Qm * 8;  // paired sweeps: 2W columns
@@ -279,6 +288,8 @@ bool team_shape(const Geometry &g, int T, int gpar, TeamShape *S) {
 // batched launch (0 = free).
 struct SolvePlan {
     bool r1;          // warp-per-row body (one label axis, Q <= 256)
+    bool line;        // two-axis line kernel (one label line per lane)
+    int Q0, Q1;       // its label-space shape
     int nbands;
     int threads;
     int em;
@@ -335,10 +346,66 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         a.NWR = NWR;
         a.nbands = (H + NWR - 1) / NWR;
         a.grid = a.nbands;
-        a.spin_limit = 4000000;
+        a.spin_limit = g_spin_limit;
         P->nbands = a.nbands;
         P->threads = 32 * NWR;
         P->em = a.EMt;
+        return EDP_OK;
+    }
+    // two label axes with a build of the line kernel (one label line per
+    // lane): single-problem solves of the linear prior
+    if (!fixed_threads && g.R == 2 && p->l1 == 1 && !g_line_off && !g_generic_team &&
+        pass_line_built(g.Qr[0], g.Qr[1])) {
+        P->line = true;
+        P->Q0 = g.Qr[0];
+        P->Q1 = g.Qr[1];
+        const int TW = pass_line_warps(P->Q0, P->Q1);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        sms = std::max(1, sms);
+        // rows per block: the most that still keeps every SM busy and every
+        // row band resident (one row per block otherwise)
+        int NT = 1;
+        if (g_tune_rb > 0) {
+            NT = std::min(g_tune_rb, 4);
+        } else {
+            for (int nt = 2; nt <= 4; ++nt) {
+                const int nb = (H + nt - 1) / nt;
+                const size_t sm = pass_line_smem(nt, P->Q0, P->Q1);
+                if (sm > (size_t)kMaxSmem) break;
+                const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, 32 * TW * nt, sm);
+                if (nb >= sms && nb <= occ * sms) NT = nt;
+            }
+        }
+        NT = std::max(1, std::min(NT, H));
+        P->smem = pass_line_smem(NT, P->Q0, P->Q1);
+        if (P->smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
+        TeamArgs &a = P->ta;
+        a.C = C;
+        for (int k = 0; k < 4; ++k) a.M[k] = M[k];
+        a.labels = labels;
+        a.ll = reinterpret_cast<int2 *>(ws + L.ll);
+        a.status = reinterpret_cast<int *>(ws);
+        a.W = W;
+        a.H = H;
+        a.Q = g.Q;
+        a.Qm = L.Qm;
+        a.R = g.R;
+        a.lam = p->lambda;
+        a.capv = (int)cap_value(p);
+        a.mode = p->prior_mode;
+        a.l1 = p->l1;
+        a.g = p->g;
+        a.T = TW;
+        a.NT = NT;
+        a.ring = team_ring(2 * W, kResidentMin);
+        a.nbands = (H + NT - 1) / NT;
+        a.spin_limit = g_spin_limit;
+        P->laps = (W + a.ring - 1) / a.ring;
+        P->nbands = a.nbands;
+        P->threads = 32 * TW * NT;
+        P->em = 0;
         return EDP_OK;
     }
     // multi-axis (team) kernel.  Lean form: two or more axes whose lines hold
@@ -437,7 +504,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
     a.l1 = p->l1;
     a.g = p->g;
     a.nbands = (H + NT - 1) / NT;
-    a.spin_limit = 4000000;
+    a.spin_limit = g_spin_limit;
     P->laps = (W + a.ring - 1) / a.ring;
     P->nbands = a.nbands;
     P->threads = fixed_threads ? fixed_threads : 32 * T * NT;
@@ -482,7 +549,7 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     SolvePlan P;
     int rc = plan_solve(C, W, H, g, p, labels, ws, &P);
     if (rc) return rc;
-    if (wh && !P.r1 && !P.ta.lean) return EDP_ERR_UNSUPPORTED;  // one-axis kernel, or the whole-line form
+    if (wh && !P.r1 && !P.line && !P.ta.lean) return EDP_ERR_UNSUPPORTED;  // not the lane-group form
     P.o.wh = P.ta.wh = wh;
     P.o.wv = P.ta.wv = wv;
     if ((rc = cuda_status(cudaMemsetAsync(ws, 0, control_bytes(P, W, g.Q), st)))) return rc;
@@ -490,7 +557,12 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     bool resident;  // every row band has a block at once
-    if (!P.r1) {
+    if (P.line) {
+        const int occ = std::max(1, edp_pass_line_occupancy(P.Q0, P.Q1, P.threads, P.smem));
+        grid_t = std::min(P.nbands, occ * sms);
+        if (grid_t < P.nbands && team_ring(2 * W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
+        resident = grid_t >= P.nbands;
+    } else if (!P.r1) {
         const int occ = std::max(1, edp_pass_team_occupancy(P.em, P.ta.lean, 0, P.threads, P.smem));
         grid_t = std::min(P.nbands, occ * sms);
         // a smaller resident set than the ring was sized for could stall the back-pressure
@@ -505,6 +577,7 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     const bool pairs = pairs_for(resident);
     const int per_it = pairs ? 2 : 4;
     g_last_launches = per_it * p->iters;
+    g_last_kernel = P.r1 ? "edp_pass_r1_kernel" : (P.line ? "edp_pass_line_kernel" : "edp_pass_team_kernel");
     for (int it = 0; it < p->iters; ++it) {
         for (int k = 0; k < per_it; ++k) {
             const int launch = it * per_it + k;
@@ -514,10 +587,22 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
             const bool prof = g_prof_events && 2 * launch + 1 < g_prof_n;
             if (prof && cudaEventRecord((cudaEvent_t)g_prof_events[2 * launch], st) != cudaSuccess)
                 return EDP_ERR_CUDA;
-            if (P.r1) {
+            if (P.line) {
+                TeamArgs a = P.ta;
+                const int slot = it * 4 + set_launch(a, it, k, p->iters, pairs);
+                a.cons = reinterpret_cast<unsigned *>(ws + P.L.lcons) + (size_t)slot * H * 4;
+                a.rflag = reinterpret_cast<unsigned *>(ws + P.L.lflag) + (size_t)slot * H * 4;
+                a.tag0 = 1 + slot * P.laps;
+                a.hold_band = g_hold_band;
+                a.band_counter = reinterpret_cast<unsigned *>(ws + P.L.counters) + slot;
+                a.grid = grid_t;
+                a.trace = trace;
+                if (launch_edp_pass_line(a, P.Q0, P.Q1, P.threads, P.smem, st)) return EDP_ERR_CUDA;
+            } else if (P.r1) {
                 PassR1Args a = P.o;
                 const int slot = it * 4 + set_launch(a, it, k, p->iters, pairs);  // counters of the first pass
                 a.tag = slot + 1;
+                a.hold_band = g_hold_band;
                 a.band_counter = reinterpret_cast<unsigned *>(ws + P.L.counters) + slot;
                 a.trace = trace;
                 if (launch_edp_pass_r1(a, P.threads, P.smem, st)) return EDP_ERR_CUDA;
@@ -527,6 +612,7 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
                 const int slot = it * 4 + set_launch(a, it, k, p->iters, pairs);
                 a.cons = reinterpret_cast<unsigned *>(ws + P.L.cons) + (size_t)slot * H;
                 a.tag0 = 1 + slot * P.laps;
+                a.hold_band = g_hold_band;
                 a.band_counter = reinterpret_cast<unsigned *>(ws + P.L.counters) + slot;
                 a.grid = grid_t;
                 a.trace = trace;
@@ -633,12 +719,13 @@ const char *edp_status_string(int status) {
 int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, int general_kernel) {
     if (rows_per_block < 0 || labels_per_lane < 0 || labels_per_lane > kEM) return EDP_ERR_INVALID_ARG;
     if (warps_per_row < 0 || warps_per_row > 12) return EDP_ERR_INVALID_ARG;
-    if (general_kernel < 0 || general_kernel > 2) return EDP_ERR_INVALID_ARG;
+    if (general_kernel < 0 || general_kernel > 3) return EDP_ERR_INVALID_ARG;
     g_tune_rb = rows_per_block;
     g_tune_e = labels_per_lane;
     g_tune_t = warps_per_row;
-    g_force_general = general_kernel >= 1;
+    g_force_general = general_kernel == 1 || general_kernel == 2;
     g_generic_team = general_kernel == 2;
+    g_line_off = general_kernel == 3;
     return EDP_OK;
 }
 
@@ -649,6 +736,20 @@ int edp_set_pass_pairs(int mode) {
 }
 
 int edp_last_pass_launches(void) { return g_last_launches; }
+
+const char *edp_last_pass_kernel(void) { return g_last_kernel; }
+
+int edp_set_spin_limit(long long polls) {
+    if (polls < 0) return EDP_ERR_INVALID_ARG;
+    g_spin_limit = polls ? polls : kSpinDefault;
+    return EDP_OK;
+}
+
+int edp_test_hold_band(int band) {
+    if (band < 0) return EDP_ERR_INVALID_ARG;
+    g_hold_band = band;
+    return EDP_OK;
+}
 
 int edp_set_profile_events(void *const *events, int n_events) {
     if (n_events < 0 || (n_events > 0 && !events)) return EDP_ERR_INVALID_ARG;
@@ -977,7 +1078,7 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     B.queue = reinterpret_cast<unsigned *>(ws + kHeader);
     B.done = reinterpret_cast<unsigned *>(ws + kHeader + 256);
     B.status = status;
-    B.spin_limit = 4000000;
+    B.spin_limit = g_spin_limit;
     size_t off = ctrl;
     long long max_entries = 0, max_pixels = 0;
     // one block shape for the wave: 8 warps (one-axis bands of 8 rows, or
@@ -1242,7 +1343,7 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
     a.Q1w = space->Q[1];
     a.em = params->l1;  // the windowed build of this prior power
     a.nbands = (H + NT - 1) / NT;
-    a.spin_limit = 4000000;
+    a.spin_limit = g_spin_limit;
     const int laps = (W + a.ring - 1) / a.ring;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1254,6 +1355,7 @@ int edp_solve_windowed(const int32_t *Cw, const int32_t *centre, int win, int W,
     const bool pairs = pairs_for(a.grid >= a.nbands);
     const int per_it = pairs ? 2 : 4;
     g_last_launches = per_it * params->iters;
+    g_last_kernel = "edp_pass_team_kernel";
     for (int it = 0; it < params->iters; ++it)
         for (int k = 0; k < per_it; ++k) {
             const int launch = it * per_it + k;
@@ -1305,6 +1407,11 @@ long long edp_net_param_count(void) { return net_param_count(); }
 size_t edp_net_workspace_size(int N, int H, int W) {
     if (N < 1 || H < 1 || W < 1) return 0;
     return net_workspace_bytes((long long)N * H * W);
+}
+
+size_t edp_net_activation_offset(int N, int H, int W, int layer) {
+    if (N < 1 || H < 1 || W < 1 || layer < 0 || layer > 5) return (size_t)-1;
+    return net_activation_offset((long long)N * H * W, layer);
 }
 
 int edp_net_forward(const float *params, const void *x, int N, int H, int W, float *out, void *ws, size_t ws_bytes,

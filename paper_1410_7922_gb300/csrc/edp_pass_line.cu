@@ -1,0 +1,61 @@
+// edp_pass_line.cu -- the two-axis scan-pass kernel (one label line per
+// lane); the band body is in pass_line.cuh.  One build per label-space shape
+// (Q0 x Q1): the lines are held in registers with exact lengths.
+#include <algorithm>
+
+#include "pass_line.cuh"
+
+namespace edp {
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(line::kMaxThreads, 1) edp_pass_line_kernel(TeamArgs A) {
+    extern __shared__ __align__(16) int smem_i[];
+    __shared__ int s_band;
+    __shared__ volatile int s_abort;
+    if (threadIdx.x == 0) s_abort = (*(volatile int *)A.status != 0);
+    __syncthreads();
+    if (s_abort) return;
+    while (true) {
+        if (threadIdx.x == 0) s_band = atomicAdd(A.band_counter, 1);
+        __syncthreads();
+        const int band = s_band;
+        if (band >= A.nbands) break;
+        if (!line_band<LA, LB>(A, band, smem_i, &s_abort)) return;
+    }
+}
+
+// the shapes with a build: (Q0, Q1) = (LB, LA)
+static void *line_kernel_for(int Q0, int Q1) {
+    if (Q0 == 65 && Q1 == 65) return reinterpret_cast<void *>(edp_pass_line_kernel<65, 65>);
+    if (Q0 == 33 && Q1 == 33) return reinterpret_cast<void *>(edp_pass_line_kernel<33, 33>);
+    if (Q0 == 25 && Q1 == 25) return reinterpret_cast<void *>(edp_pass_line_kernel<25, 25>);
+    if (Q0 == 17 && Q1 == 17) return reinterpret_cast<void *>(edp_pass_line_kernel<17, 17>);
+    if (Q0 == 27 && Q1 == 15) return reinterpret_cast<void *>(edp_pass_line_kernel<15, 27>);
+    return nullptr;
+}
+
+bool pass_line_built(int Q0, int Q1) { return line_kernel_for(Q0, Q1) != nullptr; }
+
+int pass_line_warps(int Q0, int Q1) { return (std::max(Q0, Q1) + 31) / 32; }
+
+size_t pass_line_smem(int NT, int Q0, int Q1) { return (size_t)NT * line::team_ints(Q1, Q0) * 4; }
+
+int edp_pass_line_occupancy(int Q0, int Q1, int threads, size_t smem) {
+    void *k = line_kernel_for(Q0, Q1);
+    if (!k) return 0;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
+    return occ;
+}
+
+int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, int threads, size_t smem, cudaStream_t st) {
+    void *k = line_kernel_for(Q0, Q1);
+    if (!k) return -1;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void *args[] = {const_cast<TeamArgs *>(&a)};
+    if (cudaLaunchKernel(k, dim3(a.grid), dim3(threads), args, smem, st) != cudaSuccess) return -2;
+    return 0;
+}
+
+}  // namespace edp

@@ -44,7 +44,8 @@ struct TeamArgs {
     int *M[4];              // [H][W][Qm] messages into each pixel from +x, -x, +y, -y
     int *labels;            // [H][W], written by the final pass
     int2 *ll;               // [nbands][ring][Qm] {value, tag} records between bands
-    unsigned *cons;         // [nbands] columns of each band's records consumed
+    unsigned *cons;         // [nbands] columns of each band's records consumed ([nbands][4] per warp: line kernel)
+    unsigned *rflag;        // line kernel: [nbands][4] columns of records each producing warp has written
     unsigned *band_counter;
     int *status;
     int W, H, Q, Qm, R;     // Qm: message stride, Q rounded up to a multiple of 4
@@ -65,11 +66,20 @@ struct TeamArgs {
     int em;                 // instantiation bound: labels per lane, or line length (lean)
     int nbands, grid;
     long long spin_limit;
+    int hold_band;          // test hook: > 0, the first row of this band waits for records never written
     unsigned long long *trace;  // optional: per band {start ns, end ns, 0, sm id}
 };
 int launch_edp_pass_team(const TeamArgs &a, int threads, size_t smem, cudaStream_t st);
 int edp_pass_team_occupancy(int em, int lean, int win, int threads, size_t smem);
 size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb);
+
+// one EDP scan pass, two label axes, one label line per lane (edp_pass_line.cu);
+// uses TeamArgs with T = warps per row, NT = rows per block
+bool pass_line_built(int Q0, int Q1);
+int pass_line_warps(int Q0, int Q1);
+size_t pass_line_smem(int NT, int Q0, int Q1);
+int edp_pass_line_occupancy(int Q0, int Q1, int threads, size_t smem);
+int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, int threads, size_t smem, cudaStream_t st);
 
 // one EDP scan pass, one label axis, one warp per row (edp_pass_r1.cu)
 struct PassR1Args {
@@ -90,6 +100,7 @@ struct PassR1Args {
     int NWR;                // rows (warps) per block
     int nbands, grid, tag;
     long long spin_limit;
+    int hold_band;          // test hook: > 0, the first row of this band waits for records never written
     unsigned long long *trace;
 };
 int launch_edp_pass_r1(const PassR1Args &a, int threads, size_t smem, cudaStream_t st);
@@ -195,6 +206,7 @@ int launch_cost_window(const CostArgs &a, const int *centre, int n, cudaStream_t
 // proposal network (net.cu)
 long long net_param_count();
 size_t net_workspace_bytes(long long npix);
+size_t net_activation_offset(long long npix, int layer);
 int net_forward(const float *params, const void *x, int N, int H, int W, float *out, unsigned char *ws,
                 cudaStream_t st);
 int net_backward(const float *params, const float *out, const float *target, int N, int H, int W, float *grad,

@@ -403,6 +403,7 @@ int conv(const __nv_bfloat16 *in, int N, int H, int W, int Cin, int Cout, const 
 
 long long net_param_count() { return param_offset(kLayers); }
 size_t net_workspace_bytes(long long npix) { return net_layout(npix).end; }
+size_t net_activation_offset(long long npix, int layer) { return net_layout(npix).act[layer]; }
 
 int net_forward(const float *params, const void *x, int N, int H, int W, float *out, unsigned char *ws, cudaStream_t st) {
     const long long npix = (long long)N * H * W;

@@ -25,7 +25,9 @@ std::mutex g_scratch_mu;
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The
+// cached address belongs to the device's primary context: after a
+// cudaDeviceReset of that device it is stale (see edp.h).
 int scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return EDP_ERR_CUDA;
@@ -44,14 +46,21 @@ int scratch_address(void **out) {
 
 extern "C" int edp_solve_noalloc(const int32_t *C, int W, int H, const edp_label_space *space,
                                  const edp_params *params, int32_t *labels, edp_stream_t stream) {
-    if (!C || !labels || !space || !params || W < 1 || H < 1) return EDP_ERR_INVALID_ARG;
-    const size_t need = edp_workspace_size(EDP_OP_SOLVE, W, H, space, params);
-    if (need == 0) return EDP_ERR_INVALID_ARG;
-    if (need > EDP_NOALLOC_SCRATCH_BYTES) return EDP_ERR_WORKSPACE;
     void *ws = nullptr;
     const int rc = scratch_address(&ws);
     if (rc) return rc;
-    // edp_solve clears the status word, the counters and the hand-off records
-    // it uses at the start of every call; the message arrays need no clearing.
+    // edp_solve with the array as its workspace: the same argument checks in
+    // the same order, so the same codes (EDP_ERR_WORKSPACE when the problem
+    // needs more than the array holds).  It clears the status word, the
+    // counters and the hand-off records it uses at the start of every call;
+    // the message arrays need no clearing.
     return edp_solve(C, W, H, space, params, labels, ws, EDP_NOALLOC_SCRATCH_BYTES, stream);
+}
+
+extern "C" int edp_noalloc_get_device_status(int *status, edp_stream_t stream) {
+    if (!status) return EDP_ERR_INVALID_ARG;
+    void *ws = nullptr;
+    const int rc = scratch_address(&ws);
+    if (rc) return rc;
+    return edp_get_device_status(ws, EDP_NOALLOC_SCRATCH_BYTES, status, stream);
 }

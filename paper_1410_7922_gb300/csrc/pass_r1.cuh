@@ -284,6 +284,9 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
     __syncthreads();
     unsigned long long t_band0 = (A.trace && tid == 0) ? global_ns() : 0, t_wait = 0;
     const int r = band * NWR + w;
+    // tag of the records from the previous band (the test hook hold_band makes
+    // one band expect a tag no producer writes, so its wait runs out)
+    const int tag_in = A.tag + (band == A.hold_band ? 0x20000000 : 0);
     bool aborted = false;
     if (w < NWR && r < H) {
         const int y = incy ? r : H - 1 - r;
@@ -382,7 +385,7 @@ __device__ __forceinline__ bool r1_band(const PassR1Args &A, const int band, int
                         long long spins = 0;
                         bool bad = false;
                         const int2 *p = (FAST || w > 0) ? mb_in + (s & (kMb - 1)) * Qp : ll_in + (size_t)s * Q;
-                        const int want = (FAST || w > 0) ? s + 1 : A.tag;
+                        const int want = (FAST || w > 0) ? s + 1 : tag_in;
                         const unsigned long long tw = (!FAST && A.trace && w == 0) ? global_ns() : 0;
                         // first look straight-line (the record is usually there), then the
                         // bounded spin

@@ -489,6 +489,9 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
             }
             cp_async_commit();
         };
+        // tag of the first ring lap of the records from the previous band (the
+        // test hook hold_band makes one band expect a tag no producer writes)
+        const int tag_in0 = A.tag0 + (band == A.hold_band ? 0x20000000 : 0);
         unsigned cons_seen = 0;     // consumer progress seen by this producer (lane tl == 0)
         int mb_cons_seen = 0;       // same, for the mailbox consumer
         bool aborted = false;
@@ -522,7 +525,7 @@ __device__ __forceinline__ bool team_band(const TeamArgs &A, const int band, int
                 }
             } else if (from_ring) {
                 const int2 *p = ll_in + (size_t)(s % ring) * Qm;
-                const int tag = A.tag0 + s / ring;
+                const int tag = tag_in0 + s / ring;
                 int *dst = mbox + (s % kmb) * Qm;
                 // kRecBatch record pairs per lane in flight: the first loads of a
                 // batch are independent, so a column costs about one L2 round

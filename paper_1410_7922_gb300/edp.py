@@ -69,6 +69,9 @@ def load() -> ctypes.CDLL:
         "edp_set_profile_events": ([P, I], I),
         "edp_set_pass_pairs": ([I], I),
         "edp_last_pass_launches": ([], I),
+        "edp_last_pass_kernel": ([], ctypes.c_char_p),
+        "edp_set_spin_limit": ([ctypes.c_longlong], I),
+        "edp_test_hold_band": ([I], I),
         "edp_set_trace": ([P, SZ], I),
         "edp_cost_volume": ([P, P, P, I, I, I, LS, PR, P, P], I),
         "edp_scanline_dp": ([P, I, I, LS, PR, P, P, P, SZ, P], I),
@@ -92,12 +95,14 @@ def load() -> ctypes.CDLL:
         "edp_net_targets": ([P, P, I, LS, P, P], I),
         "edp_net_param_count": ([], ctypes.c_longlong),
         "edp_net_workspace_size": ([I, I, I], SZ),
+        "edp_net_activation_offset": ([I, I, I, I], SZ),
         "edp_net_forward": ([P, P, I, I, I, P, P, SZ, P], I),
         "edp_net_backward": ([P, P, P, I, I, I, P, P, P, SZ, P], I),
         "edp_net_adam": ([P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P], I),
         "edp_net_features": ([P, P, P, P, I, I, LS, ctypes.c_float, ctypes.c_float, P, P], I),
         "edp_net_centres": ([P, I, LS, P, P], I),
         "edp_solve_noalloc": ([P, I, I, LS, PR, P, P], I),
+        "edp_noalloc_get_device_status": ([ctypes.POINTER(I), P], I),
         "edp_solve_batched": ([ctypes.POINTER(Problem), I, P, SZ, P], I),
     }
     for name, (args, res) in sig.items():
@@ -114,10 +119,12 @@ def exported_symbols() -> list[str]:
             "edp_cost_volume", "edp_scanline_dp", "edp_solve", "edp_energy", "edp_solve_images",
             "edp_solve_images_host", "edp_get_device_status", "edp_batch_workspace_size",
             "edp_solve_batched", "edp_workspace_size_windowed", "edp_cost_window", "edp_solve_windowed",
-            "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_forward", "edp_net_backward",
-            "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc", "edp_coarse_labels",
+            "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_activation_offset", "edp_net_forward", "edp_net_backward",
+            "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc",
+            "edp_noalloc_get_device_status", "edp_coarse_labels",
             "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_scanline_marginals",
-            "edp_set_pass_pairs", "edp_last_pass_launches", "edp_edge_weights", "edp_solve_weighted",
+            "edp_set_pass_pairs", "edp_last_pass_launches", "edp_last_pass_kernel", "edp_set_spin_limit",
+            "edp_test_hold_band", "edp_edge_weights", "edp_solve_weighted",
             "edp_energy_weighted"]
 
 
@@ -188,7 +195,8 @@ def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0, general_kernel
                warps_per_row: int = 0) -> None:
     """Launch shape of the DP kernels (0 = automatic); results never depend on it.
     general_kernel: 1 = one-axis spaces take the multi-axis kernel, 2 = and
-    multi-axis spaces its lane-group form."""
+    multi-axis spaces its lane-group form, 3 = two-axis spaces take the
+    multi-axis kernel instead of the two-axis line kernel."""
     _check(load().edp_set_tuning(int(rows_per_block), int(labels_per_lane), int(warps_per_row),
                                  int(general_kernel)), "set_tuning")
 
@@ -211,6 +219,22 @@ def set_pass_pairs(mode) -> None:
 def last_pass_launches() -> int:
     """Scan-pass launches of the most recent solve in this process."""
     return int(load().edp_last_pass_launches())
+
+
+def set_spin_limit(polls: int = 0) -> None:
+    """Polls before a wait between row bands gives up (0: the default)."""
+    _check(load().edp_set_spin_limit(int(polls)), "set_spin_limit")
+
+
+def test_hold_band(band: int = 0) -> None:
+    """Timeout test hook: the first row of `band` (> 0) waits for records
+    that are never written (0: off)."""
+    _check(load().edp_test_hold_band(int(band)), "test_hold_band")
+
+
+def last_pass_kernel() -> str:
+    """Name of the scan-pass kernel the most recent solve launched."""
+    return load().edp_last_pass_kernel().decode()
 
 
 def set_profile_events(events) -> None:
@@ -525,6 +549,20 @@ def net_workspace(N: int, H: int, W: int, device="cuda"):
     if n == 0:
         raise EdpError(ERR_INVALID_ARG, "net_workspace_size")
     return torch.empty(int(n), dtype=torch.uint8, device=device)
+
+
+NET_CHANNELS = (5, 32, 32, 32, 32, 32, 2)
+
+
+def net_activations(ws, N: int, H: int, W: int) -> list:
+    """The inputs of the six layers that the last net_forward left in ws
+    (bf16 [N][H][W][C] views)."""
+    out = []
+    for layer in range(6):
+        off = int(load().edp_net_activation_offset(int(N), int(H), int(W), layer))
+        n = N * H * W * NET_CHANNELS[layer]
+        out.append(ws[off:off + 2 * n].view(torch.bfloat16).view(N, H, W, NET_CHANNELS[layer]))
+    return out
 
 
 def net_forward(params_f32, x_bf16, ws, out=None, stream=None):

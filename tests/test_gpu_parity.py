@@ -144,9 +144,24 @@ def test_scanline_launch_shapes(edp_lib, rb, e):
 # EDP
 # --------------------------------------------------------------------------
 
+LINE_SHAPES = {(17, 17), (25, 25), (33, 33), (65, 65), (27, 15)}
+
+
 def run_edp(edp_lib, C, space, prior, iters):
+    """The oracle's labels and the GPU's.  Two-axis spaces the line kernel
+    is built for also run on the multi-axis kernel (the same labels are
+    asserted here)."""
     want = oracle.edp(C, space, prior, iters=iters, tier=1)
     got = host(edp_lib.solve(dev(C), space, prior, iters=iters))
+    if tuple(space["Q"][:space["R"]]) in LINE_SHAPES and prior.get("l1", 1) == 1:
+        assert edp_lib.last_pass_kernel() == "edp_pass_line_kernel"
+        edp_lib.set_tuning(0, 0, 3)
+        try:
+            other = host(edp_lib.solve(dev(C), space, prior, iters=iters))
+            assert edp_lib.last_pass_kernel() == "edp_pass_team_kernel"
+        finally:
+            edp_lib.set_tuning(0, 0, 0)
+        assert np.array_equal(other, want), "multi-axis kernel"
     return want, got
 
 

@@ -121,3 +121,22 @@ def test_targets_and_residual_centres():
     assert net.centres_residual(out, b, Q).tolist() == [[2, 0], [2, 0], [4, 3]]
     # corrections below 2 labels dropped: (1, -1) -> base; (1, -3) and (9, 9) kept
     assert net.centres_residual(out, b, Q, min_shift=2).tolist() == [[1, 1], [2, 0], [4, 3]]
+
+
+def test_gradient_magnitudes_bound_the_gradients():
+    """The absolute-value sums bound every gradient (triangle inequality) and
+    equal its magnitude where every term has one sign: the last layer's bias
+    gradient with all outputs above their targets."""
+    rng = np.random.default_rng(4)
+    params = net.init_params(6)
+    params = [(w, rng.normal(0, 0.1, size=b.shape)) for w, b in params]
+    x = net.bf16(rng.uniform(0, 1, size=(1, 5, 6, 7)))
+    tgt = rng.normal(0, 2, size=(1, 2, 6, 7))
+    _, grads = net.backward(x, params, tgt)
+    mags = net.gradient_magnitudes(x, params, tgt)
+    for (gw, gb), (mw, mb) in zip(grads, mags):
+        assert np.all(mw >= np.abs(gw) - 1e-15) and np.all(mb >= np.abs(gb) - 1e-15)
+    out = net.forward(x, params)
+    _, grads = net.backward(x, params, out - 5.0)
+    mags = net.gradient_magnitudes(x, params, out - 5.0)
+    assert np.allclose(mags[-1][1], np.abs(grads[-1][1]), rtol=1e-12)
