@@ -131,9 +131,10 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
  *                    2: in addition, multi-axis spaces take its lane-group
  *                    form instead of the whole-line form;
  *                    3: two-axis spaces take the multi-axis kernel instead
- *                    of the two-axis line kernel (which serves, by default,
- *                    Q0 x Q1 = 17 x 17, 25 x 25, 33 x 33, 65 x 65 and
- *                    27 x 15 with l1 = 1).
+ *                    of the two-axis line kernel; 4: two-axis spaces take
+ *                    the line kernel wherever it is built (Q0 x Q1 = 17 x
+ *                    17, 25 x 25, 33 x 33, 65 x 65 and 27 x 15, l1 = 1;
+ *                    by default it serves 65 x 65).
  * Used by the autotuner and the tests; results never depend on it.  A shape
  * the kernels cannot run makes the next solve return EDP_ERR_UNSUPPORTED.
  * Not thread-safe with concurrent solves. */

@@ -23,7 +23,7 @@ int g_tune_e = 0;        // labels per lane target override, scanline DP (0 = au
 int g_tune_t = 0;        // warps per row override, multi-axis scan pass (0 = automatic)
 int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass kernel
 int g_generic_team = 0;  // 1: multi-axis problems take the generic team body (tests)
-int g_line_off = 0;      // 1: two-axis problems take the team kernel instead of the line kernel (tests)
+int g_line_mode = 0;     // two-axis line kernel: 0 where it is faster (65-label lines), 1 off, 2 wherever built
 int g_pass_pairs = 2;    // P1 + P2 and P3 + P4 as paired sweeps: 0 never, 1 always, 2 when every band is resident
 int g_last_launches = 0; // scan-pass launches of the most recent solve
 const char *g_last_kernel = "";  // scan-pass kernel of the most recent solve
@@ -354,7 +354,11 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
     }
     // two label axes with a build of the line kernel (one label line per
     // lane): single-problem solves of the linear prior
-    if (!fixed_threads && g.R == 2 && p->l1 == 1 && !g_line_off && !g_generic_team &&
+    // (measured: faster than the whole-line multi-axis form where lines hold
+    // 65 labels, whose rows the multi-axis kernel cannot all keep resident;
+    // slower at 33 x 33)
+    const bool line_pick = g_line_mode == 2 || (g_line_mode == 0 && std::max(g.Qr[0], g.Qr[1]) > 33);
+    if (!fixed_threads && g.R == 2 && p->l1 == 1 && line_pick && !g_generic_team &&
         pass_line_built(g.Qr[0], g.Qr[1])) {
         P->line = true;
         P->Q0 = g.Qr[0];
@@ -719,13 +723,13 @@ const char *edp_status_string(int status) {
 int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, int general_kernel) {
     if (rows_per_block < 0 || labels_per_lane < 0 || labels_per_lane > kEM) return EDP_ERR_INVALID_ARG;
     if (warps_per_row < 0 || warps_per_row > 12) return EDP_ERR_INVALID_ARG;
-    if (general_kernel < 0 || general_kernel > 3) return EDP_ERR_INVALID_ARG;
+    if (general_kernel < 0 || general_kernel > 4) return EDP_ERR_INVALID_ARG;
     g_tune_rb = rows_per_block;
     g_tune_e = labels_per_lane;
     g_tune_t = warps_per_row;
     g_force_general = general_kernel == 1 || general_kernel == 2;
     g_generic_team = general_kernel == 2;
-    g_line_off = general_kernel == 3;
+    g_line_mode = general_kernel == 3 ? 1 : (general_kernel == 4 ? 2 : 0);
     return EDP_OK;
 }
 

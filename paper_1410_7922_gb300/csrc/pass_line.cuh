@@ -38,6 +38,8 @@
 // so no fence is on the path.  Every wait is a bounded spin that sets the
 // launch's status word when it runs out.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -71,16 +73,22 @@ __device__ __forceinline__ int ld_acq_cta(const int *p) {
 __device__ __forceinline__ void st_rel_cta(int *p, int v) {
     asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
-// {value, tag} record of another block: one 64-bit relaxed load.  No memory
-// clobber: the surrounding loads and stores may be scheduled around it (the
-// tag alone decides whether the value is the awaited one).
-__device__ __forceinline__ int2 ld_rec(const int2 *p) {
-    int2 r;
-    asm volatile("ld.relaxed.gpu.global.v2.s32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+// {value, tag} record of another block as one 64-bit word (value in the low
+// half, tag in the high half; an aligned 64-bit access is single-copy
+// atomic, so a matching tag carries its value).  No memory clobber: the
+// surrounding loads and stores may be scheduled around it (the tag alone
+// decides whether the value is the awaited one).
+__device__ __forceinline__ unsigned long long ld_rec(const int2 *p) {
+    unsigned long long r;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r) : "l"(p));
     return r;
 }
+__device__ __forceinline__ unsigned long long ld_rec_weak(const int2 *p) {
+    return __ldcg(reinterpret_cast<const unsigned long long *>(p));
+}
 __device__ __forceinline__ void st_rec(int2 *p, int v, int tag) {
-    asm volatile("st.relaxed.gpu.global.v2.s32 [%0], {%1, %2};" ::"l"(p), "r"(v), "r"(tag));
+    const unsigned long long w = (unsigned long long)(unsigned)v | ((unsigned long long)(unsigned)tag << 32);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w));
 }
 __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p) {
     unsigned v;
@@ -90,13 +98,8 @@ __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p) {
 __device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// L2 prefetch of the 16-byte aligned part of [p, p + bytes)
-__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
-    const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
-    const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
-    if (hi > lo)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
-}
+// L2 prefetch of the cache line holding p (inside an allocation)
+__device__ __forceinline__ void prefetch_line_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 // barrier of the TW warps of team tm (named barriers 1..NT)
 __device__ __forceinline__ void team_sync(int tm, int TW) {
     if (TW == 1) {
@@ -130,18 +133,92 @@ __device__ __forceinline__ unsigned long long warp_min_key(unsigned long long k)
 
 // Truncated-L1 distance transform of one line of L labels held by one lane,
 // in place: the backward sweep (Eq. L_dec5), then the forward sweep
-// (Eq. L_dec3) over its result, then the clip.
+// (Eq. L_dec3) over its result, then the clip.  A step min(h[i], h[i -/+ 1]
+// + lambda) is one add-min instruction.
 template <int L>
-__device__ __forceinline__ void line_sweeps(int (&h)[L], int lam, int clip) {
+__device__ __forceinline__ void line_sweeps1(int (&h)[L], int lam, int clip) {
 #pragma unroll
-    for (int i = L - 2; i >= 0; --i) h[i] = min(h[i], h[i + 1] + lam);
+    for (int i = L - 2; i >= 0; --i) h[i] = __viaddmin_s32(h[i + 1], lam, h[i]);
 #pragma unroll
-    for (int i = 1; i < L; ++i) h[i] = min(h[i], h[i - 1] + lam);
+    for (int i = 1; i < L; ++i) h[i] = __viaddmin_s32(h[i - 1], lam, h[i]);
 #pragma unroll
     for (int i = 0; i < L; ++i) h[i] = min(h[i], clip);
 }
 
 }  // namespace line
+
+// Phase A loads of one label column (axis-1 line) of one pixel: C, the old
+// messages m_c and m_d (global, coalesced across the lanes), m_a from xa and
+// m_b from xb (shared memory, the lane's own column; or m_b from the record
+// ring: RING), the messages this pixel received written to the message
+// arrays, and the two halved sums of Eq. DP_2D_base: S_a into hv, S_b over
+// m_b in xb.  xa is only read, so the column can be loaded again when a
+// record was not there yet.  The global loads are issued in batches of CH
+// labels, one batch ahead of the arithmetic on the previous one.  VOL: record
+// loads as relaxed loads at GPU scope (the retry after a tag that did not
+// match); otherwise plain L2 loads, whose tags are checked the same way.
+// Returns whether every record tag matched.
+template <int LA, int LB, int P0, bool RING, bool VOL>
+__device__ __forceinline__ bool line_load(const int *__restrict__ Cp, const int *__restrict__ Mcp,
+                                          const int *__restrict__ Mdp, int *__restrict__ Map, int *__restrict__ Mbp,
+                                          const int2 *__restrict__ recp, const int *__restrict__ xa,
+                                          int *__restrict__ xb, const bool c_ok, const bool d_ok, const bool has_ma,
+                                          const bool mbox, const bool st_a, const bool st_b, const bool fin,
+                                          const int tag, const int q0, int (&hv)[LA], int &lmin_a, int &lmin_b,
+                                          unsigned long long &key) {
+    constexpr int CHmax = LA > 40 ? (RING ? 6 : 10) : (RING ? 8 : 13);
+    constexpr int NB = (LA + CHmax - 1) / CHmax;
+    constexpr int CH = (LA + NB - 1) / NB;  // equal batches
+    int cv[2][CH], mcv[2][CH], mdv[2][CH];
+    unsigned long long rv[2][RING ? CH : 1];
+    auto issue = [&](const int b, const int k) {
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int i = b * CH + j;
+            if (i < LA) {
+                const int o = i * LB;
+                cv[k][j] = __ldcg(Cp + o);
+                mcv[k][j] = c_ok ? __ldcg(Mcp + o) : 0;
+                mdv[k][j] = d_ok ? __ldcg(Mdp + o) : 0;
+                if constexpr (RING) rv[k][j] = VOL ? line::ld_rec(recp + o) : line::ld_rec_weak(recp + o);
+            }
+        }
+    };
+    bool ok = true;
+    issue(0, 0);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        if (b + 1 < NB) issue(b + 1, (b + 1) & 1);
+        const int k = b & 1;
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int i = b * CH + j;
+            if (i < LA) {
+                const int o = i * LB;  // label q = o + q0
+                const int c = cv[k][j], mc = mcv[k][j], md = mdv[k][j];
+                const int ma = has_ma ? xa[i * P0] : 0;
+                int mb = 0;
+                if constexpr (RING) {
+                    mb = (int)(unsigned)rv[k][j];
+                    ok = ok && (int)(unsigned)(rv[k][j] >> 32) == tag;
+                } else {
+                    if (mbox) mb = xb[i * P0];
+                }
+                // the messages this pixel received, into the message arrays
+                if (st_a) __stcs(Map + o, ma);
+                if (st_b) __stcs(Mbp + o, mb);
+                const int t = c + ma + mb, e = md - mc;
+                const int ha = floor_half(t + e), hb = floor_half(t - e);
+                if (fin) key = min(key, line::argmin_key(t + mc + md, o + q0));
+                hv[i] = ha;
+                xb[i * P0] = hb;
+                lmin_a = min(lmin_a, ha);
+                lmin_b = min(lmin_b, hb);
+            }
+        }
+    }
+    return ok;
+}
 
 // One row band of one scan pass (or paired sweep) for a label space of
 // LB x LA labels (axis 0: LB labels, contiguous; axis 1: LA labels).  Every
@@ -207,16 +284,22 @@ __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int
             const bool has_ma = xs > 0, nxt = xs + 1 < W;
             const bool c_ok = read_c && (incx ? x + 1 < W : x - 1 >= 0);
             int *const Xb = Xa + (1 + (s & 1)) * XS;  // this column's slot
-            // L2 prefetch of the inputs two columns ahead
-            if (tl == 0 && s + 2 < ncol) {
-                const int s2 = s + 2, h2 = s2 >= W ? 1 : 0, xs2 = s2 - h2 * W;
+            // L2 prefetch of the next column's inputs (C, m_c, m_d): every lane of
+            // the team one 128-byte line per vector and step
+            if (s + 1 < ncol) {
+                const int s2 = s + 1, h2 = s2 >= W ? 1 : 0, xs2 = s2 - h2 * W;
                 const bool incx2 = ((A.pass + h2) & 1) == 0;
                 const int x2 = incx2 ? xs2 : W - 1 - xs2;
                 const size_t p2 = (size_t)y * W + x2;
                 const bool rc2 = (h2 ? A.read_c2 : A.read_c) && (incx2 ? x2 + 1 < W : x2 - 1 >= 0);
-                prefetch_l2(A.C + p2 * Q, (size_t)Q * 4);
-                if (rc2) prefetch_l2((incx2 ? A.M[1] : A.M[0]) + p2 * Qm, (size_t)Q * 4);
-                if (d_ok) prefetch_l2(Md + p2 * Qm, (size_t)Q * 4);
+                const int *const pc = A.C + p2 * Q;
+                const int *const pm = (incx2 ? A.M[1] : A.M[0]) + p2 * Qm;
+                const int *const pd = Md + p2 * Qm;
+                for (int o = tl * 32; o < Q; o += 32 * 32 * TW) {
+                    prefetch_line_l2(pc + o);
+                    if (rc2) prefetch_line_l2(pm + o);
+                    if (d_ok) prefetch_line_l2(pd + o);
+                }
             }
             // prior of the two outgoing edges (per-edge multipliers, or 1)
             int lam_a = A.lam, lam_b = A.lam, cap_a = A.capv, cap_b = A.capv;
@@ -271,49 +354,25 @@ __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int
             int lmin_a = kBig, lmin_b = kBig;
             int hv[LA];
             const int tag = tag_in0 + s / ring;
-            auto load_column = [&]() -> bool {
-                bool ok = true;
+            const bool st_a = write_a && has_ma, st_b = write_b && r > 0;
+            const int2 *const recp = from_ring ? ll_in + (size_t)(s % ring) * Qm + tl : nullptr;
+            auto load_column = [&](auto vol) -> bool {
                 lmin_a = kBig;
                 lmin_b = kBig;
                 key = ~0ull;
                 if (!colA) return true;
-                const int *const Cp = A.C + pix * Q + tl;
-                const int *const Mcp = Mc + pix * Qm + tl;
-                const int *const Mdp = Md + pix * Qm + tl;
-                int *const Map = Ma + pix * Qm + tl;
-                int *const Mbp = Mb + pix * Qm + tl;
-                const int2 *const recp = from_ring ? ll_in + (size_t)(s % ring) * Qm + tl : nullptr;
-                const bool st_a = write_a && has_ma, st_b = write_b && r > 0;
-#pragma unroll
-                for (int i = 0; i < LA; ++i) {
-                    const int o = i * LB;  // label q = o + tl
-                    const int c = __ldcg(Cp + o);
-                    const int mc = c_ok ? __ldcg(Mcp + o) : 0;
-                    const int md = d_ok ? __ldcg(Mdp + o) : 0;
-                    const int ma = has_ma ? Xa[i * P0 + tl] : 0;
-                    int mb = 0;
-                    if (from_mbox) {
-                        mb = Xb[i * P0 + tl];
-                    } else if (from_ring) {
-                        const int2 v = ld_rec(recp + o);
-                        mb = v.x;
-                        ok = ok && v.y == tag;
-                    }
-                    // the messages this pixel received, into the message arrays
-                    if (st_a) __stcs(Map + o, ma);
-                    if (st_b) __stcs(Mbp + o, mb);
-                    const int t = c + ma + mb, e = md - mc;
-                    const int ha = floor_half(t + e), hb = floor_half(t - e);
-                    if (fin) key = min(key, argmin_key(t + mc + md, o + tl));
-                    hv[i] = ha;
-                    Xb[i * P0 + tl] = hb;
-                    lmin_a = min(lmin_a, ha);
-                    lmin_b = min(lmin_b, hb);
-                }
-                return ok;
+                if (from_ring)
+                    return line_load<LA, LB, P0, true, decltype(vol)::value>(
+                        A.C + pix * Q + tl, Mc + pix * Qm + tl, Md + pix * Qm + tl, Ma + pix * Qm + tl,
+                        Mb + pix * Qm + tl, recp, Xa + tl, Xb + tl, c_ok, d_ok, has_ma, false, st_a, st_b, fin, tag,
+                        tl, hv, lmin_a, lmin_b, key);
+                return line_load<LA, LB, P0, false, false>(
+                    A.C + pix * Q + tl, Mc + pix * Qm + tl, Md + pix * Qm + tl, Ma + pix * Qm + tl,
+                    Mb + pix * Qm + tl, nullptr, Xa + tl, Xb + tl, c_ok, d_ok, has_ma, from_mbox, st_a, st_b, fin,
+                    tag, tl, hv, lmin_a, lmin_b, key);
             };
             if (!bad) {
-                bool ok = load_column();
+                bool ok = load_column(std::false_type());
                 if (from_ring) {
                     // a record whose tag does not match yet: wait and load the column again
                     spins = 0;
@@ -324,19 +383,19 @@ __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int
                             break;
                         }
                         __nanosleep(64);
-                        ok = load_column();
+                        ok = load_column(std::true_type());
                     }
                     // the records of this column have been read: the producer may reuse the slot
                     if (!bad && lane == 0) st_relaxed_gpu(cons_in, (unsigned)(s + 1));
                 }
             }
             if (!bad && colA) {
-                line_sweeps<LA>(hv, lam_a, per_axis ? lmin_a + cap_a : kBig);
+                line_sweeps1<LA>(hv, lam_a, per_axis ? lmin_a + cap_a : kBig);
 #pragma unroll
                 for (int i = 0; i < LA; ++i) Xa[i * P0 + tl] = hv[i];
 #pragma unroll
                 for (int i = 0; i < LA; ++i) hv[i] = Xb[i * P0 + tl];
-                line_sweeps<LA>(hv, lam_b, per_axis ? lmin_b + cap_b : kBig);
+                line_sweeps1<LA>(hv, lam_b, per_axis ? lmin_b + cap_b : kBig);
 #pragma unroll
                 for (int i = 0; i < LA; ++i) Xb[i * P0 + tl] = hv[i];
             }
@@ -373,27 +432,27 @@ __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int
                         ga = min(ga, ctl[8 + w]);
                         gb = min(gb, ctl[12 + w]);
                     }
+                int *const ra = Xa + tl * P0;
+                int *const rb = Xb + tl * P0;
                 int gv[LB];
-                int* const ra = Xa + tl * P0;
                 int lm = kBig;
 #pragma unroll
                 for (int j = 0; j < LB; ++j) {
                     gv[j] = ra[j];
                     lm = min(lm, gv[j]);
                 }
-                line_sweeps<LB>(gv, lam_a, (per_axis ? lm : ga) + cap_a);
+                line_sweeps1<LB>(gv, lam_a, (per_axis ? lm : ga) + cap_a);
                 if (nxt) {  // m_a of the next column of the row
 #pragma unroll
                     for (int j = 0; j < LB; ++j) ra[j] = gv[j];
                 }
-                int *const rb = Xb + tl * P0;
                 lm = kBig;
 #pragma unroll
                 for (int j = 0; j < LB; ++j) {
                     gv[j] = rb[j];
                     lm = min(lm, gv[j]);
                 }
-                line_sweeps<LB>(gv, lam_b, (per_axis ? lm : gb) + cap_b);
+                line_sweeps1<LB>(gv, lam_b, (per_axis ? lm : gb) + cap_b);
                 if (to_mbox) {  // m_b of this column of the row below
                     int *const nb = nx_slots + (s & 1) * XS + tl * P0;
 #pragma unroll

@@ -25,9 +25,12 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+LINE = 4  # general_kernel value: the line kernel wherever it is built
+
+
 @pytest.fixture(autouse=True)
 def reset_tuning(edp_lib):
-    edp_lib.set_tuning(0, 0, 0)
+    edp_lib.set_tuning(0, 0, LINE)
     edp_lib.set_pass_pairs(edp_lib.PAIRS_AUTO)
     yield
     edp_lib.set_tuning(0, 0, 0)
@@ -63,7 +66,7 @@ def test_line_kernel_rows_per_block_and_schedule(edp_lib, rows, pairs, Q):
     C = rng.integers(0, 21, size=(H, W, n)).astype(np.int32)
     prior = {"lam": 9, "g": 3, "l1": 1, "mode": "per_axis"}
     want = oracle.edp(C, sp(Q), prior, iters=3, tier=1)
-    edp_lib.set_tuning(rows, 0, 0)
+    edp_lib.set_tuning(rows, 0, LINE)
     edp_lib.set_pass_pairs(pairs)
     got = edp_lib.solve(dev(C), sp(Q), prior, iters=3).cpu().numpy()
     assert edp_lib.last_pass_kernel() == "edp_pass_line_kernel"
@@ -111,7 +114,7 @@ def test_motion_65x65_480_rows(edp_lib, kernel):
     w = synth.workload_motion_640x480(W=8, H=480)
     C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
     want = oracle.edp(C, w["space"], w["prior"], iters=1, tier=1)
-    edp_lib.set_tuning(0, 0, 0 if kernel == "line" else 3)
+    edp_lib.set_tuning(0, 0, LINE if kernel == "line" else 3)
     gC = dev(C)
     got = edp_lib.solve(gC, w["space"], w["prior"], iters=1)
     if kernel == "line":
@@ -138,6 +141,7 @@ def test_motion_640x480_full_size(edp_lib):
     # rows 0..39 look at most 32 rows down: a 72-row crop has the same costs there
     C = oracle.cost_volume(w["I0"][:72], w["I1"][:72], None, space, w["l2"], w["cmax"])
     assert np.array_equal(gC[:40].cpu().numpy(), C[:40])
+    edp_lib.set_tuning(0, 0, 0)  # the default choice for this shape
     lab_line = edp_lib.solve(gC, space, prior, iters=1)
     assert edp_lib.last_pass_kernel() == "edp_pass_line_kernel"
     edp_lib.set_tuning(0, 0, 3)

@@ -15,18 +15,22 @@ pytestmark = pytest.mark.gpu
 
 
 def _case(kind):
+    """Workload and the general_kernel tuning value that selects the kernel."""
     if kind == "one_axis":  # warp-per-row kernel, 8 rows per band
-        return synth.workload_scanline_64x48()
-    if kind == "two_axis_33":  # two-axis pass kernel, 33 x 33 labels
-        return synth.workload_motion_320x240(W=24, H=40)
-    return synth.workload_motion_640x480(W=20, H=36, vmax=4)  # two-axis, 9 x 9 labels
+        return synth.workload_scanline_64x48(), 0
+    if kind == "multi_axis_33":  # multi-axis kernel, 33 x 33 labels
+        return synth.workload_motion_320x240(W=24, H=40), 3
+    if kind == "line_33":  # two-axis line kernel, 33 x 33 labels
+        return synth.workload_motion_320x240(W=24, H=40), 4
+    return synth.workload_motion_640x480(W=20, H=36, vmax=4), 0  # multi-axis, 9 x 9 labels
 
 
-@pytest.mark.parametrize("kind", ["one_axis", "two_axis_33", "two_axis_9"])
+@pytest.mark.parametrize("kind", ["one_axis", "multi_axis_33", "line_33", "multi_axis_9"])
 @pytest.mark.parametrize("pairs", [0, 1])
 def test_timeout_sets_status_and_next_solve_is_exact(edp_lib, kind, pairs):
     edp = edp_lib
-    w = _case(kind)
+    w, general = _case(kind)
+    edp.set_tuning(0, 0, general)
     I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
     C = edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"])
     H, W, _ = C.shape
@@ -45,6 +49,9 @@ def test_timeout_sets_status_and_next_solve_is_exact(edp_lib, kind, pairs):
         edp.set_spin_limit(0)
         edp.set_pass_pairs(edp.PAIRS_AUTO)
     # the context is usable and the workspace is reset by the next solve
-    edp.solve(C, w["space"], w["prior"], iters=1, ws=ws, labels=lab)
-    assert edp.get_device_status(ws) == 0
-    assert np.array_equal(lab.cpu().numpy(), want)
+    try:
+        edp.solve(C, w["space"], w["prior"], iters=1, ws=ws, labels=lab)
+        assert edp.get_device_status(ws) == 0
+        assert np.array_equal(lab.cpu().numpy(), want)
+    finally:
+        edp.set_tuning(0, 0, 0)
