@@ -158,6 +158,7 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "edp_pass_r1_kernel": ("pass_r1.cuh", "edp_pass_r1.cu", "common.cuh"),
     "edp_pass_team_kernel": ("pass_team.cuh", "edp_pass_team.cu", "common.cuh"),
+    "edp_pass_line_kernel": ("pass_line.cuh", "edp_pass_line.cu", "common.cuh"),
 }
 
 
@@ -186,7 +187,8 @@ def profiled_traffic(workload: str, kernel: str):
         return None
     d = json.load(open(p))
     e = d.get(workload)
-    if not e or e.get("kernel") != kernel or e.get("source_hash") != kernel_source_hash(kernel):
+    if not e or kernel not in KERNEL_SOURCES or e.get("kernel") != kernel or \
+            e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return float(e["dram_bytes_per_launch"])
 

@@ -177,6 +177,7 @@ int ptr_bytes_for(int Q) { return Q <= 256 ? 1 : (Q <= 65536 ? 2 : 4); }
 // kernel: a ring of team_ring(W) columns, bands of one row or more.
 constexpr int kMinRowsR1 = 2;
 constexpr int kResidentMin = 128;  // resident blocks assumed when sizing the record ring
+constexpr int kLineRingResident = 4;  // record ring columns of the line kernel when every band is resident
 int msg_stride(int Q) { return (Q + 3) / 4 * 4; }
 // columns of the record ring: the first of K resident bands may run
 // (K - 1) * ring columns ahead of the last, which must cover the row
@@ -403,10 +404,18 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         a.g = p->g;
         a.T = TW;
         a.NT = NT;
-        a.ring = team_ring(2 * W, kResidentMin);
         a.nbands = (H + NT - 1) / NT;
+        // record ring: when every band is resident, consecutive bands run about
+        // one column apart, so a short ring suffices and stays in L2; otherwise
+        // the depth that lets the first resident band finish its row
+        {
+            const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, 32 * TW * NT, pass_line_smem(NT, P->Q0, P->Q1));
+            const bool all_resident = a.nbands <= std::max(1, occ) * sms;
+            a.ring = all_resident ? std::min(kLineRingResident, team_ring(2 * W, kResidentMin))
+                                  : team_ring(2 * W, kResidentMin);
+        }
         a.spin_limit = g_spin_limit;
-        P->laps = (W + a.ring - 1) / a.ring;
+        P->laps = (2 * W + a.ring - 1) / a.ring;
         P->nbands = a.nbands;
         P->threads = 32 * TW * NT;
         P->em = 0;

@@ -177,9 +177,10 @@ __device__ __forceinline__ bool line_load(const int *__restrict__ Cp, const int 
             const int i = b * CH + j;
             if (i < LA) {
                 const int o = i * LB;
-                cv[k][j] = __ldcg(Cp + o);
-                mcv[k][j] = c_ok ? __ldcg(Mcp + o) : 0;
-                mdv[k][j] = d_ok ? __ldcg(Mdp + o) : 0;
+                // read once per pass: evict first, so the hand-off records stay in L2
+                cv[k][j] = __ldcs(Cp + o);
+                mcv[k][j] = c_ok ? __ldcs(Mcp + o) : 0;
+                mdv[k][j] = d_ok ? __ldcs(Mdp + o) : 0;
                 if constexpr (RING) rv[k][j] = VOL ? line::ld_rec(recp + o) : line::ld_rec_weak(recp + o);
             }
         }

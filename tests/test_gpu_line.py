@@ -153,3 +153,24 @@ def test_motion_640x480_full_size(edp_lib):
     torch.cuda.empty_cache()
     Cfull = oracle.cost_volume(w["I0"], w["I1"], None, space, w["l2"], w["cmax"])
     assert e_gpu == oracle.energy(Cfull, lab_line.cpu().numpy(), space, prior)
+
+
+def test_line_kernel_repeatable_320x240(edp_lib):
+    """Repeated solves of the full 320x240 motion workload (33 x 33 labels)
+    on the line kernel, with one and two rows per block (every row, or every
+    second row, gets its messages from the block above through the record
+    ring) under both pass schedules: every run equals the oracle.  Hand-off
+    timing differs from run to run, so a protocol hazard would show as a
+    difference here."""
+    w = synth.workload_motion_320x240()
+    C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+    want = oracle.edp(C, w["space"], w["prior"], iters=1, tier=1)
+    gC = dev(C)
+    for rows in (1, 2):
+        for pairs in (0, 1):
+            edp_lib.set_tuning(rows, 0, LINE)
+            edp_lib.set_pass_pairs(pairs)
+            for _ in range(3):
+                got = edp_lib.solve(gC, w["space"], w["prior"], iters=1).cpu().numpy()
+                assert edp_lib.last_pass_kernel() == "edp_pass_line_kernel"
+                assert np.array_equal(got, want), (rows, pairs)
