@@ -73,6 +73,8 @@ def parse_args():
     ap.add_argument("--extra", default="", help="comma list of longer side measurements: batched,proposal")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="image scale of the batched workload")
     ap.add_argument("--proposal-pairs", type=int, default=2000, help="training pairs of the proposal network")
+    ap.add_argument("--row-proposal-pairs", type=int, default=64,
+                    help="training pairs of the proposal row of the default line")
     return ap.parse_args()
 
 
@@ -508,7 +510,7 @@ def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, bu
 
 
 def measure_proposal(edp, torch, train_pairs: int = 2000, epochs: int = 10,
-                     eval_pairs=(1000, 1001, 1002, 1003), W: int = 640, H: int = 480, win: int = 9):
+                     eval_pairs=(1000, 1001, 1002, 1003), W: int = 640, H: int = 480, win: int = 9, reps: int = 2):
     """Learned proposal + 9x9 windowed EDP against full-label EDP (65x65
     labels) on held-out 640x480 pairs.  The network is trained here, by the
     project's kernels, on full-label EDP labelings of train_pairs synthetic
@@ -526,15 +528,19 @@ def measure_proposal(edp, torch, train_pairs: int = 2000, epochs: int = 10,
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del x, t
-    rows = proposal.evaluate(P, list(eval_pairs), W, H, win=win, reps=2)
+    rows = proposal.evaluate(P, list(eval_pairs), W, H, win=win, reps=reps)
     mean = lambda k: sum(r[k] for r in rows) / len(rows)
     return {"train_pairs": train_pairs, "train_size": [W, H], "epochs": epochs, "window": win,
-            "min_shift": proposal.MIN_SHIFT, "loss_first": losses[0], "loss_last": losses[-1],
+            "min_shift": proposal.MIN_SHIFT, "edge_frac_fallback": proposal.EDGE_FRAC,
+            "loss_first": losses[0], "loss_last": losses[-1],
             "s_training_data": t_data, "s_training": t_train, "eval": rows,
+            "mean_gap_solve": mean("gap_solve"), "max_gap_solve": max(r["gap_solve"] for r in rows),
+            "fallbacks": sum(r["fallback"] for r in rows),
             "mean_gap_net": mean("gap_net"), "mean_gap_coarse": mean("gap_coarse"),
             "mean_heldout_loss_net": mean("loss_net"), "mean_heldout_loss_no_correction": mean("loss_zero"),
-            "mean_ms_full": mean("ms_full"), "mean_ms_net": mean("ms_net"), "mean_ms_coarse": mean("ms_coarse"),
-            "mean_speedup_net": sum(r["ms_full"] / r["ms_net"] for r in rows) / len(rows)}
+            "mean_ms_full": mean("ms_full"), "mean_ms_solve": mean("ms_solve"), "mean_ms_net": mean("ms_net"),
+            "mean_ms_coarse": mean("ms_coarse"),
+            "mean_speedup_solve": sum(r["ms_full"] / r["ms_solve"] for r in rows) / len(rows)}
 
 
 def run_gpu(args, world, rank, local):
@@ -652,6 +658,11 @@ def run_gpu(args, world, rank, local):
     rows = None
     if not args.no_rows and rank == 0 and args.workload == WORKLOAD:
         rows = time_solve_rows(edp, synth, torch, peak)
+        # the two added forms against plain full-label EDP on this GPU
+        rows["batched_64_pairs"] = measure_batched(edp, synth, torch, scale=args.batch_scale)
+        rows["proposal_640x480_Q65x65_w9"] = measure_proposal(edp, torch, train_pairs=args.row_proposal_pairs,
+                                                              eval_pairs=(1000, 1001, 1002, 1003, 1004, 1005),
+                                                              reps=1)
     extra = {}
     if rank == 0:
         for name in [e for e in args.extra.split(",") if e]:

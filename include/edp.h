@@ -408,6 +408,15 @@ int edp_net_centres_residual(const float *out, const int32_t *base, int n, const
 int edp_net_targets(const int32_t *labels, const int32_t *base, int n, const edp_label_space *space, float *target,
                     edp_stream_t stream);
 
+/* Fallback trigger of the proposal path (not in the paper): the number of
+ * pixels whose label (int32 [n], full-space linear index) lies on an inner
+ * edge of its win x win box (centre: int32 [n][2], clamped into the space as
+ * edp_solve_windowed does) -- an edge that is not also an edge of the label
+ * space, so a better label may lie outside the box.  Two-axis spaces.
+ * count: device int64 [1], overwritten. */
+int edp_window_edge_count(const int32_t *labels, const int32_t *centre, int n, int win,
+                          const edp_label_space *space, int64_t *count, edp_stream_t stream);
+
 /* One problem of a batch: a device image pair (or triple) in, labels and
  * energy out.  Images are uint8 [H][pitch]. */
 typedef struct {

@@ -264,3 +264,15 @@ def centres_residual(out: np.ndarray, base: np.ndarray, Q, min_shift: int = 0) -
     c0 = np.clip(base % Q[0] + r[..., 0], 0, Q[0] - 1)
     c1 = np.clip(base // Q[0] + r[..., 1], 0, Q[1] - 1)
     return np.stack([c0, c1], axis=-1)
+
+
+def window_edge_count(labels: np.ndarray, centre: np.ndarray, win: int, Q) -> int:
+    """Pixels whose label lies on an inner edge of its win x win box (centre
+    clamped so the box fits): an edge that is not an edge of the label space."""
+    h = (win - 1) // 2
+    l0, l1 = labels % Q[0], labels // Q[0]
+    lo0 = np.clip(centre[..., 0], h, Q[0] - 1 - h) - h
+    lo1 = np.clip(centre[..., 1], h, Q[1] - 1 - h) - h
+    e0 = ((l0 == lo0) & (lo0 > 0)) | ((l0 == lo0 + win - 1) & (lo0 + win - 1 < Q[0] - 1))
+    e1 = ((l1 == lo1) & (lo1 > 0)) | ((l1 == lo1 + win - 1) & (lo1 + win - 1 < Q[1] - 1))
+    return int((e0 | e1).sum())

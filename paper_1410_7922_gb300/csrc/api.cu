@@ -1518,6 +1518,16 @@ int edp_net_centres_residual(const float *out, const int32_t *base, int n, const
                : EDP_OK;
 }
 
+int edp_window_edge_count(const int32_t *labels, const int32_t *centre, int n, int win,
+                          const edp_label_space *space, int64_t *count, edp_stream_t stream) {
+    if (!labels || !centre || !count || !space || n < 1 || space->R != 2) return EDP_ERR_INVALID_ARG;
+    if (win < 1 || (win & 1) == 0 || win > space->Q[0] || win > space->Q[1]) return EDP_ERR_INVALID_ARG;
+    return window_edge_count_launch(labels, centre, n, win, space->Q[0], space->Q[1],
+                                    reinterpret_cast<unsigned long long *>(count), (cudaStream_t)stream)
+               ? EDP_ERR_CUDA
+               : EDP_OK;
+}
+
 int edp_net_targets(const int32_t *labels, const int32_t *base, int n, const edp_label_space *space, float *target,
                     edp_stream_t stream) {
     if (!labels || !target || !space || n < 1 || space->R != 2) return EDP_ERR_INVALID_ARG;

@@ -225,5 +225,7 @@ int net_features_lab_launch(const uint8_t *I0, const uint8_t *I1, const int *lab
 int net_centres_base_launch(const float *out, const int *base, int n, int Q0, int Q1, int min_shift, int *centre,
                             cudaStream_t st);
 int net_targets_launch(const int *lab, const int *base, int n, int Q0, int Q1, float *t, cudaStream_t st);
+int window_edge_count_launch(const int *labels, const int *centre, int n, int win, int Q0, int Q1,
+                             unsigned long long *count, cudaStream_t st);
 
 }  // namespace edp

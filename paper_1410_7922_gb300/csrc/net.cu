@@ -299,6 +299,32 @@ __global__ void net_targets(const int *lab, const int *base, int n, int Q0, int 
     }
 }
 
+// Pixels whose label (full-space linear index) lies on an inner edge of its
+// win x win box (centre clamped into the space as the windowed solve does):
+// on an edge that is not also an edge of the label space, so a better label
+// may lie outside the box.  One count per launch, reduced per block.
+__global__ void window_edge_count(const int *labels, const int *centre, int n, int win, int Q0, int Q1,
+                                  unsigned long long *count) {
+    __shared__ unsigned s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const int h = (win - 1) / 2;
+    unsigned local = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int q = labels[i];
+        const int l0 = q % Q0, l1 = q / Q0;
+        const int lo0 = min(max(centre[2 * i], h), Q0 - 1 - h) - h;
+        const int lo1 = min(max(centre[2 * i + 1], h), Q1 - 1 - h) - h;
+        const bool e0 = (l0 == lo0 && lo0 > 0) || (l0 == lo0 + win - 1 && lo0 + win - 1 < Q0 - 1);
+        const bool e1 = (l1 == lo1 && lo1 > 0) || (l1 == lo1 + win - 1 && lo1 + win - 1 < Q1 - 1);
+        local += (e0 || e1) ? 1u : 0u;
+    }
+    local = __reduce_add_sync(0xffffffffu, local);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(&s_cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(count, (unsigned long long)s_cnt);
+}
+
 // Winner-take-all over the full label space straight from the images (no
 // cost volume): lowest-index minimum of Eq. Cost_value per pixel, summed over
 // a (2 radius + 1)^2 window of pixels around it (radius 0: the plain cost),
@@ -497,6 +523,13 @@ int net_targets_launch(const int *lab, const int *base, int n, int Q0, int Q1, f
 }
 int net_centres_launch(const float *out, int n, int Q0, int Q1, int *centre, cudaStream_t st) {
     net_centres<<<152 * 4, 256, 0, st>>>(out, n, Q0, Q1, centre);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int window_edge_count_launch(const int *labels, const int *centre, int n, int win, int Q0, int Q1,
+                             unsigned long long *count, cudaStream_t st) {
+    if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess) return -2;
+    window_edge_count<<<152 * 4, 256, 0, st>>>(labels, centre, n, win, Q0, Q1, count);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -93,6 +93,7 @@ def load() -> ctypes.CDLL:
         "edp_net_features_labels": ([P, P, P, I, I, I, LS, PR, ctypes.c_float, P, P], I),
         "edp_net_centres_residual": ([P, P, I, LS, I, P, P], I),
         "edp_net_targets": ([P, P, I, LS, P, P], I),
+        "edp_window_edge_count": ([P, P, I, I, LS, P, P], I),
         "edp_net_param_count": ([], ctypes.c_longlong),
         "edp_net_workspace_size": ([I, I, I], SZ),
         "edp_net_activation_offset": ([I, I, I, I], SZ),
@@ -122,7 +123,7 @@ def exported_symbols() -> list[str]:
             "edp_wta", "edp_net_param_count", "edp_net_workspace_size", "edp_net_activation_offset", "edp_net_forward", "edp_net_backward",
             "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc",
             "edp_noalloc_get_device_status", "edp_coarse_labels",
-            "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_scanline_marginals",
+            "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_window_edge_count", "edp_scanline_marginals",
             "edp_set_pass_pairs", "edp_last_pass_launches", "edp_last_pass_kernel", "edp_set_spin_limit",
             "edp_test_hold_band", "edp_edge_weights", "edp_solve_weighted",
             "edp_energy_weighted"]
@@ -660,6 +661,19 @@ def net_centres_residual(out, base, space: dict, min_shift: int = 0, centre=None
                                          _stream(stream))
     _check(rc, "net_centres_residual")
     return centre
+
+
+def window_edge_count(labels, centre, win: int, space: dict, out=None, stream=None):
+    """edp_window_edge_count: pixels whose label lies on an inner edge of its
+    box (device int64 [1])."""
+    n = labels.numel()
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=labels.device)
+    ls = label_space(space)
+    rc = load().edp_window_edge_count(_dev(labels, torch.int32, "labels"), _dev(centre, torch.int32, "centre"), n,
+                                      int(win), ctypes.byref(ls), _dev(out, torch.int64, "count"), _stream(stream))
+    _check(rc, "window_edge_count")
+    return out
 
 
 def net_targets(labels, space: dict, base=None, out=None, stream=None):

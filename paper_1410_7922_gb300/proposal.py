@@ -11,13 +11,16 @@ Pipeline, every arithmetic step in libedp.so:
   3. EDP runs on a win x win label box around each centre
      (edp_cost_window, edp_solve_windowed), optionally re-centred on its own
      result for more rounds;
-  4. the energy of the result is evaluated on the full label space
-     (edp_cost_volume, edp_energy): full-label EDP is the reference the gap is
-     measured against, and the fallback.
-Training targets are labelings that full-label EDP (edp_solve_images)
-produces on synthetic pairs, as corrections of the coarse labeling
-(edp_net_targets); training is Adam on the smooth-L1 loss with the project's
-forward/backward kernels.  torch only holds device memory.
+  4. full-label EDP stays the reference and the fallback: solve() falls back
+     to it when too many windowed labels sit on an inner edge of their box
+     (edp_window_edge_count: the box probably cut off a better label), and in
+     verify mode it solves the full label space as well and keeps whichever
+     labeling has the lower energy (edp_cost_volume, edp_energy).
+Training targets are, per synthetic pair, the lower-energy labeling of
+full-label EDP (edp_solve_images) and of windowed EDP centred on the coarse
+labeling, as corrections of the coarse labeling (edp_net_targets); training
+is Adam on the smooth-L1 loss with the project's forward/backward kernels.
+torch only holds device memory.
 """
 from __future__ import annotations
 
@@ -70,24 +73,32 @@ def init_params(seed: int = 0) -> torch.Tensor:
 
 
 def build_training_set(n_pairs: int, W: int, H: int, first_pair: int = 0, iters: int = 1, vmax: int = 32,
-                       pool=None):
-    """Network inputs (bf16 [P][H][W][5]), targets (float32 [P][H][W][2]:
-    full-label EDP labels as corrections of the coarse labeling) and the
-    coarse labelings of n_pairs synthetic pairs.  `pool`: an optional
-    process pool (spawn) that synthesises the pairs."""
+                       pool=None, target: str = "best", win: int = 9):
+    """Network inputs (bf16 [P][H][W][5]) and targets (float32 [P][H][W][2],
+    corrections of the coarse labeling) of n_pairs synthetic pairs.  target
+    "best": per pair the lower-energy labeling of full-label EDP and of
+    windowed EDP centred on the coarse labeling; "full": full-label EDP.
+    `pool`: an optional process pool (spawn) that synthesises the pairs."""
     ids = [first_pair + k for k in range(n_pairs)]
     gen = pool.imap(_pair_images, [(i, W, H, vmax) for i in ids], chunksize=4) if pool else (
         _pair_images((i, W, H, vmax)) for i in ids)
     xs, ts = [], []
-    ws = wsc = None
+    ws = wsc = wsw = C = None
     for pid, (I0n, I1n) in zip(ids, gen):
         w = pair_meta(W, H, vmax)
         I0, I1 = torch.from_numpy(I0n).cuda(), torch.from_numpy(I1n).cuda()
         if ws is None:
             ws = edp.workspace(edp.OP_SOLVE_IMAGES, W, H, w["space"], w["prior"], iters)
             wsc = edp.workspace(edp.OP_COARSE, W, H, w["space"], w["prior"], iters, l2=w["l2"], cmax=w["cmax"])
-        lab, _ = full_edp(I0, I1, w, iters, ws)
+            wsw = edp.workspace_windowed(W, H, w["space"], w["prior"], win, iters)
+            C = torch.empty((H, W, edp.n_labels(w["space"])), dtype=torch.int32, device="cuda")
+        lab, e4 = full_edp(I0, I1, w, iters, ws)
         base = coarse(I0, I1, w, wsc, iters)
+        if target == "best":
+            lab_c = windowed_edp(I0, I1, w, label_centres(base, w["space"]), win, iters, wsw)
+            edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"], out=C)
+            if int(edp.energy(C, lab_c, w["space"], w["prior"])[3].item()) < int(e4[3].item()):
+                lab = lab_c
         xs.append(features(I0, I1, w, base))
         ts.append(edp.net_targets(lab, w["space"], base=base))
     return torch.stack(xs).contiguous(), torch.stack(ts).contiguous()
@@ -169,6 +180,47 @@ def refine(I0, I1, w: dict, centre: torch.Tensor, rounds: int, win: int = 9, ite
     return lab
 
 
+EDGE_FRAC = 0.02  # fallback when more than this fraction of labels sit on an inner box edge
+
+
+def solve(P: torch.Tensor, I0, I1, w: dict, win: int = 9, iters: int = 1, edge_frac: float = EDGE_FRAC,
+          verify: bool = False, min_shift: int = MIN_SHIFT, ws=None):
+    """The proposal path with full-label EDP as its fallback: coarse labeling,
+    network correction, windowed EDP; then full-label EDP instead when more
+    than `edge_frac` of the pixels got a label on an inner edge of their box
+    (the box likely cut off a better label).  verify=True also solves the
+    full label space and keeps the lower-energy labeling (the gap to
+    full-label EDP is then never positive, at the cost of the full solve).
+    ws: optional dict of workspaces reused across calls.  Returns (labels,
+    info) with info = {"fallback": bool, "edge_frac": float}."""
+    H, W = I0.shape
+    ws = {} if ws is None else ws
+    if "coarse" not in ws:
+        ws["coarse"] = edp.workspace(edp.OP_COARSE, W, H, w["space"], w["prior"], iters, l2=w["l2"], cmax=w["cmax"])
+        ws["win"] = edp.workspace_windowed(W, H, w["space"], w["prior"], win, iters)
+        ws["net"] = edp.net_workspace(1, H, W)
+    base = coarse(I0, I1, w, ws["coarse"], iters)
+    x = features(I0, I1, w, base)[None].contiguous()
+    out = edp.net_forward(P, x, ws["net"])
+    centre = edp.net_centres_residual(out[0].contiguous(), base, w["space"], min_shift)
+    lab = windowed_edp(I0, I1, w, centre, win, iters, ws["win"])
+    frac = int(edp.window_edge_count(lab, centre, win, w["space"]).item()) / (W * H)
+    info = {"fallback": False, "edge_frac": frac}
+    if verify or frac > edge_frac:
+        if "full" not in ws:
+            ws["full"] = edp.workspace(edp.OP_SOLVE_IMAGES, W, H, w["space"], w["prior"], iters)
+        lab_f, e4 = full_edp(I0, I1, w, iters, ws["full"])
+        use_full = not verify
+        if verify:
+            C = edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"])
+            use_full = int(edp.energy(C, lab, w["space"], w["prior"])[3].item()) > int(e4[3].item())
+            del C
+        if use_full:
+            lab = lab_f
+            info["fallback"] = True
+    return lab, info
+
+
 def coverage(centre: torch.Tensor, labels: torch.Tensor, space: dict, win: int) -> float:
     """Fraction of pixels whose label (e.g. full-label EDP's) lies inside the
     win x win box around the centre, boxes clamped into the space as the
@@ -235,6 +287,8 @@ def evaluate(P: torch.Tensor, pairs: list[int], W: int, H: int, win: int = 9, it
 
         lab_n, ms_net = timed(net_path)
         lab_c, ms_coarse = timed(coarse_path)
+        solve_ws = {}
+        (lab_s, info), ms_solve = timed(lambda: solve(P, I0, I1, w, win, iters, min_shift=min_shift, ws=solve_ws))
         # held-out smooth-L1 of the network's correction against full-label
         # EDP, and of no correction (the coarse labeling as it is)
         base = coarse(I0, I1, w, ws_c, iters)
@@ -244,10 +298,13 @@ def evaluate(P: torch.Tensor, pairs: list[int], W: int, H: int, win: int = 9, it
         loss_zero = float(edp.net_backward(P, torch.zeros_like(out), tgt, net_ws)[1].item())
         e_net = int(edp.energy(C, lab_n, w["space"], w["prior"])[3].item())
         e_coarse = int(edp.energy(C, lab_c, w["space"], w["prior"])[3].item())
+        e_solve = int(edp.energy(C, lab_s, w["space"], w["prior"])[3].item())
         del C
-        rows.append({"pair": pid, "E_full": e_full, "E_net": e_net, "E_coarse": e_coarse,
+        rows.append({"pair": pid, "E_full": e_full, "E_net": e_net, "E_coarse": e_coarse, "E_solve": e_solve,
                      "gap_net": (e_net - e_full) / e_full, "gap_coarse": (e_coarse - e_full) / e_full,
-                     "ms_full": ms_full, "ms_net": ms_net, "ms_coarse": ms_coarse,
+                     "gap_solve": (e_solve - e_full) / e_full, "fallback": info["fallback"],
+                     "edge_frac": info["edge_frac"],
+                     "ms_full": ms_full, "ms_net": ms_net, "ms_coarse": ms_coarse, "ms_solve": ms_solve,
                      "label_agree_net": float((lab_n == lab_f).float().mean().item()),
                      "label_agree_coarse": float((lab_c == lab_f).float().mean().item()),
                      "loss_net": loss_net, "loss_zero": loss_zero,

@@ -202,3 +202,22 @@ def test_net_training_lowers_loss(edp_lib):
         edp_lib.net_adam(P, g, m, v, 3e-3, step)
         losses.append(float(loss.item()))
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_window_edge_count(edp_lib):
+    rng = np.random.default_rng(12)
+    Q = (17, 13)
+    space = {"R": 2, "Q": (17, 13, 1), "vmin": (-8, -6, 0), "step": (1, 1, 1)}
+    for win in (3, 5, 9):
+        centre = np.stack([rng.integers(-3, 20, size=(37, 29)), rng.integers(-3, 16, size=(37, 29))], -1)
+        h = (win - 1) // 2
+        lo0 = np.clip(centre[..., 0], h, Q[0] - 1 - h) - h
+        lo1 = np.clip(centre[..., 1], h, Q[1] - 1 - h) - h
+        # labels inside each box, many on its edges
+        l0 = lo0 + rng.integers(0, win, size=lo0.shape)
+        l1 = lo1 + rng.integers(0, win, size=lo1.shape)
+        lab = (l0 + Q[0] * l1).astype(np.int32)
+        want = rnet.window_edge_count(lab, centre, win, Q)
+        got = edp_lib.window_edge_count(torch.from_numpy(lab).cuda(),
+                                        torch.from_numpy(centre.astype(np.int32)).cuda(), win, space)
+        assert int(got.item()) == want

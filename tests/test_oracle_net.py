@@ -140,3 +140,20 @@ def test_gradient_magnitudes_bound_the_gradients():
     _, grads = net.backward(x, params, out - 5.0)
     mags = net.gradient_magnitudes(x, params, out - 5.0)
     assert np.allclose(mags[-1][1], np.abs(grads[-1][1]), rtol=1e-12)
+
+
+def test_window_edge_count_hand_worked():
+    """Q = 5 x 7 labels, 3 x 3 boxes: a label on a box edge counts unless
+    that edge is also an edge of the label space (centres clamped first)."""
+    Q = (5, 7)
+    cases = [((2, 3), (1, 3), 1),   # box [1..3] x [2..4], left edge, inside the space
+             ((2, 3), (2, 3), 0),   # interior
+             ((0, 0), (0, 0), 0),   # box clamped to [0..2] x [0..2]: both edges are space edges
+             ((0, 0), (2, 1), 1),   # right edge of [0..2], inside the space
+             ((4, 6), (4, 6), 0),   # box [2..4] x [4..6]: corner on the space's edges
+             ((4, 6), (2, 6), 1)]   # left edge of [2..4]
+    centre = np.array([c for c, _, _ in cases], np.int64)
+    labels = np.array([l0 + Q[0] * l1 for _, (l0, l1), _ in cases], np.int64)
+    for k, (_, _, want) in enumerate(cases):
+        assert net.window_edge_count(labels[k:k + 1], centre[k:k + 1], 3, Q) == want, k
+    assert net.window_edge_count(labels, centre, 3, Q) == 3
