@@ -486,6 +486,13 @@ def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, bu
 
     ms_per = timed(per_pair, reps=1)
     per_labels = [it["labels"].clone() for it in items]
+    # which problems get launches of their own (pixels; 0: none)
+    splits = {}
+    for split in (0, 76800, 172800, 307200):
+        edp.set_batch_split(split)
+        splits[split] = timed(lambda: edp.solve_batched(probs, wsb), reps=1)
+    best_split = min(splits, key=splits.get)
+    edp.set_batch_split(best_split)
     tuned = autotune.tune(lambda: edp.solve_batched(probs, wsb), rows=(0,), warps=(0, 1, 2, 4), reps=1)
     ms_batched = timed(lambda: edp.solve_batched(probs, wsb))
     same = all(torch.equal(a, it["labels"]) for a, it in zip(per_labels, items))
@@ -501,9 +508,11 @@ def measure_batched(edp, synth, torch, scale: float = 1.0, n_pairs: int = 64, bu
     ms_graph = timed(lambda: g.replay())
     same_graph = all(torch.equal(a, it["labels"]) for a, it in zip(per_labels, items))
     edp.set_tuning(0, 0, False)
+    edp.set_batch_split(172800)
     return {"pairs": n_pairs, "scale": scale, "workspace_gb": wsb.numel() / 1e9,
             "all_resident_gb": full / 1e9, "updates_per_step": updates,
             "ms_per_pair_launches": ms_per, "ms_batched": ms_batched, "ms_batched_graph": ms_graph,
+            "split_pixels": best_split, "ms_by_split": {str(k): v for k, v in splits.items()},
             "speedup_batched": ms_per / ms_batched, "speedup_graph": ms_per / ms_graph,
             "updates_per_s_batched": updates / (ms_graph * 1e-3), "labels_identical": bool(same and same_graph),
             "autotune": {"rows": tuned[0], "warps_per_row": tuned[1], "table": tuned[3]}}

@@ -442,8 +442,19 @@ size_t edp_batch_workspace_size(const edp_problem *probs, int n);
  * problem), and one launch evaluates every energy.  Results are identical to
  * solving each problem alone.  `probs` is host memory and is read during the
  * call only.  The call enqueues work and returns; it can be captured in a
- * CUDA graph (after one uncaptured call has set the kernels' attributes). */
+ * CUDA graph (after one uncaptured call has set the kernels' attributes).
+ * Problems at or above the size set by edp_set_batch_split run with launches
+ * of their own inside the call. */
 int edp_solve_batched(const edp_problem *probs, int n, void *ws, size_t ws_bytes, edp_stream_t stream);
+
+/* Split of edp_solve_batched (process-wide): a problem of at least
+ * `min_pixels` pixels fills the GPU by itself and is solved with its own
+ * launches in the problem's best shape (cost volume, scan passes, energy),
+ * the smaller problems of a wave share one persistent launch.  0 puts every
+ * problem into the persistent launch.  The default is 172,800 pixels
+ * (480 x 360).  Results never depend on it.  Not thread-safe with
+ * concurrent solves. */
+int edp_set_batch_split(long long min_pixels);
 
 /* Reads the device status word of a workspace used by edp_solve /
  * edp_solve_images / edp_scanline_dp.  Synchronises `stream`. */

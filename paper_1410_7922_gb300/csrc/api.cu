@@ -30,6 +30,7 @@ const char *g_last_kernel = "";  // scan-pass kernel of the most recent solve
 constexpr long long kSpinDefault = 4000000;
 long long g_spin_limit = kSpinDefault;  // polls before an inter-block wait gives up
 int g_hold_band = 0;     // test hook: the band whose first row waits for records never written
+int g_batch_alone_pixels = 172800;  // batched solve: problems of this many pixels or more get their own launches
 void *const *g_prof_events = nullptr;  // optional per-pass events (profiling hook)
 int g_prof_n = 0;
 unsigned long long *g_trace = nullptr;  // optional per-band trace buffer (device)
@@ -752,6 +753,12 @@ int edp_last_pass_launches(void) { return g_last_launches; }
 
 const char *edp_last_pass_kernel(void) { return g_last_kernel; }
 
+int edp_set_batch_split(long long min_pixels) {
+    if (min_pixels < 0) return EDP_ERR_INVALID_ARG;
+    g_batch_alone_pixels = min_pixels > INT_MAX ? INT_MAX : (int)min_pixels;
+    return EDP_OK;
+}
+
 int edp_set_spin_limit(long long polls) {
     if (polls < 0) return EDP_ERR_INVALID_ARG;
     g_spin_limit = polls ? polls : kSpinDefault;
@@ -1068,8 +1075,10 @@ int check_problem(const edp_problem &pr, Geometry *g) {
     return check_range(pr.W, pr.H, *g, &pr.params);
 }
 
-int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, int iters, unsigned char *ws,
-             cudaStream_t st) {
+// One persistent launch over the problems idx[0..n) of a chunk; problem
+// idx[k] has its region (solve workspace, then cost volume) at ws + offs[k].
+int run_wave(const edp_problem *probs_all, const Geometry *geo_all, const int *idx, const size_t *offs, int n,
+             int iters, unsigned char *ws, cudaStream_t st) {
     const size_t ctrl = batch_ctrl_bytes(iters);
     int *status = reinterpret_cast<int *>(ws);
     ZeroBatch zb;
@@ -1092,7 +1101,6 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     B.done = reinterpret_cast<unsigned *>(ws + kHeader + 256);
     B.status = status;
     B.spin_limit = g_spin_limit;
-    size_t off = ctrl;
     long long max_entries = 0, max_pixels = 0;
     // one block shape for the wave: 8 warps (one-axis bands of 8 rows, or
     // teams of the multi-axis body)
@@ -1104,14 +1112,13 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     static SolvePlan plans[kMaxBatch];
     for (int k = 0; k < n; ++k) {
-        const edp_problem &pr = probs[first + k];
-        const Geometry &g = geo[first + k];
-        unsigned char *pws = ws + off;
+        const edp_problem &pr = probs_all[idx[k]];
+        const Geometry &g = geo_all[idx[k]];
+        unsigned char *pws = ws + offs[k];
         const SolveLayout L = solve_layout(pr.W, pr.H, g.Q, g.R, iters);
         int32_t *C = reinterpret_cast<int32_t *>(pws + L.end);
         int rc = plan_solve(C, pr.W, pr.H, g, &pr.params, pr.labels, pws, &plans[k], threads);
         if (rc) return rc;
-        off += problem_bytes(pr, g);
         if (plans[k].r1 ? plans[k].o.l1 == 2 : plans[k].ta.l1 == 2) quad = 1;
         if (!plans[k].r1 && !plans[k].ta.lean) gen = 1;
         smem = std::max(smem, plans[k].smem);
@@ -1123,21 +1130,19 @@ int run_wave(const edp_problem *probs, const Geometry *geo, int first, int n, in
     int order[kMaxBatch], slot_of[kMaxBatch];
     for (int k = 0; k < n; ++k) order[k] = k;
     auto work = [&](int k) {
-        const edp_problem &pr = probs[first + k];
-        return (double)pr.W * pr.H * geo[first + k].Q;
+        const edp_problem &pr = probs_all[idx[k]];
+        return (double)pr.W * pr.H * geo_all[idx[k]].Q;
     };
     std::stable_sort(order, order + n, [&](int a, int b) { return work(a) > work(b); });
     for (int j = 0; j < n; ++j) slot_of[order[j]] = j;
     for (int j = 0; j < n; ++j) B.prefix[j + 1] = B.prefix[j] + plans[order[j]].nbands;
-    off = ctrl;
     for (int k = 0; k < n; ++k) {
-        const edp_problem &pr = probs[first + k];
-        const Geometry &g = geo[first + k];
-        unsigned char *pws = ws + off;
+        const edp_problem &pr = probs_all[idx[k]];
+        const Geometry &g = geo_all[idx[k]];
+        unsigned char *pws = ws + offs[k];
         const SolveLayout L = solve_layout(pr.W, pr.H, g.Q, g.R, iters);
         int32_t *C = reinterpret_cast<int32_t *>(pws + L.end);
         const SolvePlan &P = plans[k];
-        off += problem_bytes(pr, g);
         if (!P.r1 && team_ring(B.pairs ? 2 * pr.W : pr.W, occ * sms) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
         BatchProblem &bp = B.p[slot_of[k]];
         bp.r1 = P.r1;
@@ -1245,8 +1250,33 @@ int edp_solve_batched(const edp_problem *probs, int n, void *ws, size_t ws_bytes
             ++cnt;
         }
         if (cnt == 0) return EDP_ERR_WORKSPACE;
-        int rc = run_wave(probs, geo, first, cnt, iters, w, st);
-        if (rc) return rc;
+        // regions of the chunk's problems; problems that fill the GPU on their
+        // own run with their own launch shapes (one after another), the others
+        // share one persistent launch
+        int widx[kMaxBatch];
+        size_t woff[kMaxBatch];
+        int nw = 0;
+        size_t off = ctrl;
+        for (int k = first; k < first + cnt; ++k) {
+            const edp_problem &pr = probs[k];
+            const Geometry &g = geo[k];
+            if (g_batch_alone_pixels > 0 && (long long)pr.W * pr.H >= g_batch_alone_pixels) {
+                unsigned char *pws = w + off;
+                int32_t *C = reinterpret_cast<int32_t *>(pws + solve_layout(pr.W, pr.H, g.Q, g.R, iters).end);
+                int rc = run_cost(pr.I0, pr.I1, pr.I2, pr.W, pr.H, pr.pitch, &pr.space, &pr.params, g.Q, C, st);
+                if (!rc) rc = run_solve(C, pr.W, pr.H, g, &pr.params, pr.labels, pws, st);
+                if (!rc && pr.energy4) rc = run_energy(C, pr.labels, pr.W, pr.H, &pr.space, &pr.params, g.Q, pr.energy4, st);
+                if (rc) return rc;
+            } else {
+                widx[nw] = k;
+                woff[nw++] = off;
+            }
+            off += problem_bytes(pr, g);
+        }
+        if (nw > 0) {
+            int rc = run_wave(probs, geo, widx, woff, nw, iters, w, st);
+            if (rc) return rc;
+        }
         first += cnt;
     }
     return EDP_OK;

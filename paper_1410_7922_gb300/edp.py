@@ -71,6 +71,7 @@ def load() -> ctypes.CDLL:
         "edp_last_pass_launches": ([], I),
         "edp_last_pass_kernel": ([], ctypes.c_char_p),
         "edp_set_spin_limit": ([ctypes.c_longlong], I),
+        "edp_set_batch_split": ([ctypes.c_longlong], I),
         "edp_test_hold_band": ([I], I),
         "edp_set_trace": ([P, SZ], I),
         "edp_cost_volume": ([P, P, P, I, I, I, LS, PR, P, P], I),
@@ -125,7 +126,7 @@ def exported_symbols() -> list[str]:
             "edp_noalloc_get_device_status", "edp_coarse_labels",
             "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_window_edge_count", "edp_scanline_marginals",
             "edp_set_pass_pairs", "edp_last_pass_launches", "edp_last_pass_kernel", "edp_set_spin_limit",
-            "edp_test_hold_band", "edp_edge_weights", "edp_solve_weighted",
+            "edp_test_hold_band", "edp_set_batch_split", "edp_edge_weights", "edp_solve_weighted",
             "edp_energy_weighted"]
 
 
@@ -226,6 +227,12 @@ def last_pass_launches() -> int:
 def set_spin_limit(polls: int = 0) -> None:
     """Polls before a wait between row bands gives up (0: the default)."""
     _check(load().edp_set_spin_limit(int(polls)), "set_spin_limit")
+
+
+def set_batch_split(min_pixels: int) -> None:
+    """edp_solve_batched: problems of at least min_pixels pixels get their
+    own launches (0: every problem in the persistent launch)."""
+    _check(load().edp_set_batch_split(int(min_pixels)), "set_batch_split")
 
 
 def test_hold_band(band: int = 0) -> None:
