@@ -45,16 +45,22 @@ WORKLOAD = "motion_edp_640x480_Q65x65"
 WORKLOADS = ("motion_edp_640x480_Q65x65", "motion_edp_320x240_Q33x33", "stereo_edp_450x375_Q64")
 
 
-def make_workload(name: str, pair: int = 0) -> dict:
+def make_workload(name: str, pair: int = 0, size: str = "") -> dict:
+    """The named workload; `size` ("WxH") replaces its image size (smaller
+    cases of the same kernel for profiling)."""
     from paper_1410_7922_gb300 import synth
+    kw = {}
+    if size:
+        W, H = (int(v) for v in size.lower().split("x"))
+        kw = {"W": W, "H": H}
     if name == "stereo_edp_450x375_Q64":
-        w = synth.workload_stereo_450x375(pair=pair)
+        w = synth.workload_stereo_450x375(pair=pair, **kw)
         w["desc"] = {"prior": "truncated linear, lambda=20, K=4", "cost": "min(|IL-IR|, 20)"}
     elif name == "motion_edp_320x240_Q33x33":
-        w = synth.workload_motion_320x240(pair=pair)
+        w = synth.workload_motion_320x240(pair=pair, **kw)
         w["desc"] = {"prior": "per-axis truncated linear, lambda=15, K=3", "cost": "min(|I1(x+o)-I0(x)|, 20)"}
     else:
-        w = synth.workload_motion_640x480(pair=pair)
+        w = synth.workload_motion_640x480(pair=pair, **kw)
         w["desc"] = {"prior": "per-axis truncated linear, lambda=15, K=3", "cost": "min(|I1(x+o)-I0(x)|, 20)"}
     return w
 PASS_NAMES = ["P1", "P2", "P3", "P4"]
@@ -68,6 +74,7 @@ def parse_args():
     ap.add_argument("--iters", type=int, default=1, help="EDP iterations j per step")
     ap.add_argument("--impl", default="edp", choices=["edp", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS)
+    ap.add_argument("--size", default="", help="WxH: the workload at another image size (profiling runs)")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--extra", default="", help="comma list of longer side measurements: batched,proposal")
@@ -333,7 +340,7 @@ def run_reference(args, world, rank):
         return
     import oracle
     oracle.build()
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, size=args.size)
     H, W = w["I0"].shape
     Q = 1
     for r in range(w["space"]["R"]):
@@ -563,7 +570,7 @@ def run_gpu(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     j = args.iters
-    w = make_workload(args.workload, pair=rank)  # weak scaling: one pair per rank
+    w = make_workload(args.workload, pair=rank, size=args.size)  # weak scaling: one pair per rank
     H, W = w["I0"].shape
     space, prior = w["space"], w["prior"]
     Q = edp.n_labels(space)
@@ -633,7 +640,7 @@ def run_gpu(args, world, rank, local):
     msg_bytes = sum(launch_bytes(npass, W, H, Q, j))
     peak, peak_kind = measured_peaks()
     kernel = edp.last_pass_kernel()
-    traffic = profiled_traffic(args.workload, kernel)
+    traffic = profiled_traffic(args.workload + (f"@{args.size}" if args.size else ""), kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
                 "bytes_per_launch_avg": nbytes / npass, "bytes_model": "20*Q per pixel per pass (sums form)",
@@ -686,7 +693,8 @@ def run_gpu(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": args.workload, "W": W, "H": H, "Q": Q, "iters": j,
+                "config": {"workload": args.workload + (f"@{args.size}" if args.size else ""), "W": W, "H": H,
+                           "Q": Q, "iters": j,
                            "prior": w["desc"]["prior"], "cost": w["desc"]["cost"],
                            "l2_cache": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world} (one independent pair per GPU)"},
