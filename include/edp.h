@@ -43,8 +43,11 @@
  *  the clip) is built for edp_solve / edp_solve_images / edp_solve_batched
  *  when every label axis is served by the one-axis kernel (R = 1, Q <= 256)
  *  or by the whole-line form of the multi-axis kernel (all axes of 9, 17 or
- *  33 labels, or all of 65), and for edp_solve_windowed; other shapes and
- *  edp_scanline_dp return EDP_ERR_UNSUPPORTED for l1 = 2.
+ *  33 labels, or all of 65), for edp_solve / edp_solve_images on the
+ *  two-axis spaces 27 x 15 (the paper's +-13 x +-7 motion space) and
+ *  25 x 25 (the two-axis line kernel), for edp_solve_windowed, and for
+ *  edp_scanline_dp / edp_scanline_marginals on one label axis; other shapes
+ *  return EDP_ERR_UNSUPPORTED for l1 = 2.
  *  Cost, Eq. Cost_value: C(x, q) = min(|I1(x + o(q)) - I0(x)|^l2, cmax),
  *  cmax where x + o(q) leaves the image.
  */
@@ -230,7 +233,8 @@ int edp_scanline_dp(const int32_t *C, int W, int H, const edp_label_space *space
  * = F(x, q) + B(x, q) - C(x, q), and labels[y][x] is its lowest-index
  * argmin.  marginals: optional int32 [H][W][Q] output of S_Omega (NULL:
  * not written).  ws: edp_workspace_size(EDP_OP_SCANLINE_MARGINALS, ...)
- * bytes, 256-byte aligned.  l1 = 1 only (EDP_ERR_UNSUPPORTED otherwise);
+ * bytes, 256-byte aligned.  l1 = 1, or l1 = 2 on one label axis
+ * (EDP_ERR_UNSUPPORTED otherwise);
  * EDP_ERR_RANGE when W * (cmax + R * lambda * g^l1) >= 2^29. */
 int edp_scanline_marginals(const int32_t *C, int W, int H, const edp_label_space *space, const edp_params *params,
                            int32_t *labels, int32_t *marginals, void *ws, size_t ws_bytes, edp_stream_t stream);

@@ -359,9 +359,11 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
     // (measured: faster than the whole-line multi-axis form where lines hold
     // 65 labels, whose rows the multi-axis kernel cannot all keep resident;
     // slower at 33 x 33)
-    const bool line_pick = g_line_mode == 2 || (g_line_mode == 0 && std::max(g.Qr[0], g.Qr[1]) > 33);
-    if (!fixed_threads && g.R == 2 && p->l1 == 1 && line_pick && !g_generic_team &&
-        pass_line_built(g.Qr[0], g.Qr[1])) {
+    // The quadratic prior: the line kernel serves the shapes it has a build
+    // for (no other form serves them with l1 = 2).
+    const bool line_pick = g_line_mode == 2 ||
+                           (g_line_mode == 0 && (std::max(g.Qr[0], g.Qr[1]) > 33 || p->l1 == 2));
+    if (!fixed_threads && g.R == 2 && line_pick && !g_generic_team && pass_line_built(g.Qr[0], g.Qr[1], p->l1)) {
         P->line = true;
         P->Q0 = g.Qr[0];
         P->Q1 = g.Qr[1];
@@ -380,7 +382,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
                 const int nb = (H + nt - 1) / nt;
                 const size_t sm = pass_line_smem(nt, P->Q0, P->Q1);
                 if (sm > (size_t)kMaxSmem) break;
-                const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, 32 * TW * nt, sm);
+                const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, p->l1, 32 * TW * nt, sm);
                 if (nb >= sms && nb <= occ * sms) NT = nt;
             }
         }
@@ -410,7 +412,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         // one column apart, so a short ring suffices and stays in L2; otherwise
         // the depth that lets the first resident band finish its row
         {
-            const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, 32 * TW * NT, pass_line_smem(NT, P->Q0, P->Q1));
+            const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, p->l1, 32 * TW * NT, pass_line_smem(NT, P->Q0, P->Q1));
             const bool all_resident = a.nbands <= std::max(1, occ) * sms;
             a.ring = all_resident ? std::min(kLineRingResident, team_ring(2 * W, kResidentMin))
                                   : team_ring(2 * W, kResidentMin);
@@ -572,7 +574,7 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     bool resident;  // every row band has a block at once
     if (P.line) {
-        const int occ = std::max(1, edp_pass_line_occupancy(P.Q0, P.Q1, P.threads, P.smem));
+        const int occ = std::max(1, edp_pass_line_occupancy(P.Q0, P.Q1, P.ta.l1, P.threads, P.smem));
         grid_t = std::min(P.nbands, occ * sms);
         if (grid_t < P.nbands && team_ring(2 * W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
         resident = grid_t >= P.nbands;
@@ -865,7 +867,7 @@ int edp_scanline_dp(const int32_t *C, int W, int H, const edp_label_space *space
     if ((rc = check_prior(params))) return rc;
     if (!C || !labels || !ws || W < 1 || H < 1) return EDP_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
-    if (params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    if (params->l1 != 1 && g.R != 1) return EDP_ERR_UNSUPPORTED;  // quadratic taps: one label axis
     if (ws_bytes < edp_workspace_size(EDP_OP_SCANLINE_DP, W, H, space, params)) return EDP_ERR_WORKSPACE;
     // S values along a row stay below W * (cmax + R * lambda * g)
     if ((long long)W * (params->cmax + (long long)g.R * cap_value(params)) >= (1LL << 29)) return EDP_ERR_RANGE;
@@ -892,6 +894,8 @@ int edp_scanline_dp(const int32_t *C, int W, int H, const edp_label_space *space
     a.lam = params->lambda;
     a.capv = (int)cap_value(params);
     a.mode = params->prior_mode;
+    a.l1 = params->l1;
+    a.g = params->g;
     a.RB = cfg.RB;
     const int grid = (H + cfg.RB - 1) / cfg.RB;
     return launch_scanline(a, cfg.em, cfg.threads, cfg.smem, grid, st) ? EDP_ERR_CUDA : EDP_OK;
@@ -905,7 +909,7 @@ int edp_scanline_marginals(const int32_t *C, int W, int H, const edp_label_space
     if ((rc = check_prior(params))) return rc;
     if (!C || !labels || !ws || W < 1 || H < 1) return EDP_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(ws) % kAlign) return EDP_ERR_INVALID_ARG;
-    if (params->l1 != 1) return EDP_ERR_UNSUPPORTED;
+    if (params->l1 != 1 && g.R != 1) return EDP_ERR_UNSUPPORTED;  // quadratic taps: one label axis
     if (ws_bytes < edp_workspace_size(EDP_OP_SCANLINE_MARGINALS, W, H, space, params)) return EDP_ERR_WORKSPACE;
     // forward and backward sums stay below W * (cmax + R * lambda * g): their
     // sum minus the cost fits int32
@@ -930,6 +934,8 @@ int edp_scanline_marginals(const int32_t *C, int W, int H, const edp_label_space
     a.lam = params->lambda;
     a.capv = (int)cap_value(params);
     a.mode = params->prior_mode;
+    a.l1 = params->l1;
+    a.g = params->g;
     a.RB = cfg.RB;
     a.no_ptr = 1;
     const int grid = (H + cfg.RB - 1) / cfg.RB;

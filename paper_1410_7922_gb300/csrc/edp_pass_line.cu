@@ -7,7 +7,7 @@
 
 namespace edp {
 
-template <int LA, int LB>
+template <int LA, int LB, bool QUAD = false>
 __global__ void __launch_bounds__(line::kMaxThreads, 1) edp_pass_line_kernel(TeamArgs A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
@@ -20,12 +20,19 @@ __global__ void __launch_bounds__(line::kMaxThreads, 1) edp_pass_line_kernel(Tea
         __syncthreads();
         const int band = s_band;
         if (band >= A.nbands) break;
-        if (!line_band<LA, LB>(A, band, smem_i, &s_abort)) return;
+        if (!line_band<LA, LB, QUAD>(A, band, smem_i, &s_abort)) return;
     }
 }
 
-// the shapes with a build: (Q0, Q1) = (LB, LA)
-static void *line_kernel_for(int Q0, int Q1) {
+// the shapes with a build: (Q0, Q1) = (LB, LA); the truncated quadratic
+// prior for the two shapes no other kernel serves with it
+static void *line_kernel_for(int Q0, int Q1, int l1) {
+    if (l1 == 2) {
+        if (Q0 == 27 && Q1 == 15) return reinterpret_cast<void *>(edp_pass_line_kernel<15, 27, true>);
+        if (Q0 == 25 && Q1 == 25) return reinterpret_cast<void *>(edp_pass_line_kernel<25, 25, true>);
+        return nullptr;
+    }
+    if (l1 != 1) return nullptr;
     if (Q0 == 65 && Q1 == 65) return reinterpret_cast<void *>(edp_pass_line_kernel<65, 65>);
     if (Q0 == 33 && Q1 == 33) return reinterpret_cast<void *>(edp_pass_line_kernel<33, 33>);
     if (Q0 == 25 && Q1 == 25) return reinterpret_cast<void *>(edp_pass_line_kernel<25, 25>);
@@ -34,14 +41,14 @@ static void *line_kernel_for(int Q0, int Q1) {
     return nullptr;
 }
 
-bool pass_line_built(int Q0, int Q1) { return line_kernel_for(Q0, Q1) != nullptr; }
+bool pass_line_built(int Q0, int Q1, int l1) { return line_kernel_for(Q0, Q1, l1) != nullptr; }
 
 int pass_line_warps(int Q0, int Q1) { return (std::max(Q0, Q1) + 31) / 32; }
 
 size_t pass_line_smem(int NT, int Q0, int Q1) { return (size_t)NT * line::team_ints(Q1, Q0) * 4; }
 
-int edp_pass_line_occupancy(int Q0, int Q1, int threads, size_t smem) {
-    void *k = line_kernel_for(Q0, Q1);
+int edp_pass_line_occupancy(int Q0, int Q1, int l1, int threads, size_t smem) {
+    void *k = line_kernel_for(Q0, Q1, l1);
     if (!k) return 0;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
@@ -50,7 +57,7 @@ int edp_pass_line_occupancy(int Q0, int Q1, int threads, size_t smem) {
 }
 
 int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, int threads, size_t smem, cudaStream_t st) {
-    void *k = line_kernel_for(Q0, Q1);
+    void *k = line_kernel_for(Q0, Q1, a.l1);
     if (!k) return -1;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     void *args[] = {const_cast<TeamArgs *>(&a)};

@@ -75,10 +75,10 @@ size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb);
 
 // one EDP scan pass, two label axes, one label line per lane (edp_pass_line.cu);
 // uses TeamArgs with T = warps per row, NT = rows per block
-bool pass_line_built(int Q0, int Q1);
+bool pass_line_built(int Q0, int Q1, int l1);
 int pass_line_warps(int Q0, int Q1);
 size_t pass_line_smem(int NT, int Q0, int Q1);
-int edp_pass_line_occupancy(int Q0, int Q1, int threads, size_t smem);
+int edp_pass_line_occupancy(int Q0, int Q1, int l1, int threads, size_t smem);
 int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, int threads, size_t smem, cudaStream_t st);
 
 // one EDP scan pass, one label axis, one warp per row (edp_pass_r1.cu)
@@ -151,6 +151,7 @@ struct ScanArgs {
     int W, H, Q, R;
     AxisCfg ax[3];
     int lam, capv, mode;
+    int l1, g;              // prior power (2: quadratic taps, one label axis) and truncation
     int RB;
     int *sums;              // optional [H][W][Q]: S of every column (min-marginal mode)
     int reverse;            // 1: the chain runs from column W-1 to 0

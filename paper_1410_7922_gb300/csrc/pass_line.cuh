@@ -145,6 +145,28 @@ __device__ __forceinline__ void line_sweeps1(int (&h)[L], int lam, int clip) {
     for (int i = 0; i < L; ++i) h[i] = min(h[i], clip);
 }
 
+// Truncated quadratic prior (l1 = 2, the generalized RMS of Eq. M_decmp) on
+// one line of L labels held by one lane: h[i] <- min over the taps |d| < g of
+// input[i + d] + lambda d^2 (sources farther away cost at least the clip
+// lambda g^2), then the clip.  The input is read from the lane's own copy of
+// the line in shared memory, src[i * st]; no other lane writes it meanwhile.
+template <int L>
+__device__ __forceinline__ void line_quad(int (&h)[L], const int *src, int st, int lam, int g, int clip) {
+    const int dmax = min(g, L);
+    for (int d = 1; d < dmax; ++d) {
+        const int w = lam * d * d;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            int c = kBig;
+            if (i + d < L) c = src[(i + d) * st];
+            if (i - d >= 0) c = min(c, src[(i - d) * st]);
+            h[i] = min(h[i], c + w);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) h[i] = min(h[i], clip);
+}
+
 }  // namespace line
 
 // Phase A loads of one label column (axis-1 line) of one pixel: C, the old
@@ -225,7 +247,8 @@ __device__ __forceinline__ bool line_load(const int *__restrict__ Cp, const int 
 // LB x LA labels (axis 0: LB labels, contiguous; axis 1: LA labels).  Every
 // thread of the block calls it with the same band; returns false when the
 // pass was aborted (a wait timed out).
-template <int LA, int LB>
+// QUAD: the build for the truncated quadratic prior (l1 = 2).
+template <int LA, int LB, bool QUAD = false>
 __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int *smem, volatile int *s_abort) {
     using namespace line;
     constexpr int P0 = pitch0(LB);
@@ -391,12 +414,22 @@ __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int
                 }
             }
             if (!bad && colA) {
-                line_sweeps1<LA>(hv, lam_a, per_axis ? lmin_a + cap_a : kBig);
+                if constexpr (QUAD) {
+                    // the taps read the column from shared memory (m_a is no longer needed)
+#pragma unroll
+                    for (int i = 0; i < LA; ++i) Xa[i * P0 + tl] = hv[i];
+                    line_quad<LA>(hv, Xa + tl, P0, lam_a, A.g, per_axis ? lmin_a + cap_a : kBig);
+                } else {
+                    line_sweeps1<LA>(hv, lam_a, per_axis ? lmin_a + cap_a : kBig);
+                }
 #pragma unroll
                 for (int i = 0; i < LA; ++i) Xa[i * P0 + tl] = hv[i];
 #pragma unroll
                 for (int i = 0; i < LA; ++i) hv[i] = Xb[i * P0 + tl];
-                line_sweeps1<LA>(hv, lam_b, per_axis ? lmin_b + cap_b : kBig);
+                if constexpr (QUAD)
+                    line_quad<LA>(hv, Xb + tl, P0, lam_b, A.g, per_axis ? lmin_b + cap_b : kBig);
+                else
+                    line_sweeps1<LA>(hv, lam_b, per_axis ? lmin_b + cap_b : kBig);
 #pragma unroll
                 for (int i = 0; i < LA; ++i) Xb[i * P0 + tl] = hv[i];
             }
@@ -442,7 +475,10 @@ __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int
                     gv[j] = ra[j];
                     lm = min(lm, gv[j]);
                 }
-                line_sweeps1<LB>(gv, lam_a, (per_axis ? lm : ga) + cap_a);
+                if constexpr (QUAD)
+                    line_quad<LB>(gv, ra, 1, lam_a, A.g, (per_axis ? lm : ga) + cap_a);
+                else
+                    line_sweeps1<LB>(gv, lam_a, (per_axis ? lm : ga) + cap_a);
                 if (nxt) {  // m_a of the next column of the row
 #pragma unroll
                     for (int j = 0; j < LB; ++j) ra[j] = gv[j];
@@ -453,7 +489,10 @@ __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int
                     gv[j] = rb[j];
                     lm = min(lm, gv[j]);
                 }
-                line_sweeps1<LB>(gv, lam_b, (per_axis ? lm : gb) + cap_b);
+                if constexpr (QUAD)
+                    line_quad<LB>(gv, rb, 1, lam_b, A.g, (per_axis ? lm : gb) + cap_b);
+                else
+                    line_sweeps1<LB>(gv, lam_b, (per_axis ? lm : gb) + cap_b);
                 if (to_mbox) {  // m_b of this column of the row below
                     int *const nb = nx_slots + (s & 1) * XS + tl * P0;
 #pragma unroll

@@ -127,7 +127,34 @@ __global__ void __launch_bounds__(kMaxThreads) scanline_kernel(ScanArgs A) {
                 k[i] = (gvalid && i < a0.E && p < a0.L) ? (((long long)Sv[w0 * Q + q] << 32) | (unsigned)q)
                                                         : kBigKey;
             }
-            const long long lmin = line_dt_key<EM>(k, a0.E, a0.G, j0, lam_k);
+            long long lmin;
+            if (A.l1 == 2 && A.R == 1) {
+                // truncated quadratic prior (Eq. M_decmp, l1 = 2) on one label
+                // axis: the taps |d| < g on keys, read from this row's S(x - 1)
+                // in shared memory (farther sources cost at least the clip)
+                lmin = kBigKey;
+#pragma unroll
+                for (int i = 0; i < EM; ++i) lmin = min(lmin, k[i]);
+                for (int d = a0.G >> 1; d >= 1; d >>= 1) lmin = min(lmin, __shfl_xor_sync(full, lmin, d, a0.G));
+                const int dmax = min(A.g, a0.L);
+#pragma unroll
+                for (int i = 0; i < EM; ++i) {
+                    const int p = j0 * a0.E + i;
+                    if (!(gvalid && i < a0.E && p < a0.L)) continue;
+                    long long o = k[i];
+                    for (int d = 1; d < dmax; ++d) {
+                        const long long w = (long long)(A.lam * d * d) << 32;
+                        if (p + d < a0.L)
+                            o = min(o, (((long long)Sv[w0 * Q + base0 + p + d] << 32) | (unsigned)(base0 + p + d)) + w);
+                        if (p - d >= 0)
+                            o = min(o, (((long long)Sv[w0 * Q + base0 + p - d] << 32) | (unsigned)(base0 + p - d)) + w);
+                    }
+                    k[i] = o;
+                }
+                __syncwarp();  // every lane of the line has read S(x - 1) before it is overwritten
+            } else {
+                lmin = line_dt_key<EM>(k, a0.E, a0.G, j0, lam_k);
+            }
             if (!gvalid) continue;
             if (A.R == 1) {
 #pragma unroll

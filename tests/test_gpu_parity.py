@@ -112,6 +112,29 @@ def test_scanline_random(edp_lib, Q, mode):
         assert np.array_equal(host(glab), lab), prior
 
 
+@pytest.mark.parametrize("Q", [(7,), (20,), (64,), (100,), (300,)])
+@pytest.mark.parametrize("g", [1, 2, 3, 5])
+def test_scanline_quadratic_prior(edp_lib, Q, g):
+    """Truncated quadratic prior (l1 = 2, the taps of Eq. M_decmp) in the
+    scanline DP on one label axis: labels and row energies against the
+    oracle's definition tier, and the min-marginal mode, on random and
+    tie-heavy costs (the lane-group shapes of 7 .. 300 labels)."""
+    rng = np.random.default_rng(sum(Q) * 5 + g)
+    n = int(np.prod(Q))
+    H, W = 11, 23
+    for hi in (30, 4):
+        C = rng.integers(0, hi, size=(H, W, n)).astype(np.int32)
+        prior = {"lam": int(rng.integers(1, 7)), "g": g, "l1": 2, "mode": "joint"}
+        lab, row_e = oracle.scanline_dp(C, sp(Q), prior, tier=0)
+        glab, grow = edp_lib.scanline_dp(dev(C), sp(Q), prior)
+        assert np.array_equal(host(grow), row_e), prior
+        assert np.array_equal(host(glab), lab), prior
+        S = oracle.min_marginals(C, sp(Q), prior, tier=0)
+        mlab, marg = edp_lib.scanline_marginals(dev(C), sp(Q), prior, marginals=True)
+        assert np.array_equal(host(marg).astype(np.int64), S), prior
+        assert np.array_equal(host(mlab), np.argmin(S, axis=2)), prior
+
+
 @pytest.mark.parametrize("Q,mode", [((16,), "joint"), ((64,), "joint"), ((130,), "joint"), ((5, 4), "per_axis"),
                                     ((9, 9), "joint"), ((3, 4, 3), "per_axis")])
 def test_scanline_min_marginals(edp_lib, Q, mode):
@@ -209,7 +232,8 @@ def test_edp_sixteen_iterations(edp_lib, Q, mode):
 
 @pytest.mark.parametrize("Q,mode", [((7,), "joint"), ((64,), "joint"), ((100,), "joint"), ((9, 9), "joint"),
                                     ((9, 9), "per_axis"), ((17, 9), "per_axis"), ((33, 33), "joint"),
-                                    ((17, 17, 9), "per_axis"), ((65, 65), "per_axis")])
+                                    ((17, 17, 9), "per_axis"), ((65, 65), "per_axis"), ((27, 15), "per_axis"),
+                                    ((27, 15), "joint"), ((25, 25), "per_axis")])
 @pytest.mark.parametrize("g", [1, 2, 3, 5])
 def test_edp_quadratic_prior(edp_lib, Q, mode, g):
     """Truncated quadratic prior (l1 = 2, the generalized RMS of Eq. M_decmp)
@@ -232,7 +256,7 @@ def test_quadratic_prior_unsupported_shapes(edp_lib):
         edp_lib.solve(C, sp((5, 4)), prior)
     assert e.value.code == edp_lib.ERR_UNSUPPORTED
     with pytest.raises(edp_lib.EdpError) as e:
-        edp_lib.scanline_dp(C, sp((20,)), prior)
+        edp_lib.scanline_dp(C, sp((5, 4)), prior)
     assert e.value.code == edp_lib.ERR_UNSUPPORTED
 
 
