@@ -137,7 +137,10 @@ size_t edp_workspace_size(int op, int W, int H, const edp_label_space *space,
  *                    of the two-axis line kernel; 4: two-axis spaces take
  *                    the line kernel wherever it is built (Q0 x Q1 = 17 x
  *                    17, 25 x 25, 33 x 33, 65 x 65 and 27 x 15, l1 = 1;
- *                    by default it serves 65 x 65).
+ *                    by default it serves 65 x 65); 5: as 4, with one lane
+ *                    per label line also at 65 x 65 (by default the lines
+ *                    of 65 x 65 are split over two lanes when lambda <=
+ *                    2^30 / (34 * 255)).
  * Used by the autotuner and the tests; results never depend on it.  A shape
  * the kernels cannot run makes the next solve return EDP_ERR_UNSUPPORTED.
  * Not thread-safe with concurrent solves. */
@@ -192,7 +195,8 @@ int edp_set_spin_limit(long long polls);
 /* Test hook for the timeout path (0, the default, turns it off): in the
  * solves enqueued after the call (edp_solve, edp_solve_images,
  * edp_solve_weighted), the first row of row band `band` (> 0) waits for
- * hand-off records of a tag no producer writes.  Its wait runs out after the
+ * hand-off data that is never published (records of a tag no producer
+ * writes, or a column past the last one).  Its wait runs out after the
  * spin limit, the launch sets EDP_ERR_TIMEOUT in the device status word and
  * every kernel of the solve returns; the labels are then undefined.  Makes
  * the wait expire without a fault.  Not thread-safe with concurrent solves. */

@@ -24,6 +24,7 @@ int g_tune_t = 0;        // warps per row override, multi-axis scan pass (0 = au
 int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass kernel
 int g_generic_team = 0;  // 1: multi-axis problems take the generic team body (tests)
 int g_line_mode = 0;     // two-axis line kernel: 0 where it is faster (65-label lines), 1 off, 2 wherever built
+int g_line_split = 1;    // 65 x 65 labels: lines split over lane pairs (0: one lane per line)
 int g_pass_pairs = 2;    // P1 + P2 and P3 + P4 as paired sweeps: 0 never, 1 always, 2 when every band is resident
 int g_last_launches = 0; // scan-pass launches of the most recent solve
 const char *g_last_kernel = "";  // scan-pass kernel of the most recent solve
@@ -193,11 +194,11 @@ SolveLayout solve_layout(int W, int H, int Q, int R, int iters) {
     L.Qm = msg_stride(Q);
     L.cons = kHeader;
     L.counters = align_up(L.cons + npass * H * 4);
-    // two-axis line kernel: per-warp consumed columns and producer flags of
-    // the record ring, [4*iters][H][4] each
+    // two-axis line kernels: per-warp consumed columns and producer flags of
+    // the record ring, [4*iters][H][kLineFlagStride] each
     L.lcons = align_up(L.counters + npass * 4);
-    L.lflag = align_up(L.lcons + npass * H * 16);
-    L.ll = align_up(L.lflag + npass * H * 16);
+    L.lflag = align_up(L.lcons + npass * H * kLineFlagStride * 4);
+    L.ll = align_up(L.lflag + npass * H * kLineFlagStride * 4);
     // one-axis kernel: a record per column of a paired sweep (2W) for every band boundary
     const size_t r1 = (R == 1 && Q <= 256) ? (size_t)((H + kMinRowsR1 - 1) / kMinRowsR1) * 2 * W * Q * 8 : 0;
     const size_t tm = (size_t)H * team_ring(2 * W, kResidentMin) * L.Qm * 8;  // paired sweeps: 2W columns
@@ -291,6 +292,7 @@ bool team_shape(const Geometry &g, int T, int gpar, TeamShape *S) {
 struct SolvePlan {
     bool r1;          // warp-per-row body (one label axis, Q <= 256)
     bool line;        // two-axis line kernel (one label line per lane)
+    bool split;       // its form with each line split over two lanes
     int Q0, Q1;       // its label-space shape
     int nbands;
     int threads;
@@ -367,27 +369,41 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         P->line = true;
         P->Q0 = g.Qr[0];
         P->Q1 = g.Qr[1];
-        const int TW = pass_line_warps(P->Q0, P->Q1);
+        // lines split over lane pairs where built; the completions of the
+        // split sweeps add up to 33 lambda, bounded here for the heaviest
+        // per-edge multiplier (255)
+        P->split = g_line_split && pass_line_split_built(P->Q0, P->Q1, p->l1) &&
+                   (long long)p->lambda * 255 <= pass_line_split_max_lambda();
+        const bool split = P->split;
+        const int TW = pass_line_warps(P->Q0, P->Q1, split);
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         sms = std::max(1, sms);
-        // rows per block: the most that still keeps every SM busy and every
-        // row band resident (one row per block otherwise)
+        // rows per block: every row band resident, the fewest rows on the
+        // busiest SM (blocks are spread evenly), then the most rows per block
+        // (fewer hand-offs between blocks); one row per block when no shape
+        // keeps every band resident
         int NT = 1;
         if (g_tune_rb > 0) {
             NT = std::min(g_tune_rb, 4);
         } else {
-            for (int nt = 2; nt <= 4; ++nt) {
+            int best = INT_MAX;
+            for (int nt = 1; nt <= 4; ++nt) {
                 const int nb = (H + nt - 1) / nt;
-                const size_t sm = pass_line_smem(nt, P->Q0, P->Q1);
+                const size_t sm = pass_line_smem(nt, P->Q0, P->Q1, split);
                 if (sm > (size_t)kMaxSmem) break;
-                const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, p->l1, 32 * TW * nt, sm);
-                if (nb >= sms && nb <= occ * sms) NT = nt;
+                const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, p->l1, split, 32 * TW * nt, sm);
+                if (occ < 1 || nb > occ * sms) continue;
+                const int load = nt * ((nb + sms - 1) / sms);
+                if (load <= best) {
+                    best = load;
+                    NT = nt;
+                }
             }
         }
         NT = std::max(1, std::min(NT, H));
-        P->smem = pass_line_smem(NT, P->Q0, P->Q1);
+        P->smem = pass_line_smem(NT, P->Q0, P->Q1, split);
         if (P->smem > (size_t)kMaxSmem) return EDP_ERR_UNSUPPORTED;
         TeamArgs &a = P->ta;
         a.C = C;
@@ -412,7 +428,7 @@ int plan_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_para
         // one column apart, so a short ring suffices and stays in L2; otherwise
         // the depth that lets the first resident band finish its row
         {
-            const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, p->l1, 32 * TW * NT, pass_line_smem(NT, P->Q0, P->Q1));
+            const int occ = edp_pass_line_occupancy(P->Q0, P->Q1, p->l1, split, 32 * TW * NT, P->smem);
             const bool all_resident = a.nbands <= std::max(1, occ) * sms;
             a.ring = all_resident ? std::min(kLineRingResident, team_ring(2 * W, kResidentMin))
                                   : team_ring(2 * W, kResidentMin);
@@ -574,7 +590,7 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     bool resident;  // every row band has a block at once
     if (P.line) {
-        const int occ = std::max(1, edp_pass_line_occupancy(P.Q0, P.Q1, P.ta.l1, P.threads, P.smem));
+        const int occ = std::max(1, edp_pass_line_occupancy(P.Q0, P.Q1, P.ta.l1, P.split, P.threads, P.smem));
         grid_t = std::min(P.nbands, occ * sms);
         if (grid_t < P.nbands && team_ring(2 * W, grid_t) > P.ta.ring) return EDP_ERR_UNSUPPORTED;
         resident = grid_t >= P.nbands;
@@ -593,7 +609,9 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
     const bool pairs = pairs_for(resident);
     const int per_it = pairs ? 2 : 4;
     g_last_launches = per_it * p->iters;
-    g_last_kernel = P.r1 ? "edp_pass_r1_kernel" : (P.line ? "edp_pass_line_kernel" : "edp_pass_team_kernel");
+    g_last_kernel = P.r1     ? "edp_pass_r1_kernel"
+                    : P.line ? (P.split ? "edp_pass_line2_kernel" : "edp_pass_line_kernel")
+                             : "edp_pass_team_kernel";
     for (int it = 0; it < p->iters; ++it) {
         for (int k = 0; k < per_it; ++k) {
             const int launch = it * per_it + k;
@@ -606,14 +624,14 @@ int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_param
             if (P.line) {
                 TeamArgs a = P.ta;
                 const int slot = it * 4 + set_launch(a, it, k, p->iters, pairs);
-                a.cons = reinterpret_cast<unsigned *>(ws + P.L.lcons) + (size_t)slot * H * 4;
-                a.rflag = reinterpret_cast<unsigned *>(ws + P.L.lflag) + (size_t)slot * H * 4;
+                a.cons = reinterpret_cast<unsigned *>(ws + P.L.lcons) + (size_t)slot * H * kLineFlagStride;
+                a.rflag = reinterpret_cast<unsigned *>(ws + P.L.lflag) + (size_t)slot * H * kLineFlagStride;
                 a.tag0 = 1 + slot * P.laps;
                 a.hold_band = g_hold_band;
                 a.band_counter = reinterpret_cast<unsigned *>(ws + P.L.counters) + slot;
                 a.grid = grid_t;
                 a.trace = trace;
-                if (launch_edp_pass_line(a, P.Q0, P.Q1, P.threads, P.smem, st)) return EDP_ERR_CUDA;
+                if (launch_edp_pass_line(a, P.Q0, P.Q1, P.split, P.threads, P.smem, st)) return EDP_ERR_CUDA;
             } else if (P.r1) {
                 PassR1Args a = P.o;
                 const int slot = it * 4 + set_launch(a, it, k, p->iters, pairs);  // counters of the first pass
@@ -735,13 +753,14 @@ const char *edp_status_string(int status) {
 int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, int general_kernel) {
     if (rows_per_block < 0 || labels_per_lane < 0 || labels_per_lane > kEM) return EDP_ERR_INVALID_ARG;
     if (warps_per_row < 0 || warps_per_row > 12) return EDP_ERR_INVALID_ARG;
-    if (general_kernel < 0 || general_kernel > 4) return EDP_ERR_INVALID_ARG;
+    if (general_kernel < 0 || general_kernel > 5) return EDP_ERR_INVALID_ARG;
     g_tune_rb = rows_per_block;
     g_tune_e = labels_per_lane;
     g_tune_t = warps_per_row;
     g_force_general = general_kernel == 1 || general_kernel == 2;
     g_generic_team = general_kernel == 2;
-    g_line_mode = general_kernel == 3 ? 1 : (general_kernel == 4 ? 2 : 0);
+    g_line_mode = general_kernel == 3 ? 1 : (general_kernel >= 4 ? 2 : 0);
+    g_line_split = general_kernel == 5 ? 0 : 1;
     return EDP_OK;
 }
 

@@ -1,9 +1,10 @@
-// edp_pass_line.cu -- the two-axis scan-pass kernel (one label line per
-// lane); the band body is in pass_line.cuh.  One build per label-space shape
-// (Q0 x Q1): the lines are held in registers with exact lengths.
+// edp_pass_line.cu -- the two-axis scan-pass kernels: one label line per
+// lane (band body in pass_line.cuh) and each line split over two lanes
+// (pass_line2.cuh).  One build per label-space shape (Q0 x Q1): the lines
+// are held in registers with exact lengths.
 #include <algorithm>
 
-#include "pass_line.cuh"
+#include "pass_line2.cuh"
 
 namespace edp {
 
@@ -24,9 +25,32 @@ __global__ void __launch_bounds__(line::kMaxThreads, 1) edp_pass_line_kernel(Tea
     }
 }
 
+// lines split over lane pairs; CH: global loads per batch and lane
+template <int LA, int LB, int CH>
+__global__ void __launch_bounds__(line2::kMaxThreads, 1) edp_pass_line2_kernel(TeamArgs A) {
+    extern __shared__ __align__(16) int smem_i[];
+    __shared__ int s_band;
+    __shared__ volatile int s_abort;
+    if (threadIdx.x == 0) s_abort = (*(volatile int *)A.status != 0);
+    __syncthreads();
+    if (s_abort) return;
+    while (true) {
+        if (threadIdx.x == 0) s_band = atomicAdd(A.band_counter, 1);
+        __syncthreads();
+        const int band = s_band;
+        if (band >= A.nbands) break;
+        if (!line2_band<LA, LB, CH>(A, band, smem_i, &s_abort)) return;
+    }
+}
+
+static void *line2_kernel_for(int Q0, int Q1, int l1) {
+    if (l1 == 1 && Q0 == 65 && Q1 == 65) return reinterpret_cast<void *>(edp_pass_line2_kernel<65, 65, 6>);
+    return nullptr;
+}
+
 // the shapes with a build: (Q0, Q1) = (LB, LA); the truncated quadratic
 // prior for the two shapes no other kernel serves with it
-static void *line_kernel_for(int Q0, int Q1, int l1) {
+static void *line1_kernel_for(int Q0, int Q1, int l1) {
     if (l1 == 2) {
         if (Q0 == 27 && Q1 == 15) return reinterpret_cast<void *>(edp_pass_line_kernel<15, 27, true>);
         if (Q0 == 25 && Q1 == 25) return reinterpret_cast<void *>(edp_pass_line_kernel<25, 25, true>);
@@ -41,14 +65,26 @@ static void *line_kernel_for(int Q0, int Q1, int l1) {
     return nullptr;
 }
 
-bool pass_line_built(int Q0, int Q1, int l1) { return line_kernel_for(Q0, Q1, l1) != nullptr; }
+static void *line_kernel_for(int Q0, int Q1, int l1, bool split) {
+    return split ? line2_kernel_for(Q0, Q1, l1) : line1_kernel_for(Q0, Q1, l1);
+}
 
-int pass_line_warps(int Q0, int Q1) { return (std::max(Q0, Q1) + 31) / 32; }
+bool pass_line_built(int Q0, int Q1, int l1) { return line1_kernel_for(Q0, Q1, l1) != nullptr; }
 
-size_t pass_line_smem(int NT, int Q0, int Q1) { return (size_t)NT * line::team_ints(Q1, Q0) * 4; }
+bool pass_line_split_built(int Q0, int Q1, int l1) { return line2_kernel_for(Q0, Q1, l1) != nullptr; }
 
-int edp_pass_line_occupancy(int Q0, int Q1, int l1, int threads, size_t smem) {
-    void *k = line_kernel_for(Q0, Q1, l1);
+int pass_line_split_max_lambda() { return line2::kMaxLambda; }
+
+int pass_line_warps(int Q0, int Q1, bool split) {
+    return split ? (std::max(Q0, Q1) + 15) / 16 : (std::max(Q0, Q1) + 31) / 32;
+}
+
+size_t pass_line_smem(int NT, int Q0, int Q1, bool split) {
+    return (size_t)NT * (split ? line2::team_ints(Q1) : line::team_ints(Q1, Q0)) * 4;
+}
+
+int edp_pass_line_occupancy(int Q0, int Q1, int l1, bool split, int threads, size_t smem) {
+    void *k = line_kernel_for(Q0, Q1, l1, split);
     if (!k) return 0;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
@@ -56,8 +92,8 @@ int edp_pass_line_occupancy(int Q0, int Q1, int l1, int threads, size_t smem) {
     return occ;
 }
 
-int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, int threads, size_t smem, cudaStream_t st) {
-    void *k = line_kernel_for(Q0, Q1, a.l1);
+int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, bool split, int threads, size_t smem, cudaStream_t st) {
+    void *k = line_kernel_for(Q0, Q1, a.l1, split);
     if (!k) return -1;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     void *args[] = {const_cast<TeamArgs *>(&a)};

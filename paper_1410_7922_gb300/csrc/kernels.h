@@ -44,8 +44,8 @@ struct TeamArgs {
     int *M[4];              // [H][W][Qm] messages into each pixel from +x, -x, +y, -y
     int *labels;            // [H][W], written by the final pass
     int2 *ll;               // [nbands][ring][Qm] {value, tag} records between bands
-    unsigned *cons;         // [nbands] columns of each band's records consumed ([nbands][4] per warp: line kernel)
-    unsigned *rflag;        // line kernel: [nbands][4] columns of records each producing warp has written
+    unsigned *cons;         // [nbands] columns of each band's records consumed ([nbands][8] per warp: line kernels)
+    unsigned *rflag;        // line kernels: [nbands][8] columns of records each producing warp has written
     unsigned *band_counter;
     int *status;
     int W, H, Q, Qm, R;     // Qm: message stride, Q rounded up to a multiple of 4
@@ -75,11 +75,17 @@ size_t pass_team_smem(int NT, int Qm, int R, int nbuf, int kmb);
 
 // one EDP scan pass, two label axes, one label line per lane (edp_pass_line.cu);
 // uses TeamArgs with T = warps per row, NT = rows per block
+// split: the form with each label line shared by two lanes (pass_line2.cuh)
 bool pass_line_built(int Q0, int Q1, int l1);
-int pass_line_warps(int Q0, int Q1);
-size_t pass_line_smem(int NT, int Q0, int Q1);
-int edp_pass_line_occupancy(int Q0, int Q1, int l1, int threads, size_t smem);
-int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, int threads, size_t smem, cudaStream_t st);
+bool pass_line_split_built(int Q0, int Q1, int l1);
+int pass_line_split_max_lambda();
+int pass_line_warps(int Q0, int Q1, bool split);
+size_t pass_line_smem(int NT, int Q0, int Q1, bool split);
+int edp_pass_line_occupancy(int Q0, int Q1, int l1, bool split, int threads, size_t smem);
+int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, bool split, int threads, size_t smem, cudaStream_t st);
+// per-band stride of the line kernels' record flags and consumed counters
+// (one per warp of the producing / consuming team)
+constexpr int kLineFlagStride = 8;
 
 // one EDP scan pass, one label axis, one warp per row (edp_pass_r1.cu)
 struct PassR1Args {

@@ -283,10 +283,10 @@ __device__ __forceinline__ bool line_band(const TeamArgs &A, const int band, int
         // records, [band][warp] flags and consumed counters
         const int2 *const ll_in = from_ring ? A.ll + (size_t)(band - 1) * ring * Qm : nullptr;
         int2 *const ll_out = to_ring ? A.ll + (size_t)band * ring * Qm : nullptr;
-        const unsigned *const flag_in = from_ring ? A.rflag + (size_t)(band - 1) * kMaxWarps + wt : nullptr;
-        unsigned *const flag_out = to_ring ? A.rflag + (size_t)band * kMaxWarps + wt : nullptr;
-        unsigned *const cons_in = from_ring ? A.cons + (size_t)(band - 1) * kMaxWarps + wt : nullptr;
-        const unsigned *const cons_out = to_ring ? A.cons + (size_t)band * kMaxWarps + wt : nullptr;
+        const unsigned *const flag_in = from_ring ? A.rflag + (size_t)(band - 1) * kLineFlagStride + wt : nullptr;
+        unsigned *const flag_out = to_ring ? A.rflag + (size_t)band * kLineFlagStride + wt : nullptr;
+        unsigned *const cons_in = from_ring ? A.cons + (size_t)(band - 1) * kLineFlagStride + wt : nullptr;
+        const unsigned *const cons_out = to_ring ? A.cons + (size_t)band * kLineFlagStride + wt : nullptr;
         // the test hook hold_band makes one band expect tags no producer writes
         const int tag_in0 = A.tag0 + (band == A.hold_band ? 0x20000000 : 0);
         const int ncol = A.pair ? 2 * W : W;

@@ -199,7 +199,8 @@ def set_tuning(rows_per_block: int = 0, labels_per_lane: int = 0, general_kernel
     general_kernel: 1 = one-axis spaces take the multi-axis kernel, 2 = and
     multi-axis spaces its lane-group form, 3 = two-axis spaces take the
     multi-axis kernel instead of the two-axis line kernel, 4 = two-axis spaces
-    take the line kernel wherever it is built."""
+    take the line kernel wherever it is built, 5 = as 4 with one lane per label
+    line also where lines are split over lane pairs by default (65 x 65)."""
     _check(load().edp_set_tuning(int(rows_per_block), int(labels_per_lane), int(warps_per_row),
                                  int(general_kernel)), "set_tuning")
 

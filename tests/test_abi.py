@@ -59,7 +59,7 @@ def test_host_validation_without_gpu(lib):
     assert a >= 4 * 64 * 48 * 16 * 4 and b > a
     assert edp.status_string(edp.ERR_TIMEOUT) == "EDP_ERR_TIMEOUT"
     assert lib.edp_set_tuning(-1, 0, 0, 0) == edp.ERR_INVALID_ARG
-    assert lib.edp_set_tuning(0, 0, 0, 5) == edp.ERR_INVALID_ARG
+    assert lib.edp_set_tuning(0, 0, 0, 6) == edp.ERR_INVALID_ARG
     assert lib.edp_set_tuning(0, 0, 13, 0) == edp.ERR_INVALID_ARG
     # pass schedule: off, on, or paired when every band is resident (default)
     assert lib.edp_set_pass_pairs(3) == edp.ERR_INVALID_ARG

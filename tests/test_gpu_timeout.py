@@ -1,6 +1,6 @@
 """The timeout path of the bounded waits between row bands, made to run out
 without any fault: the test hook edp_test_hold_band makes the first row of
-one band wait for hand-off records of a tag no producer writes.  The wait
+one band wait for hand-off data no producer publishes.  The wait
 gives up after the spin limit, the launch writes EDP_ERR_TIMEOUT to the
 device status word, every kernel of the solve returns, and the next normal
 solve on the same workspace is bit-exact against the oracle."""
@@ -22,10 +22,12 @@ def _case(kind):
         return synth.workload_motion_320x240(W=24, H=40), 3
     if kind == "line_33":  # two-axis line kernel, 33 x 33 labels
         return synth.workload_motion_320x240(W=24, H=40), 4
+    if kind == "line_65":  # two-axis line kernel, lines split over lane pairs, 65 x 65 labels
+        return synth.workload_motion_640x480(W=12, H=36), 4
     return synth.workload_motion_640x480(W=20, H=36, vmax=4), 0  # multi-axis, 9 x 9 labels
 
 
-@pytest.mark.parametrize("kind", ["one_axis", "multi_axis_33", "line_33", "multi_axis_9"])
+@pytest.mark.parametrize("kind", ["one_axis", "multi_axis_33", "line_33", "line_65", "multi_axis_9"])
 @pytest.mark.parametrize("pairs", [0, 1])
 def test_timeout_sets_status_and_next_solve_is_exact(edp_lib, kind, pairs):
     edp = edp_lib
