@@ -168,6 +168,7 @@ KERNEL_SOURCES = {
     "edp_pass_r1_kernel": ("pass_r1.cuh", "edp_pass_r1.cu", "common.cuh"),
     "edp_pass_team_kernel": ("pass_team.cuh", "edp_pass_team.cu", "common.cuh"),
     "edp_pass_line_kernel": ("pass_line.cuh", "edp_pass_line.cu", "common.cuh"),
+    "edp_pass_line2_kernel": ("pass_line2.cuh", "pass_line.cuh", "edp_pass_line.cu", "common.cuh"),
 }
 
 

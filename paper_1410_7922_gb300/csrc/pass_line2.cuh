@@ -27,14 +27,15 @@
 // 16 lanes of the first halves and the 16 of the second halves fall on
 // different banks.
 //
-// Between blocks the hand-off is a ring of plain 32-bit values in global
-// memory (not {value, tag} words): each warp of the last row of a block
-// stores its values of a column, then one lane publishes the column with a
-// release store of the warp's flag at GPU scope; the first row of the block
-// below acquires the flag in every lane, loads the values (32-bit loads need
-// half the registers of 64-bit ones, which at this kernel's register bound
-// decides whether they stay in flight together) into its own, otherwise
-// unused, mailbox slot, and then runs as every other row.
+// Between blocks the hand-off ships the mailbox slot as it is: a ring of
+// slot images in global memory (the quadrant layout, plain 32-bit values,
+// no {value, tag} words).  Each thread of the last row of a block copies its
+// 16-byte chunks of the outgoing slot there, then one lane per warp
+// publishes them with a release store of the warp's flag at GPU scope; the
+// same thread of the first row of the block below acquires that flag and
+// copies the same chunks into its own, otherwise unused, mailbox slot with
+// asynchronous copies (no registers in flight), and after a team barrier
+// the row runs as every other row.
 #pragma once
 #include "pass_line.cuh"
 
@@ -118,7 +119,31 @@ __device__ __forceinline__ void split_sweeps(int (&h)[N], const bool lo, const i
 // from xa and m_b from xb (shared memory, stride kPQ); the messages this
 // pixel received written to the message arrays, and the two halved sums of
 // Eq. DP_2D_base: S_a into hv (kBig above the lane's n labels), S_b over m_b
-// in xb.
+// in xb.  Two batches are in flight ahead of the arithmetic.
+template <int N, int LB, int CH>
+__device__ __forceinline__ void issue_batch(const int *__restrict__ Mcp, const int *__restrict__ Mdp,
+                                            const bool c_ok, const bool d_ok, const int n, const int b,
+                                            int (&mcv)[CH], int (&mdv)[CH]) {
+#pragma unroll
+    for (int jj = 0; jj < CH; ++jj) {
+        const int i = b * CH + jj;
+        if (i < N && i < n) {
+            const int o = i * LB;
+            mcv[jj] = c_ok ? ld_cs(Mcp + o) : 0;
+            mdv[jj] = d_ok ? ld_cs(Mdp + o) : 0;
+        }
+    }
+}
+template <int N, int LB, int CH>
+__device__ __forceinline__ void front_load(const int *__restrict__ Cp, const int *__restrict__ Mcp,
+                                           const int *__restrict__ Mdp, const bool c_ok, const bool d_ok,
+                                           const int n, int (&hv)[N], int (&mcv)[2][CH], int (&mdv)[2][CH]) {
+    constexpr int NB = (N + CH - 1) / CH;
+#pragma unroll
+    for (int i = 0; i < N; ++i) hv[i] = i < n ? ld_cs(Cp + i * LB) : kBig;
+    issue_batch<N, LB, CH>(Mcp, Mdp, c_ok, d_ok, n, 0, mcv[0], mdv[0]);
+    if (NB > 1) issue_batch<N, LB, CH>(Mcp, Mdp, c_ok, d_ok, n, 1, mcv[1], mdv[1]);
+}
 template <int N, int LB, int CH>
 __device__ __forceinline__ void half_load(const int *__restrict__ Cp, const int *__restrict__ Mcp,
                                           const int *__restrict__ Mdp, int *__restrict__ Map,
@@ -128,24 +153,10 @@ __device__ __forceinline__ void half_load(const int *__restrict__ Cp, const int 
                                           const int q0, int (&hv)[N], int &lmin_a, int &lmin_b,
                                           unsigned long long &key) {
     constexpr int NB = (N + CH - 1) / CH;
-#pragma unroll
-    for (int i = 0; i < N; ++i) hv[i] = i < n ? ld_cs(Cp + i * LB) : kBig;
     int mcv[2][CH], mdv[2][CH];
-    auto issue = [&](const int b, const int k) {
-#pragma unroll
-        for (int jj = 0; jj < CH; ++jj) {
-            const int i = b * CH + jj;
-            if (i < N && i < n) {
-                const int o = i * LB;
-                mcv[k][jj] = c_ok ? ld_cs(Mcp + o) : 0;
-                mdv[k][jj] = d_ok ? ld_cs(Mdp + o) : 0;
-            }
-        }
-    };
-    issue(0, 0);
+    front_load<N, LB, CH>(Cp, Mcp, Mdp, c_ok, d_ok, n, hv, mcv, mdv);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        if (b + 1 < NB) issue(b + 1, (b + 1) & 1);
         const int k = b & 1;
 #pragma unroll
         for (int jj = 0; jj < CH; ++jj) {
@@ -166,21 +177,20 @@ __device__ __forceinline__ void half_load(const int *__restrict__ Cp, const int 
                 lmin_b = min(lmin_b, hb);
             }
         }
+        // the batch after next, into the registers just consumed
+        if (b + 2 < NB) issue_batch<N, LB, CH>(Mcp, Mdp, c_ok, d_ok, n, b + 2, mcv[k], mdv[k]);
     }
 }
 
-// The hand-off values of one half label column (published, so every load
-// returns the value of this column) copied into the own mailbox slot
-// (stride kPQ), all loads in flight at once.
-template <int N, int LB>
-__device__ __forceinline__ void val_copy(const int *__restrict__ rp, int *__restrict__ xb, const int n) {
-    int v[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i < n) v[i] = ld_cg(rp + i * LB);
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i < n) xb[i * kPQ] = v[i];
+// 16-byte asynchronous copy global -> shared (L2 only), and the wait for
+// this thread's copies
+__device__ __forceinline__ void cp_async16(int *sdst, const int *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 }  // namespace line2
@@ -226,10 +236,11 @@ __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, in
         int *const nx_slots = to_mbox ? smem + (size_t)(tm + 1) * TI + KC + XS : nullptr;
         const int *const nx_ctl = to_mbox ? smem + (size_t)(tm + 1) * TI : nullptr;
         const int *const pv_ctl = from_mbox ? smem + (size_t)(tm - 1) * TI : nullptr;
-        // the ring of hand-off values between blocks: [band][ring][Qm] ints
+        // the ring of slot images between blocks: [band][ring][XS] ints; the
+        // team's thread tl moves the 16-byte chunks tl, tl + 32 TW, ...
         int *const llv = reinterpret_cast<int *>(A.ll);
-        const int *const ll_in = from_ring ? llv + (size_t)(band - 1) * ring * Qm : nullptr;
-        int *const ll_out = to_ring ? llv + (size_t)band * ring * Qm : nullptr;
+        const int *const ll_in = from_ring ? llv + (size_t)(band - 1) * ring * XS : nullptr;
+        int *const ll_out = to_ring ? llv + (size_t)band * ring * XS : nullptr;
         const unsigned *const flag_in = from_ring ? A.rflag + (size_t)(band - 1) * kLineFlagStride + wt : nullptr;
         unsigned *const flag_out = to_ring ? A.rflag + (size_t)band * kLineFlagStride + wt : nullptr;
         unsigned *const cons_in = from_ring ? A.cons + (size_t)(band - 1) * kLineFlagStride + wt : nullptr;
@@ -299,8 +310,8 @@ __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, in
                 }
                 __syncwarp();
             } else if (from_ring) {
-                // the producing warp's column s: published flag (acquired by
-                // every lane, which orders its loads of the values after it)
+                // the producing warp's chunks of column s: published flag
+                // (acquired by every lane, which orders its copies after it)
                 while (true) {
                     const bool ok = (int)line2::ld_acq_gpu(flag_in) >= s + 1 + hold;
                     if (__all_sync(kFull, ok)) break;
@@ -312,11 +323,14 @@ __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, in
                     __nanosleep(32);
                 }
                 if (!bad) {
-                    if (colA) line2::val_copy<NA, LB>(ll_in + (size_t)(s % ring) * Qm + q0, Xb + offA, nA);
-                    // the values are in registers or shared memory: the producer may reuse the slot
+                    const int *const src = ll_in + (size_t)(s % ring) * XS;
+                    for (int c = tl; c < XS / 4; c += 32 * TW) line2::cp_async16(Xb + 4 * c, src + 4 * c);
+                    line2::cp_async_wait_all();
+                    // the chunks are in shared memory: the producer may reuse them
                     __syncwarp();
                     if (lane == 0) st_relaxed_gpu(cons_in, (unsigned)(s + 1));
                 }
+                team_sync(tm, TW);  // every warp's chunks of the slot have arrived
             }
             if (!bad && to_mbox) {  // the slot of this column in the team below is free
                 spins = 0;
@@ -338,7 +352,8 @@ __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, in
                 const bool st_a = write_a && has_ma, st_b = write_b && r > 0;
                 line2::half_load<NA, LB, CH>(A.C + pix * Q + q0, Mc + pix * Qm + q0, Md + pix * Qm + q0,
                                              Ma + pix * Qm + q0, Mb + pix * Qm + q0, Xa + offA, Xb + offA, c_ok,
-                                             d_ok, has_ma, r > 0, st_a, st_b, fin, nA, q0, hv, lmin_a, lmin_b, key);
+                                             d_ok, has_ma, r > 0, st_a, st_b, fin, nA, q0, hv, lmin_a, lmin_b,
+                                             key);
                 const int la = min(lmin_a, __shfl_xor_sync(mA, lmin_a, 16));
                 const int lb = min(lmin_b, __shfl_xor_sync(mA, lmin_b, 16));
                 line2::split_sweeps<NA>(hv, lo, lam_a, per_axis ? la + cap_a : kBig, mA);
@@ -423,7 +438,7 @@ __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, in
             }
             team_sync(tm, TW);  // barrier: rows of X_a (and of the outgoing slot) written
 
-            // ---- phase C (last row of the block): m_b as records, column layout ----
+            // ---- phase C (last row of the block): the outgoing slot into the ring ----
             if (to_ring) {
                 spins = 0;
                 const int need = s - ring + 1;
@@ -437,11 +452,10 @@ __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, in
                     }
                     __nanosleep(32);
                 }
-                if (!bad && colA) {
-                    int *const dst = ll_out + (size_t)(s % ring) * Qm + q0;
-#pragma unroll
-                    for (int i = 0; i < NA; ++i)
-                        if (i < nA) __stcg(dst + i * LB, Xb[offA + i * kPQ]);
+                if (!bad) {
+                    int *const dst = ll_out + (size_t)(s % ring) * XS;
+                    for (int c = tl; c < XS / 4; c += 32 * TW)
+                        __stcg(reinterpret_cast<int4 *>(dst) + c, reinterpret_cast<const int4 *>(Xb)[c]);
                 }
                 // publish column s: the warp's stores, then the flag (release at
                 // GPU scope, cumulative over the stores the barrier ordered)
