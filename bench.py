@@ -442,6 +442,15 @@ def time_solve_rows(edp, synth, torch, peak: float):
     out = torch.empty(4, dtype=torch.int64, device="cuda")
     ms = timed(lambda: edp.energy(C, lab, w["space"], w["prior"], out=out))
     rows["energy_450x375_Q64"] = {"ms": ms}
+    # cost volume of the bench workload (5.2 GB written), the first kernel of its step
+    del C
+    w = make_workload(WORKLOAD)
+    I0, I1 = torch.from_numpy(w["I0"]).cuda(), torch.from_numpy(w["I1"]).cuda()
+    C = torch.empty((480, 640, 65 * 65), dtype=torch.int32, device="cuda")
+    ms = timed(lambda: edp.cost_volume(I0, I1, None, w["space"], w["l2"], w["cmax"], out=C), reps=10)
+    rows["cost_volume_640x480_Q65x65"] = {"ms": ms, "write_gbs": C.numel() * 4 / (ms * 1e-3) / 1e9,
+                                          "frac_of_hbm": C.numel() * 4 / (ms * 1e-3) / 1e9 / peak}
+    del C
     return rows
 
 

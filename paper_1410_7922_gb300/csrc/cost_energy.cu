@@ -1,5 +1,7 @@
 // cost_energy.cu -- cost volume (Eq. Cost_value, Eq. Cost_cmp) and energy
 // (Eq. GE_objective_function) kernels, sm_103a.
+#include <cstdint>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -76,7 +78,113 @@ __device__ __forceinline__ void cost_body(const CostArgs &A) {
     }
 }
 
+// C(x, o) of one entry (Eq. Cost_value / Eq. Cost_cmp), as cost_body computes it
+__device__ __forceinline__ int cost_entry(const CostArgs &A, int x, int y, int o0, int o1, int o2) {
+    bool oob1, oob2;
+    if (A.mode == 0) {
+        const int c = cost_term(A.I1, A.I0, A.W, A.H, A.pitch, x, y, o0, o1, A.l2, oob1);
+        return oob1 ? A.cmax : min(c, A.cmax);
+    }
+    if (A.mode == 1) {
+        const int c1 = cost_term(A.I1, A.I0, A.W, A.H, A.pitch, x, y, o0, o1, A.l2, oob1);
+        const int c2 = cost_term(A.I2, A.I0, A.W, A.H, A.pitch, x, y, o2, 0, A.l2, oob2);
+        return (oob1 || oob2) ? A.cmax : min(c1 + c2, A.cmax);
+    }
+    int c1 = cost_term(A.I1, A.I0, A.W, A.H, A.pitch, x, y, o0, o1, A.l2, oob1);
+    int c2 = cost_term(A.I2, A.I0, A.W, A.H, A.pitch, x, y, -o0, -o1, A.l2, oob2);
+    c1 = oob1 ? A.cmax : min(c1, A.cmax);
+    c2 = oob2 ? A.cmax : min(c2, A.cmax);
+    return min(c1, c2);
+}
+
+// Position of one entry of the flat [H][W][Q] array: pixel (x, y) and label
+// coordinates (q0, q1, q2), advanced by mixed-radix increments.
+struct CostPos {
+    int x, y, q0, q1, q2;
+};
+__device__ __forceinline__ void cost_step(CostPos &p, const CostArgs &A, int d0, int d1, int d2, int dx, int dy) {
+    p.q0 += d0;
+    int c = p.q0 >= A.Q0;
+    p.q0 -= c * A.Q0;
+    p.q1 += d1 + c;
+    c = p.q1 >= A.Q1;
+    p.q1 -= c * A.Q1;
+    p.q2 += d2 + c;
+    c = p.q2 >= A.Q2;
+    p.q2 -= c * A.Q2;
+    p.x += dx + c;
+    p.y += dy;
+    if (p.x >= A.W) {
+        p.x -= A.W;
+        ++p.y;
+    }
+}
+
+// The same cost volume with four consecutive entries of the flat array per
+// thread and step, stored as one 16-byte word (the pixel boundaries need not
+// be aligned: Q may be odd).  C must be 16-byte aligned.  The positions of
+// the four entries follow from the first by mixed-radix increments; the pair
+// cost (mode 0) is computed inline, without the per-mode dispatch.
+__device__ __forceinline__ void cost_vec_body(const CostArgs &A) {
+    const long long N = (long long)A.W * A.H * A.Q;
+    const long long nv = N >> 2;
+    const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // per step the flat index advances by 4 stride = sp pixels + st labels
+    const long long es = 4 * stride;
+    const int sp = (int)(es / A.Q), st = (int)(es % A.Q);
+    const int s0 = st % A.Q0, s1 = (st / A.Q0) % A.Q1, s2 = st / (A.Q0 * A.Q1);
+    const int spy = sp / A.W, spx = sp - spy * A.W;
+    CostPos p;
+    {
+        const long long e0 = 4 * k0;
+        const long long pix = e0 / A.Q;
+        const int q = (int)(e0 - pix * A.Q);
+        p.q0 = q % A.Q0;
+        p.q1 = (q / A.Q0) % A.Q1;
+        p.q2 = q / (A.Q0 * A.Q1);
+        p.y = (int)(pix / A.W);
+        p.x = (int)(pix - (long long)p.y * A.W);
+    }
+    const int v1 = A.R >= 2 ? A.vmin[1] : 0, t1 = A.R >= 2 ? A.step[1] : 0;
+    const int v2 = A.R >= 3 ? A.vmin[2] : 0, t2 = A.R >= 3 ? A.step[2] : 0;
+    int4 *const C4 = reinterpret_cast<int4 *>(A.C);
+    for (long long k = k0; k < nv; k += stride) {
+        int v[4];
+        CostPos e = p;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o0 = A.vmin[0] + A.step[0] * e.q0, o1 = v1 + t1 * e.q1;
+            if (A.mode == 0) {
+                const int xs = e.x + o0, ys = e.y + o1;
+                if (xs < 0 || xs >= A.W || ys < 0 || ys >= A.H) {
+                    v[j] = A.cmax;
+                } else {
+                    const int d = abs((int)A.I1[(size_t)ys * A.pitch + xs] - (int)A.I0[(size_t)e.y * A.pitch + e.x]);
+                    v[j] = min(A.l2 == 1 ? d : d * d, A.cmax);
+                }
+            } else {
+                v[j] = cost_entry(A, e.x, e.y, o0, o1, v2 + t2 * e.q2);
+            }
+            if (j < 3) cost_step(e, A, 1, 0, 0, 0, 0);
+        }
+        C4[k] = make_int4(v[0], v[1], v[2], v[3]);
+        cost_step(p, A, s0, s1, s2, spx, spy);
+    }
+    // the last N mod 4 entries
+    if (k0 == 0) {
+        for (long long e = nv * 4; e < N; ++e) {
+            const long long pix = e / A.Q;
+            const int q = (int)(e - pix * A.Q);
+            const int y = (int)(pix / A.W), x = (int)(pix - (long long)y * A.W);
+            const int q0 = q % A.Q0, q1 = (q / A.Q0) % A.Q1, q2 = q / (A.Q0 * A.Q1);
+            A.C[e] = cost_entry(A, x, y, A.vmin[0] + A.step[0] * q0, v1 + t1 * q1, v2 + t2 * q2);
+        }
+    }
+}
+
 __global__ void cost_kernel(CostArgs A) { cost_body(A); }
+__global__ void cost_vec_kernel(CostArgs A) { cost_vec_body(A); }
 
 // one launch for a wave of problems: blockIdx.y selects the problem
 __global__ void cost_batched_kernel(const __grid_constant__ CostBatch B) { cost_body(B.c[blockIdx.y]); }
@@ -93,6 +201,13 @@ int launch_cost_batched(const CostBatch &a, long long max_entries, cudaStream_t 
 int launch_cost(const CostArgs &a, cudaStream_t st) {
     const long long n = (long long)a.W * a.H * a.Q;
     const int threads = 256;
+    if ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0) {  // four entries per thread and step
+        long long blocks = (n / 4 + threads - 1) / threads;
+        if (blocks > 152LL * 8) blocks = 152LL * 8;
+        if (blocks < 1) blocks = 1;
+        cost_vec_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
+        return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    }
     long long blocks = (n + threads - 1) / threads;
     if (blocks > 152LL * 16) blocks = 152LL * 16;
     if (blocks < 1) blocks = 1;

@@ -81,6 +81,50 @@ def test_cost_volume_pitched_rows(edp_lib):
     assert np.array_equal(host(out), want)
 
 
+@pytest.mark.parametrize("case", [
+    ("motion_65x65", sp((65, 65), (-32, -32)), "pair", 1, 20),
+    ("motion_9x7_steps", {"R": 2, "Q": (9, 7), "vmin": (4, -3), "step": (-1, 1)}, "pair", 1, 20),
+    ("stereo_63", sp((63,), (-62,)), "pair", 1, 300),
+    ("stereo_63_sq", sp((63,), (-62,)), "pair", 2, 3000),
+    ("axis3", sp((5, 3, 3), (-2, -1, 0)), "pair_stereo3", 1, 40),
+    ("composite", sp((7, 5), (-3, -2)), "composite", 1, 30),
+])
+@pytest.mark.parametrize("shift", [0, 1, 2, 3])
+def test_cost_volume_vector_and_scalar_forms(edp_lib, case, shift):
+    """The cost volume written four entries per thread (output 16-byte
+    aligned, shift 0; odd Q puts pixel boundaries inside the 16-byte words,
+    and the bytewise form covers inner labels of the pair cost) and one entry
+    per thread (output shifted by 1..3 entries), on a frame whose borders cut
+    the label windows; I1 also from a base that is not 4-byte aligned."""
+    import ctypes
+    name, space, mode, l2, cmax = case
+    rng = np.random.default_rng(len(name) * 7 + shift)
+    H, W, P = 19, 41, 45
+    I0, I1, I2 = (rng.integers(0, 256, size=(H, P)).astype(np.uint8) for _ in range(3))
+    use2 = mode != "pair"
+    want = oracle.cost_volume(I0[:, :W].copy(), I1[:, :W].copy(), I2[:, :W].copy() if use2 else None, space,
+                              l2, cmax, mode)
+    Q = want.shape[2]
+    lib = edp_lib.load()
+    ls = edp_lib.label_space(space)
+    pr = edp_lib.params({"lam": 0, "g": 1}, l2=l2, cmax=cmax, cost_mode=mode)
+    t0, t2 = dev(I0), dev(I2)
+    for i1_off in (0, 1):
+        # I1 from a buffer one byte longer, the image at byte i1_off
+        big1 = np.zeros(H * P + 1, np.uint8)
+        big1[i1_off:i1_off + H * P] = I1.reshape(-1)
+        t1 = dev(big1)
+        buf = torch.full((H * W * Q + 4,), -7, dtype=torch.int32, device="cuda")
+        rc = lib.edp_cost_volume(ctypes.c_void_p(t0.data_ptr()), ctypes.c_void_p(t1.data_ptr() + i1_off),
+                                 ctypes.c_void_p(t2.data_ptr()) if use2 else None, W, H, P, ctypes.byref(ls),
+                                 ctypes.byref(pr), ctypes.c_void_p(buf.data_ptr() + 4 * shift),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0
+        b = host(buf)
+        assert np.array_equal(b[shift:shift + H * W * Q].reshape(H, W, Q), want), (name, shift, i1_off)
+        assert (b[:shift] == -7).all() and (b[shift + H * W * Q:] == -7).all()
+
+
 # --------------------------------------------------------------------------
 # scanline DP
 # --------------------------------------------------------------------------
