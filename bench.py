@@ -77,6 +77,8 @@ def parse_args():
     ap.add_argument("--size", default="", help="WxH: the workload at another image size (profiling runs)")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--net-only", action="store_true",
+                    help="only the proposal network's forward / backward timing (one JSON line; profiling runs)")
     ap.add_argument("--extra", default="", help="comma list of longer side measurements: batched,proposal")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="image scale of the batched workload")
     ap.add_argument("--proposal-pairs", type=int, default=2000, help="training pairs of the proposal network")
@@ -154,6 +156,64 @@ def sums_bytes_per_pass(W: int, H: int, Q: int) -> int:
     """Algorithmic bytes of one scan pass in the paper's sums form: per pixel
     read C(x, .) and the two old sums, write the two new sums, 20 * Q bytes."""
     return 20 * Q * W * H
+
+
+def measured_bf16_peak():
+    """Dense bf16 TFLOP/s measured on this machine (burst: a kernel timed alone)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
+def measure_net(edp, torch, sizes=((1, 480, 640), (8, 240, 320)), reps=10):
+    """Proposal network forward and backward (parameter gradients) on random
+    inputs, with the 32 -> 32 convolutions on the tensor cores and on the
+    CUDA cores; TFLOP/s of the forward's four 32 -> 32 layers against the
+    measured bf16 peak (the forward's other two layers, 5 -> 32 and
+    32 -> 2, run on the CUDA cores inside the same time)."""
+    import statistics
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return statistics.median(ts)
+
+    peak, kind = measured_bf16_peak()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    out_rows = {}
+    for (N, H, W) in sizes:
+        P = (torch.randn(edp.net_param_count(), device="cuda", generator=g) * 0.05).float()
+        x = torch.rand((N, H, W, 5), device="cuda", generator=g).to(torch.bfloat16)
+        tgt = torch.randn((N, H, W, 2), device="cuda", generator=g)
+        ws = edp.net_workspace(N, H, W)
+        r = {}
+        for tc in (True, False):
+            edp.set_net_tensor_cores(tc)
+            out = edp.net_forward(P, x, ws)
+            f = timed(lambda: edp.net_forward(P, x, ws, out=out))
+            b = timed(lambda: edp.net_backward(P, out, tgt, ws))
+            r["tensor_cores" if tc else "cuda_cores"] = {"forward_ms": f, "backward_ms": b,
+                                                         "status": edp.net_device_status(ws)}
+        edp.set_net_tensor_cores(True)
+        flops = 4 * 2 * N * H * W * 32 * 288
+        r["tc_layers_forward_tflop"] = flops / 1e12
+        r["tc_forward_tflops"] = flops / (r["tensor_cores"]["forward_ms"] * 1e-3) / 1e12
+        r["frac_of_bf16_peak"] = r["tc_forward_tflops"] / peak
+        r["bf16_peak_tflops"] = peak
+        r["peak_kind"] = kind
+        out_rows[f"{N}x{H}x{W}"] = r
+        del ws
+    return out_rows
 
 
 def measured_peaks():
@@ -579,6 +639,10 @@ def run_gpu(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.net_only:
+        if rank == 0:
+            print(json.dumps({"proposal_net": measure_net(edp, torch)}), flush=True)
+        return
     j = args.iters
     w = make_workload(args.workload, pair=rank, size=args.size)  # weak scaling: one pair per rank
     H, W = w["I0"].shape
@@ -689,6 +753,7 @@ def run_gpu(args, world, rank, local):
         rows["proposal_640x480_Q65x65_w9"] = measure_proposal(edp, torch, train_pairs=args.row_proposal_pairs,
                                                               eval_pairs=(1000, 1001, 1002, 1003, 1004, 1005),
                                                               reps=1)
+        rows["proposal_net"] = measure_net(edp, torch)
     extra = {}
     if rank == 0:
         for name in [e for e in args.extra.split(",") if e]:

@@ -367,6 +367,19 @@ int edp_net_forward(const float *params, const void *x, int N, int H, int W, flo
  * loss: device float64 [1]. */
 int edp_net_backward(const float *params, const float *out, const float *target, int N, int H, int W, float *grad,
                      double *loss, void *ws, size_t ws_bytes, edp_stream_t stream);
+/* Where the 3x3 convolutions of 32 -> 32 channels run (layers 1-4 forward
+ * and their input gradients): 1 (the default) on the tensor cores
+ * (tcgen05.mma, bf16 operands, float32 accumulation in tensor memory, one
+ * implicit GEMM per 8 x 16 pixel tile: M = 128 pixels, N = 32 channels,
+ * K = 9 x 32), 0 on the CUDA cores (float32 FMA).  The two forms round the
+ * same bf16 products and differ only in the order of the float32 sums.
+ * Returns EDP_ERR_INVALID_ARG unless on is 0 or 1.  Not thread-safe with
+ * concurrent calls. */
+int edp_set_net_tensor_cores(int on);
+/* The network workspace's status word (0, or EDP_ERR_TIMEOUT when a bounded
+ * wait of a tensor-core convolution ran out; cleared by edp_net_forward),
+ * read after the work queued on `stream`.  Synchronises the stream. */
+int edp_net_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stream_t stream);
 /* One Adam step (step >= 1) on the float32 parameters. */
 int edp_net_adam(float *params, const float *grad, float *m, float *v, float lr, float beta1, float beta2, float eps,
                  int step, edp_stream_t stream);

@@ -1501,6 +1501,20 @@ int edp_net_backward(const float *params, const float *out, const float *target,
                : EDP_OK;
 }
 
+int edp_set_net_tensor_cores(int on) {
+    if (on != 0 && on != 1) return EDP_ERR_INVALID_ARG;
+    net_set_tensor_cores(on);
+    return EDP_OK;
+}
+
+int edp_net_get_device_status(const void *ws, size_t ws_bytes, int *status, edp_stream_t stream) {
+    if (!ws || !status || ws_bytes < net_status_offset() + sizeof(int)) return EDP_ERR_INVALID_ARG;
+    const auto *p = static_cast<const unsigned char *>(ws) + net_status_offset();
+    if (cudaMemcpyAsync(status, p, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+        return EDP_ERR_CUDA;
+    return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? EDP_OK : EDP_ERR_CUDA;
+}
+
 int edp_net_adam(float *params, const float *grad, float *m, float *v, float lr, float beta1, float beta2, float eps,
                  int step, edp_stream_t stream) {
     if (!params || !grad || !m || !v || step < 1) return EDP_ERR_INVALID_ARG;

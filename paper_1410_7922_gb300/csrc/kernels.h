@@ -212,6 +212,14 @@ int launch_cost_window(const CostArgs &a, const int *centre, int n, cudaStream_t
 
 // proposal network (net.cu)
 long long net_param_count();
+void net_set_tensor_cores(int on);
+size_t net_status_offset();
+// tensor-core 3x3 convolution of 32 -> 32 channels (net_tc.cu): B image of a
+// layer's weights (flip: the input-gradient form), and the convolution
+// (mode 0: bias + ReLU; mode 2: input gradient masked by act > 0)
+int net_prep_tc_launch(const float *w, int flip, void *out, cudaStream_t st);
+int net_conv_tc_launch(const void *in, int N, int H, int W, const void *wB, const float *bias, int mode, void *out,
+                       const void *act, int *status, cudaStream_t st);
 size_t net_workspace_bytes(long long npix);
 size_t net_activation_offset(long long npix, int layer);
 int net_forward(const float *params, const void *x, int N, int H, int W, float *out, unsigned char *ws,

@@ -385,14 +385,17 @@ long long param_offset(int l) {
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 struct NetLayout {
+    size_t status;        // int: EDP_ERR_TIMEOUT when a tensor-core wait ran out
     size_t act[kLayers];  // bf16 inputs of every layer (act[0] = features)
     size_t g0, g1;        // bf16 gradient ping-pong [N][H][W][32]
     size_t wprep;         // float [9][32][32]
+    size_t wtc;           // bf16 B image of a 32 -> 32 layer for the tensor-core convolution
     size_t end;
 };
 NetLayout net_layout(long long npix) {
     NetLayout L;
-    size_t off = 0;
+    L.status = 0;
+    size_t off = 256;
     for (int l = 0; l < kLayers; ++l) {
         L.act[l] = off;
         off = al(off + (size_t)npix * kChan[l] * 2);
@@ -403,6 +406,8 @@ NetLayout net_layout(long long npix) {
     off = al(off + (size_t)npix * 32 * 2);
     L.wprep = off;
     off = al(off + 9 * 32 * 32 * 4);
+    L.wtc = off;
+    off = al(off + 9 * 32 * 32 * 2);
     L.end = off;
     return L;
 }
@@ -427,7 +432,13 @@ int conv(const __nv_bfloat16 *in, int N, int H, int W, int Cin, int Cout, const 
 }
 }  // namespace
 
+// 32 -> 32 convolutions on the tensor cores (1, the default) or on the CUDA
+// cores (0)
+int g_net_tc = 1;
+
 long long net_param_count() { return param_offset(kLayers); }
+void net_set_tensor_cores(int on) { g_net_tc = on ? 1 : 0; }
+size_t net_status_offset() { return 0; }
 size_t net_workspace_bytes(long long npix) { return net_layout(npix).end; }
 size_t net_activation_offset(long long npix, int layer) { return net_layout(npix).act[layer]; }
 
@@ -435,14 +446,21 @@ int net_forward(const float *params, const void *x, int N, int H, int W, float *
     const long long npix = (long long)N * H * W;
     const NetLayout L = net_layout(npix);
     auto *act0 = reinterpret_cast<__nv_bfloat16 *>(ws + L.act[0]);
+    int *status = reinterpret_cast<int *>(ws + L.status);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return -2;
     if (cudaMemcpyAsync(act0, x, (size_t)npix * 5 * 2, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return -2;
     float *wprep = reinterpret_cast<float *>(ws + L.wprep);
     for (int l = 0; l < kLayers; ++l) {
         const int Ci = kChan[l], Co = kChan[l + 1];
         const float *w = params + param_offset(l);
         const float *b = w + (long long)Co * Ci * 9;
-        net_prep_weights<<<36, 256, 0, st>>>(w, Co, Ci, 0, wprep);
         const auto *in = reinterpret_cast<const __nv_bfloat16 *>(ws + L.act[l]);
+        if (g_net_tc && Ci == 32 && Co == 32 && l < kLayers - 1) {
+            if (net_prep_tc_launch(w, 0, ws + L.wtc, st)) return -2;
+            if (net_conv_tc_launch(in, N, H, W, ws + L.wtc, b, 0, ws + L.act[l + 1], nullptr, status, st)) return -2;
+            continue;
+        }
+        net_prep_weights<<<36, 256, 0, st>>>(w, Co, Ci, 0, wprep);
         if (l < kLayers - 1) {
             auto *o = reinterpret_cast<__nv_bfloat16 *>(ws + L.act[l + 1]);
             if (conv(in, N, H, W, Ci, Co, wprep, b, 0, o, nullptr, nullptr, st)) return -2;
@@ -472,9 +490,16 @@ int net_backward(const float *params, const float *out, const float *target, int
         cudaFuncSetAttribute(net_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
         net_wgrad<<<grid, 288, smw, st>>>(g, xin, N, H, W, Ci, Co, grad + po, grad + po + (long long)Co * Ci * 9);
         if (l > 0) {
-            net_prep_weights<<<36, 256, 0, st>>>(params + po, Co, Ci, 1, wprep);
             // input gradient of layer l = output gradient of layer l-1, masked by its ReLU
-            if (conv(g, N, H, W, Co, Ci, wprep, nullptr, 2, g2, nullptr, xin, st)) return -2;
+            if (g_net_tc && Ci == 32 && Co == 32) {
+                if (net_prep_tc_launch(params + po, 1, ws + L.wtc, st)) return -2;
+                if (net_conv_tc_launch(g, N, H, W, ws + L.wtc, nullptr, 2, g2, xin,
+                                       reinterpret_cast<int *>(ws + L.status), st))
+                    return -2;
+            } else {
+                net_prep_weights<<<36, 256, 0, st>>>(params + po, Co, Ci, 1, wprep);
+                if (conv(g, N, H, W, Co, Ci, wprep, nullptr, 2, g2, nullptr, xin, st)) return -2;
+            }
             auto *t = g;
             g = g2;
             g2 = t;

@@ -1,0 +1,244 @@
+// net_tc.cu -- the 32 -> 32 channel 3x3 convolutions of the proposal network
+// on the 5th-generation tensor cores (tcgen05), sm_103a.
+//
+// Implicit GEMM per tile of 8 x 16 output pixels: D[m][n] = sum over k of
+// A[m][k] B[k][n], M = 128 pixels, N = 32 output channels, K = 9 taps x 32
+// input channels, bf16 operands, float32 accumulation in tensor memory.
+// The tile's input halo (10 x 18 pixels, 32 channels) sits in shared memory
+// in the no-swizzle K-major layout of the MMA operands: for halo row hy,
+// channel chunk c (8 channels = 16 bytes) and halo column hx the chunk is at
+// (hy * 4 + c) * 160 + hx * 16.  Eight consecutive output pixels of a tile
+// row then read eight consecutive 16-byte rows, one core matrix, for every
+// tap: the A operand of tap (dy, dx) is the same buffer seen through a
+// descriptor starting at dy * 640 + dx * 16 (8-row groups 640 bytes apart,
+// channel chunks 160 bytes apart), so no im2col copy is made.  The weights
+// are prepared once per call in the same layout (B: N = 32 rows, K-major).
+// One thread issues the 18 MMAs of a tile (9 taps x 2 chunk pairs of
+// K = 16) and commits them to an mbarrier; the four warps then read the
+// accumulator (warp w owns TMEM lanes 32w .. 32w + 31 = pixels 32w ..) and
+// apply the epilogue: bias and ReLU (forward), or the ReLU mask of the
+// layer below (input gradient).  Every wait is bounded; a wait that runs out
+// sets the status word and the block stops after freeing its tensor memory.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace edp {
+namespace {
+
+constexpr int kTX = 8, kTY = 16;       // output tile (pixels)
+constexpr int kHX = kTX + 2, kHY = kTY + 2;
+constexpr int kChunkStride = kHX * 16;  // bytes between channel chunks of one halo row
+constexpr int kRowStride = 4 * kChunkStride;
+constexpr int kHaloBytes = kHY * kRowStride;          // 11520
+constexpr int kBBytes = 9 * 32 * 32 * 2;              // 18432
+constexpr int kSmem = kBBytes + kHaloBytes + 16;      // + mbarrier, tensor-memory address
+constexpr long long kSpin = 1LL << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor (no swizzle): start address, the byte
+// offset between core matrices along K (lbo) and along M / N (sbo), and the
+// descriptor version bits of this architecture
+__device__ __forceinline__ uint64_t mat_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+// instruction descriptor: D float32, A and B bf16, both K-major, N = 32, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, bool acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"((uint32_t)acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (long long it = 0; it < kSpin; ++it) {
+        uint32_t r;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(r)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (r) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool ok) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ __nv_bfloat16 f2bf(float v) { return __float2bfloat16_rn(v); }
+
+// B image of one layer in global memory, laid out as the kernel's shared
+// memory wants it: tap t, channel chunk c, row group g, row r, 8 bf16 at
+// t * 1024 + c * 256 + g * 64 + r * 8 (elements).  Rows n are output
+// channels, K = (tap, input channel).  flip: the input-gradient form, rows
+// are the layer's input channels and K = (8 - tap, output channel).
+__global__ void net_prep_tc(const float *w, int flip, __nv_bfloat16 *out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 9 * 32 * 32; e += gridDim.x * blockDim.x) {
+        const int tap = e % 9, ci = (e / 9) % 32, co = e / (9 * 32);  // w[co][ci][tap]
+        const int t = flip ? 8 - tap : tap;
+        const int n = flip ? ci : co, k = flip ? co : ci;
+        const size_t o = (size_t)t * 1024 + (k / 8) * 256 + (n / 8) * 64 + (n % 8) * 8 + (k % 8);
+        out[o] = f2bf(w[e]);
+    }
+}
+
+// MODE 0: out = bf16(relu(z + bias)); MODE 2: out = bf16(z if act > 0 else 0)
+template <int MODE>
+__global__ void __launch_bounds__(128) net_conv_tc(const __nv_bfloat16 *in, int N, int H, int W,
+                                                   const __nv_bfloat16 *wB, const float *bias,
+                                                   __nv_bfloat16 *out, const __nv_bfloat16 *act, int *status) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned char *const Bs = sm;
+    unsigned char *const halo = sm + kBBytes;
+    unsigned long long *const mbar = reinterpret_cast<unsigned long long *>(sm + kBBytes + kHaloBytes);
+    uint32_t *const taddr = reinterpret_cast<uint32_t *>(sm + kBBytes + kHaloBytes + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights into shared memory (16-byte copies)
+    for (int e = tid; e < kBBytes / 16; e += blockDim.x)
+        reinterpret_cast<uint4 *>(Bs)[e] = reinterpret_cast<const uint4 *>(wB)[e];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(taddr)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *taddr;
+    const uint32_t sB = smem_u32(Bs), sH = smem_u32(halo), sMbar = smem_u32(mbar);
+
+    const int tx_n = (W + kTX - 1) / kTX, ty_n = (H + kTY - 1) / kTY;
+    const long long tiles = (long long)N * tx_n * ty_n;
+    uint32_t parity = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int n = (int)(tile / ((long long)tx_n * ty_n));
+        const int rem = (int)(tile - (long long)n * tx_n * ty_n);
+        const int y0 = (rem / tx_n) * kTY, x0 = (rem % tx_n) * kTX;
+        // halo: 18 rows x 10 pixels x 4 chunks of 16 bytes, zero outside the image
+        for (int e = tid; e < kHY * kHX * 4; e += blockDim.x) {
+            const int hy = e / (kHX * 4), r2 = e - hy * (kHX * 4), hx = r2 >> 2, c = r2 & 3;
+            const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+            const bool inb = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const __nv_bfloat16 *src = inb ? in + (((size_t)n * H + gy) * W + gx) * 32 + c * 8 : in;
+            cp_async16_zfill(sH + (hy * 4 + c) * kChunkStride + hx * 16, src, inb);
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int dy = t / 3, dx = t % 3;
+#pragma unroll
+                for (int cp = 0; cp < 2; ++cp) {
+                    const uint64_t a = mat_desc(sH + dy * kRowStride + dx * 16 + cp * 2 * kChunkStride,
+                                                kChunkStride, kRowStride);
+                    const uint64_t b = mat_desc(sB + t * 2048 + cp * 1024, 512, 128);
+                    mma_bf16(tmem, a, b, t != 0 || cp != 0);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sMbar)
+                         : "memory");
+        }
+        // the outcome of the wait is made block-uniform before anyone leaves
+        ok = __syncthreads_and(mbar_wait(sMbar, parity)) != 0;
+        parity ^= 1;
+        if (!ok) {
+            if (tid == 0) atomicCAS(status, 0, EDP_ERR_TIMEOUT_CODE);
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int m = 32 * warp + lane, x = x0 + (m % kTX), y = y0 + m / kTX;
+        if (x < W && y < H) {
+            const size_t o = (((size_t)n * H + y) * W + x) * 32;
+            uint32_t pk[16];
+            if (MODE == 0) {
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    const __nv_bfloat16 lo = f2bf(fmaxf(__uint_as_float(v[c]) + bias[c], 0.f));
+                    const __nv_bfloat16 hi = f2bf(fmaxf(__uint_as_float(v[c + 1]) + bias[c + 1], 0.f));
+                    pk[c / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+                }
+            } else {
+                uint4 a4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) a4[q] = reinterpret_cast<const uint4 *>(act + o)[q];
+                const __nv_bfloat16 *ab = reinterpret_cast<const __nv_bfloat16 *>(a4);
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    const __nv_bfloat16 lo = f2bf(__bfloat162float(ab[c]) > 0.f ? __uint_as_float(v[c]) : 0.f);
+                    const __nv_bfloat16 hi =
+                        f2bf(__bfloat162float(ab[c + 1]) > 0.f ? __uint_as_float(v[c + 1]) : 0.f);
+                    pk[c / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                reinterpret_cast<uint4 *>(out + o)[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        }
+        // the accumulator and the halo are rewritten by the next tile
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+}  // namespace
+
+int net_prep_tc_launch(const float *w, int flip, void *out, cudaStream_t st) {
+    net_prep_tc<<<36, 256, 0, st>>>(w, flip, static_cast<__nv_bfloat16 *>(out));
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int net_conv_tc_launch(const void *in, int N, int H, int W, const void *wB, const float *bias, int mode, void *out,
+                       const void *act, int *status, cudaStream_t st) {
+    const long long tiles = (long long)N * ((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long grid = std::min<long long>(tiles, (long long)std::max(1, sms) * 6);
+    const auto *i = static_cast<const __nv_bfloat16 *>(in);
+    const auto *b = static_cast<const __nv_bfloat16 *>(wB);
+    auto *o = static_cast<__nv_bfloat16 *>(out);
+    const auto *a = static_cast<const __nv_bfloat16 *>(act);
+    if (mode == 0) {
+        cudaFuncSetAttribute(net_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        net_conv_tc<0><<<(unsigned)grid, 128, kSmem, st>>>(i, N, H, W, b, bias, o, nullptr, status);
+    } else {
+        cudaFuncSetAttribute(net_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        net_conv_tc<2><<<(unsigned)grid, 128, kSmem, st>>>(i, N, H, W, b, nullptr, o, a, status);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace edp

@@ -105,6 +105,8 @@ def load() -> ctypes.CDLL:
         "edp_net_centres": ([P, I, LS, P, P], I),
         "edp_solve_noalloc": ([P, I, I, LS, PR, P, P], I),
         "edp_noalloc_get_device_status": ([ctypes.POINTER(I), P], I),
+        "edp_set_net_tensor_cores": ([I], I),
+        "edp_net_get_device_status": ([P, SZ, ctypes.POINTER(I), P], I),
         "edp_solve_batched": ([ctypes.POINTER(Problem), I, P, SZ, P], I),
     }
     for name, (args, res) in sig.items():
@@ -127,7 +129,7 @@ def exported_symbols() -> list[str]:
             "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_window_edge_count", "edp_scanline_marginals",
             "edp_set_pass_pairs", "edp_last_pass_launches", "edp_last_pass_kernel", "edp_set_spin_limit",
             "edp_test_hold_band", "edp_set_batch_split", "edp_edge_weights", "edp_solve_weighted",
-            "edp_energy_weighted"]
+            "edp_energy_weighted", "edp_set_net_tensor_cores", "edp_net_get_device_status"]
 
 
 def status_string(code: int) -> str:
@@ -562,6 +564,20 @@ def net_workspace(N: int, H: int, W: int, device="cuda"):
 
 
 NET_CHANNELS = (5, 32, 32, 32, 32, 32, 2)
+
+
+def set_net_tensor_cores(on: bool) -> None:
+    """edp_set_net_tensor_cores: the 32 -> 32 convolutions on the tensor cores
+    (True, the default) or on the CUDA cores (False)."""
+    _check(load().edp_set_net_tensor_cores(1 if on else 0), "set_net_tensor_cores")
+
+
+def net_device_status(ws, stream=None) -> int:
+    """edp_net_get_device_status: the network workspace's status word."""
+    s = ctypes.c_int(-1)
+    _check(load().edp_net_get_device_status(_dev(ws, torch.uint8, "ws"), ws.numel(), ctypes.byref(s), _stream(stream)),
+           "net_get_device_status")
+    return s.value
 
 
 def net_activations(ws, N: int, H: int, W: int) -> list:

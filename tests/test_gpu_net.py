@@ -1,6 +1,7 @@
 """GPU proposal network against its CPU reference (oracle/net.py): forward
 outputs and parameter gradients within 1e-2 relative (bf16 storage on both
-sides, float32 vs float64 accumulation), features, centres, the
+sides, float32 vs float64 accumulation), with the 32 -> 32 convolutions on
+the tensor cores (the default) and on the CUDA cores; features, centres, the
 winner-take-all kernel, and a short training run that lowers the loss."""
 import numpy as np
 import pytest
@@ -58,8 +59,16 @@ def assert_close(got, want, what, mags=None):
 
 
 # 21 x 35: ragged against every conv tile; 96 x 128: several tiles and thread
-# blocks of the conv kernels in both directions
-SIZES = [(2, 21, 35), (2, 96, 128)]
+# blocks of the conv kernels in both directions; 37 x 61: ragged against the
+# tensor-core tile (8 x 16 pixels) in both directions, one image
+SIZES = [(2, 21, 35), (2, 96, 128), (1, 37, 61)]
+
+
+@pytest.fixture(params=[True, False], ids=["tensor_cores", "cuda_cores"])
+def tc(request, edp_lib):
+    edp_lib.set_net_tensor_cores(request.param)
+    yield request.param
+    edp_lib.set_net_tensor_cores(True)
 
 
 def make_setup(edp_lib, N, H, W):
@@ -74,18 +83,30 @@ def make_setup(edp_lib, N, H, W):
 
 
 @pytest.mark.parametrize("N,H,W", SIZES)
-def test_net_forward_parity(edp_lib, N, H, W):
+def test_net_forward_parity(edp_lib, tc, N, H, W):
     ps, P, x, tgt = make_setup(edp_lib, N, H, W)
     want = rnet.forward(x, unflat(P))                       # [N][2][H][W]
     xg = torch.from_numpy(x.transpose(0, 2, 3, 1).astype(np.float32)).to(torch.bfloat16).cuda().contiguous()
     Pg = torch.from_numpy(P).cuda()
     ws = edp_lib.net_workspace(N, H, W)
     out = edp_lib.net_forward(Pg, xg, ws).cpu().numpy().transpose(0, 3, 1, 2)
+    assert edp_lib.net_device_status(ws) == 0
     assert_close(out, want, "forward output")
+    # every hidden activation, one layer at a time: the reference layer run
+    # on the GPU's own input to that layer (as the backward test does), so
+    # that a pre-activation rounded to the other side of zero upstream does
+    # not show as a ReLU decision here
+    acts = [a.float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2)
+            for a in edp_lib.net_activations(ws, N, H, W)]
+    ps_ = unflat(P)
+    for layer in range(1, 6):
+        w, b = ps_[layer - 1]
+        z = rnet.conv3x3(acts[layer - 1], rnet.bf16(w), np.asarray(b, np.float32).astype(np.float64))
+        assert_close(acts[layer], rnet.bf16(np.maximum(z, 0.0)), f"activation {layer}")
 
 
 @pytest.mark.parametrize("N,H,W", SIZES)
-def test_net_backward_parity(edp_lib, N, H, W):
+def test_net_backward_parity(edp_lib, tc, N, H, W):
     """The backward kernels element by element against the reference
     backward run on the activations and output of the GPU's own forward pass
     (read back from the workspace; the forward pass is checked element by
@@ -106,6 +127,7 @@ def test_net_backward_parity(edp_lib, N, H, W):
     assert np.array_equal(acts[0], x)
     out_np = out.cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2)
     g, loss = edp_lib.net_backward(Pg, out, tg, ws)
+    assert edp_lib.net_device_status(ws) == 0
     loss_want, grads = rnet.backward(x, unflat(P), tgt.astype(np.float64), acts=acts, out=out_np)
     assert abs(float(loss.item()) - loss_want) <= RTOL * abs(loss_want)
     gp = unflat(g.cpu().numpy())
