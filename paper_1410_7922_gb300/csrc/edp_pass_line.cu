@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(line2::kMaxThreads, 1) edp_pass_line2_kernel(T
 }
 
 static void *line2_kernel_for(int Q0, int Q1, int l1) {
-    if (l1 == 1 && Q0 == 65 && Q1 == 65) return reinterpret_cast<void *>(edp_pass_line2_kernel<65, 65, 6>);
+    if (l1 == 1 && Q0 == 65 && Q1 == 65) return reinterpret_cast<void *>(edp_pass_line2_kernel<65, 65, 5>);
     return nullptr;
 }
 

@@ -36,7 +36,7 @@ constexpr int kChunkStride = kHX * 16;  // bytes between channel chunks of one h
 constexpr int kRowStride = 4 * kChunkStride;
 constexpr int kHaloBytes = kHY * kRowStride;          // 11520
 constexpr int kBBytes = 9 * 32 * 32 * 2;              // 18432
-constexpr int kSmem = kBBytes + kHaloBytes + 16;      // + mbarrier, tensor-memory address
+constexpr int kSmem = kBBytes + 2 * kHaloBytes + 32;  // + two mbarriers, tensor-memory address
 constexpr long long kSpin = 1LL << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -94,56 +94,126 @@ __global__ void net_prep_tc(const float *w, int flip, __nv_bfloat16 *out) {
     }
 }
 
-// MODE 0: out = bf16(relu(z + bias)); MODE 2: out = bf16(z if act > 0 else 0)
+// Epilogue of one tile: the accumulator (warp w: TMEM lanes 32w.. = pixels
+// 32w..) to bf16 with bias + ReLU (MODE 0) or the ReLU mask of act (MODE 2).
+template <int MODE>
+__device__ __forceinline__ void tile_epilogue(uint32_t acc, int n, int x0, int y0, int H, int W,
+                                              const float *bias, __nv_bfloat16 *out,
+                                              const __nv_bfloat16 *act, int warp, int lane) {
+    uint32_t v[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(acc + ((uint32_t)(32 * warp) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int m = 32 * warp + lane, x = x0 + (m % kTX), y = y0 + m / kTX;
+    if (x >= W || y >= H) return;
+    const size_t o = (((size_t)n * H + y) * W + x) * 32;
+    uint32_t pk[16];
+    if (MODE == 0) {
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+            const __nv_bfloat16 lo = f2bf(fmaxf(__uint_as_float(v[c]) + bias[c], 0.f));
+            const __nv_bfloat16 hi = f2bf(fmaxf(__uint_as_float(v[c + 1]) + bias[c + 1], 0.f));
+            pk[c / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+    } else {
+        uint4 a4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a4[q] = reinterpret_cast<const uint4 *>(act + o)[q];
+        const __nv_bfloat16 *ab = reinterpret_cast<const __nv_bfloat16 *>(a4);
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+            const __nv_bfloat16 lo = f2bf(__bfloat162float(ab[c]) > 0.f ? __uint_as_float(v[c]) : 0.f);
+            const __nv_bfloat16 hi = f2bf(__bfloat162float(ab[c + 1]) > 0.f ? __uint_as_float(v[c + 1]) : 0.f);
+            pk[c / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        reinterpret_cast<uint4 *>(out + o)[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+}
+
+// Asynchronous copies of one tile's halo: 18 rows x 10 pixels x 4 chunks of
+// 16 bytes, zero outside the image.
+__device__ __forceinline__ void halo_load(uint32_t sH, const __nv_bfloat16 *in, int n, int x0, int y0, int H,
+                                          int W, int tid) {
+    for (int e = tid; e < kHY * kHX * 4; e += 128) {
+        const int hy = e / (kHX * 4), r2 = e - hy * (kHX * 4), hx = r2 >> 2, c = r2 & 3;
+        const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+        const bool inb = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const __nv_bfloat16 *src = inb ? in + (((size_t)n * H + gy) * W + gx) * 32 + c * 8 : in;
+        cp_async16_zfill(sH + (hy * 4 + c) * kChunkStride + hx * 16, src, inb);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// MODE 0: out = bf16(relu(z + bias)); MODE 2: out = bf16(z if act > 0 else 0).
+// A block walks its tiles two deep: while the MMAs of tile i run, the halo
+// of tile i + 1 is copied into the other buffer and tile i - 1's
+// accumulator (the other half of the block's 64 tensor-memory columns)
+// goes through the epilogue.
 template <int MODE>
 __global__ void __launch_bounds__(128) net_conv_tc(const __nv_bfloat16 *in, int N, int H, int W,
                                                    const __nv_bfloat16 *wB, const float *bias,
                                                    __nv_bfloat16 *out, const __nv_bfloat16 *act, int *status) {
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char *const Bs = sm;
-    unsigned char *const halo = sm + kBBytes;
-    unsigned long long *const mbar = reinterpret_cast<unsigned long long *>(sm + kBBytes + kHaloBytes);
-    uint32_t *const taddr = reinterpret_cast<uint32_t *>(sm + kBBytes + kHaloBytes + 8);
+    unsigned char *const halo = sm + kBBytes;  // two buffers
+    unsigned long long *const mbar = reinterpret_cast<unsigned long long *>(sm + kBBytes + 2 * kHaloBytes);
+    uint32_t *const taddr = reinterpret_cast<uint32_t *>(sm + kBBytes + 2 * kHaloBytes + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // weights into shared memory (16-byte copies)
     for (int e = tid; e < kBBytes / 16; e += blockDim.x)
         reinterpret_cast<uint4 *>(Bs)[e] = reinterpret_cast<const uint4 *>(wB)[e];
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(taddr)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(taddr)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *taddr;
-    const uint32_t sB = smem_u32(Bs), sH = smem_u32(halo), sMbar = smem_u32(mbar);
+    const uint32_t sB = smem_u32(Bs), sH0 = smem_u32(halo);
 
     const int tx_n = (W + kTX - 1) / kTX, ty_n = (H + kTY - 1) / kTY;
     const long long tiles = (long long)N * tx_n * ty_n;
-    uint32_t parity = 0;
-    bool ok = true;
-    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const int n = (int)(tile / ((long long)tx_n * ty_n));
+    auto coords = [&](long long tile, int &n, int &x0, int &y0) {
+        n = (int)(tile / ((long long)tx_n * ty_n));
         const int rem = (int)(tile - (long long)n * tx_n * ty_n);
-        const int y0 = (rem / tx_n) * kTY, x0 = (rem % tx_n) * kTX;
-        // halo: 18 rows x 10 pixels x 4 chunks of 16 bytes, zero outside the image
-        for (int e = tid; e < kHY * kHX * 4; e += blockDim.x) {
-            const int hy = e / (kHX * 4), r2 = e - hy * (kHX * 4), hx = r2 >> 2, c = r2 & 3;
-            const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-            const bool inb = gy >= 0 && gy < H && gx >= 0 && gx < W;
-            const __nv_bfloat16 *src = inb ? in + (((size_t)n * H + gy) * W + gx) * 32 + c * 8 : in;
-            cp_async16_zfill(sH + (hy * 4 + c) * kChunkStride + hx * 16, src, inb);
-        }
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        y0 = (rem / tx_n) * kTY;
+        x0 = (rem % tx_n) * kTX;
+    };
+    const long long first = blockIdx.x, step = gridDim.x;
+    if (first < tiles) {
+        int n, x0, y0;
+        coords(first, n, x0, y0);
+        halo_load(sH0, in, n, x0, y0, H, W, tid);
+    }
+    bool ok = true;
+    int pn = 0, px0 = 0, py0 = 0;  // the previous tile
+    long long i = 0;
+    for (long long tile = first; tile < tiles; tile += step, ++i) {
+        const int b = (int)(i & 1);
+        int n, x0, y0;
+        coords(tile, n, x0, y0);
+        // this tile's halo has arrived (only its copies are in flight)
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sH = sH0 + b * kHaloBytes, acc = tmem + 32 * b;
 #pragma unroll
             for (int t = 0; t < 9; ++t) {
                 const int dy = t / 3, dx = t % 3;
@@ -151,66 +221,47 @@ __global__ void __launch_bounds__(128) net_conv_tc(const __nv_bfloat16 *in, int 
                 for (int cp = 0; cp < 2; ++cp) {
                     const uint64_t a = mat_desc(sH + dy * kRowStride + dx * 16 + cp * 2 * kChunkStride,
                                                 kChunkStride, kRowStride);
-                    const uint64_t b = mat_desc(sB + t * 2048 + cp * 1024, 512, 128);
-                    mma_bf16(tmem, a, b, t != 0 || cp != 0);
+                    const uint64_t bd = mat_desc(sB + t * 2048 + cp * 1024, 512, 128);
+                    mma_bf16(acc, a, bd, t != 0 || cp != 0);
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sMbar)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(mbar + b))
                          : "memory");
         }
-        // the outcome of the wait is made block-uniform before anyone leaves
-        ok = __syncthreads_and(mbar_wait(sMbar, parity)) != 0;
-        parity ^= 1;
-        if (!ok) {
-            if (tid == 0) atomicCAS(status, 0, EDP_ERR_TIMEOUT_CODE);
-            break;
+        if (i > 0) {
+            // the previous tile's MMAs: done (its halo buffer and accumulator free up)
+            const int pb = b ^ 1;
+            ok = __syncthreads_and(mbar_wait(smem_u32(mbar + pb), (uint32_t)(((i - 1) >> 1) & 1))) != 0;
+            if (!ok) break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        uint32_t v[32];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int m = 32 * warp + lane, x = x0 + (m % kTX), y = y0 + m / kTX;
-        if (x < W && y < H) {
-            const size_t o = (((size_t)n * H + y) * W + x) * 32;
-            uint32_t pk[16];
-            if (MODE == 0) {
-#pragma unroll
-                for (int c = 0; c < 32; c += 2) {
-                    const __nv_bfloat16 lo = f2bf(fmaxf(__uint_as_float(v[c]) + bias[c], 0.f));
-                    const __nv_bfloat16 hi = f2bf(fmaxf(__uint_as_float(v[c + 1]) + bias[c + 1], 0.f));
-                    pk[c / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-                }
-            } else {
-                uint4 a4[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) a4[q] = reinterpret_cast<const uint4 *>(act + o)[q];
-                const __nv_bfloat16 *ab = reinterpret_cast<const __nv_bfloat16 *>(a4);
-#pragma unroll
-                for (int c = 0; c < 32; c += 2) {
-                    const __nv_bfloat16 lo = f2bf(__bfloat162float(ab[c]) > 0.f ? __uint_as_float(v[c]) : 0.f);
-                    const __nv_bfloat16 hi =
-                        f2bf(__bfloat162float(ab[c + 1]) > 0.f ? __uint_as_float(v[c + 1]) : 0.f);
-                    pk[c / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                reinterpret_cast<uint4 *>(out + o)[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        if (tile + step < tiles) {
+            int n2, x2, y2;
+            coords(tile + step, n2, x2, y2);
+            halo_load(sH0 + (b ^ 1) * kHaloBytes, in, n2, x2, y2, H, W, tid);
         }
-        // the accumulator and the halo are rewritten by the next tile
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        if (i > 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tile_epilogue<MODE>(tmem + 32 * (b ^ 1), pn, px0, py0, H, W, bias, out, act, warp, lane);
+        }
+        pn = n;
+        px0 = x0;
+        py0 = y0;
     }
+    if (ok && i > 0) {  // the last tile
+        const int lb = (int)((i - 1) & 1);
+        ok = __syncthreads_and(mbar_wait(smem_u32(mbar + lb), (uint32_t)(((i - 1) >> 1) & 1))) != 0;
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tile_epilogue<MODE>(tmem + 32 * lb, pn, px0, py0, H, W, bias, out, act, warp, lane);
+        }
+    }
+    if (!ok && tid == 0) atomicCAS(status, 0, EDP_ERR_TIMEOUT_CODE);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
 }  // namespace
@@ -226,7 +277,7 @@ int net_conv_tc_launch(const void *in, int N, int H, int W, const void *wB, cons
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long grid = std::min<long long>(tiles, (long long)std::max(1, sms) * 6);
+    const long long grid = std::min<long long>(tiles, (long long)std::max(1, sms) * 5);
     const auto *i = static_cast<const __nv_bfloat16 *>(in);
     const auto *b = static_cast<const __nv_bfloat16 *>(wB);
     auto *o = static_cast<__nv_bfloat16 *>(out);
