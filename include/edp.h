@@ -367,8 +367,9 @@ int edp_net_forward(const float *params, const void *x, int N, int H, int W, flo
  * loss: device float64 [1]. */
 int edp_net_backward(const float *params, const float *out, const float *target, int N, int H, int W, float *grad,
                      double *loss, void *ws, size_t ws_bytes, edp_stream_t stream);
-/* Where the 3x3 convolutions of 32 -> 32 channels run (layers 1-4 forward
- * and their input gradients): 1 (the default) on the tensor cores
+/* Where the 3x3 convolutions of 32 -> 32 channels run (layers 1-4 forward,
+ * their input gradients and their weight gradients): 1 (the default) on the
+ * tensor cores
  * (tcgen05.mma, bf16 operands, float32 accumulation in tensor memory, one
  * implicit GEMM per 8 x 16 pixel tile: M = 128 pixels, N = 32 channels,
  * K = 9 x 32), 0 on the CUDA cores (float32 FMA).  The two forms round the

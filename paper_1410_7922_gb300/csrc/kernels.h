@@ -220,6 +220,10 @@ size_t net_status_offset();
 int net_prep_tc_launch(const float *w, int flip, void *out, cudaStream_t st);
 int net_conv_tc_launch(const void *in, int N, int H, int W, const void *wB, const float *bias, int mode, void *out,
                        const void *act, int *status, cudaStream_t st);
+// weight and bias gradients of a 32 -> 32 layer on the tensor cores (added
+// to dW [32][32][9] and db [32])
+int net_wgrad_tc_launch(const void *g, const void *x, int N, int H, int W, float *dW, float *db, int *status,
+                        cudaStream_t st);
 size_t net_workspace_bytes(long long npix);
 size_t net_activation_offset(long long npix, int layer);
 int net_forward(const float *params, const void *x, int N, int H, int W, float *out, unsigned char *ws,

@@ -486,9 +486,15 @@ int net_backward(const float *params, const float *out, const float *target, int
         const int Ci = kChan[l], Co = kChan[l + 1];
         const long long po = param_offset(l);
         const auto *xin = reinterpret_cast<const __nv_bfloat16 *>(ws + L.act[l]);
-        const size_t smw = (size_t)((kT + 2) * (kT + 2) * Ci + kT * kT * Co) * 4;
-        cudaFuncSetAttribute(net_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
-        net_wgrad<<<grid, 288, smw, st>>>(g, xin, N, H, W, Ci, Co, grad + po, grad + po + (long long)Co * Ci * 9);
+        if (g_net_tc && Ci == 32 && Co == 32) {
+            if (net_wgrad_tc_launch(g, xin, N, H, W, grad + po, grad + po + (long long)Co * Ci * 9,
+                                    reinterpret_cast<int *>(ws + L.status), st))
+                return -2;
+        } else {
+            const size_t smw = (size_t)((kT + 2) * (kT + 2) * Ci + kT * kT * Co) * 4;
+            cudaFuncSetAttribute(net_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+            net_wgrad<<<grid, 288, smw, st>>>(g, xin, N, H, W, Ci, Co, grad + po, grad + po + (long long)Co * Ci * 9);
+        }
         if (l > 0) {
             // input gradient of layer l = output gradient of layer l-1, masked by its ReLU
             if (g_net_tc && Ci == 32 && Co == 32) {

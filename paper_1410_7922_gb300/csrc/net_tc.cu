@@ -1,5 +1,6 @@
 // net_tc.cu -- the 32 -> 32 channel 3x3 convolutions of the proposal network
-// on the 5th-generation tensor cores (tcgen05), sm_103a.
+// and their weight gradients on the 5th-generation tensor cores (tcgen05),
+// sm_103a.
 //
 // Implicit GEMM per tile of 8 x 16 output pixels: D[m][n] = sum over k of
 // A[m][k] B[k][n], M = 128 pixels, N = 32 output channels, K = 9 taps x 32
@@ -264,7 +265,193 @@ __global__ void __launch_bounds__(128) net_conv_tc(const __nv_bfloat16 *in, int 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
+// ---------------------------------------------------------------------------
+// Weight and bias gradients of a 32 -> 32 layer:
+//   dW[co][ci][dy][dx] = sum over pixels p of g[p][co] x[p + (dy-1, dx-1)][ci],
+//   db[co] = sum over p of g[p][co].
+// Per horizontal tap dx one GEMM with K = pixels: D[(dy, ci)][co], M = 128
+// rows = 4 vertical offsets dy (the fourth, dy = 3, is padding and dropped)
+// x 32 input channels, N = 32.  Both operands are MN-major (8 consecutive
+// channels per 16-byte row, one row per pixel).  The A operand is the input
+// halo (19 rows here) seen through a descriptor: channel chunk c of halo row
+// (r + dy) sits at (r + dy) * 640 + c * 160, so the 16 groups (dy, c) are 160
+// bytes apart and the pixels of tile row r 640 bytes apart; the B operand is
+// the tile of g (tile row r, chunk c at r * 512 + c * 128).  Each block
+// accumulates its tiles into three tensor-memory accumulators (one per dx)
+// and adds them to dW at the end; db is summed on the CUDA cores from the
+// same g tiles.
+// ---------------------------------------------------------------------------
+constexpr int kWHY = kTY + 3;                    // halo rows for dy = 0..3
+constexpr int kWHaloBytes = kWHY * kRowStride;   // 12160
+constexpr int kGBytes = kTY * 512;               // 8192
+constexpr int kWStage = kWHaloBytes + kGBytes;   // one buffer: halo + g tile
+constexpr int kWSmem = 2 * kWStage + 32;
+
+__device__ __forceinline__ void wgrad_tile_load(uint32_t sH, uint32_t sG, const __nv_bfloat16 *x,
+                                                const __nv_bfloat16 *g, int n, int x0, int y0, int H, int W,
+                                                int tid) {
+    for (int e = tid; e < kWHY * kHX * 4; e += 128) {
+        const int hy = e / (kHX * 4), r2 = e - hy * (kHX * 4), hx = r2 >> 2, c = r2 & 3;
+        const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+        const bool inb = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const __nv_bfloat16 *src = inb ? x + (((size_t)n * H + gy) * W + gx) * 32 + c * 8 : x;
+        cp_async16_zfill(sH + (hy * 4 + c) * kChunkStride + hx * 16, src, inb);
+    }
+    for (int e = tid; e < kTY * kTX * 4; e += 128) {
+        const int r = e / (kTX * 4), r2 = e - r * (kTX * 4), px = r2 >> 2, c = r2 & 3;
+        const int gy = y0 + r, gx = x0 + px;
+        const bool inb = gy < H && gx < W;
+        const __nv_bfloat16 *src = inb ? g + (((size_t)n * H + gy) * W + gx) * 32 + c * 8 : g;
+        cp_async16_zfill(sG + r * 512 + c * 128 + px * 16, src, inb);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128) net_wgrad_tc(const __nv_bfloat16 *g, const __nv_bfloat16 *x, int N, int H,
+                                                    int W, float *dW, float *db, int *status) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned long long *const mbar = reinterpret_cast<unsigned long long *>(sm + 2 * kWStage);
+    uint32_t *const taddr = reinterpret_cast<uint32_t *>(sm + 2 * kWStage + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(taddr)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *taddr;
+    const uint32_t s0 = smem_u32(sm);
+    // instruction descriptor: as kIdesc with both operands MN-major
+    constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);
+
+    const int tx_n = (W + kTX - 1) / kTX, ty_n = (H + kTY - 1) / kTY;
+    const long long tiles = (long long)N * tx_n * ty_n;
+    auto coords = [&](long long tile, int &n, int &x0, int &y0) {
+        n = (int)(tile / ((long long)tx_n * ty_n));
+        const int rem = (int)(tile - (long long)n * tx_n * ty_n);
+        y0 = (rem / tx_n) * kTY;
+        x0 = (rem % tx_n) * kTX;
+    };
+    const long long first = blockIdx.x, step = gridDim.x;
+    if (first < tiles) {
+        int n, x0, y0;
+        coords(first, n, x0, y0);
+        wgrad_tile_load(s0, s0 + kWHaloBytes, x, g, n, x0, y0, H, W, tid);
+    }
+    float bsum[32];  // db partial sums of this thread's pixel (tile pixel tid)
+#pragma unroll
+    for (int c = 0; c < 32; ++c) bsum[c] = 0.f;
+    bool ok = true;
+    long long i = 0;
+    for (long long tile = first; tile < tiles; tile += step, ++i) {
+        const int b = (int)(i & 1);
+        const uint32_t sH = s0 + b * kWStage, sG = sH + kWHaloBytes;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                for (int k = 0; k < kTY / 2; ++k) {  // 16 pixels (two tile rows) per MMA
+                    const uint64_t a = mat_desc(sH + dx * 16 + k * 2 * kRowStride, kRowStride, kChunkStride);
+                    const uint64_t bd = mat_desc(sG + k * 1024, 512, 128);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + 32 * dx),
+                        "l"(a), "l"(bd), "r"(kIdescMN), "r"((uint32_t)(i > 0 || k > 0)));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(mbar + b))
+                         : "memory");
+        }
+        // db: this thread's pixel of the tile, all 32 channels (zero outside the image)
+        {
+            const unsigned char *gp = sm + b * kWStage + kWHaloBytes + (tid / kTX) * 512 + (tid % kTX) * 16;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(gp + c * 128);
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) bsum[c * 8 + e] += __bfloat162float(h[e]);
+            }
+        }
+        if (i > 0) {
+            ok = __syncthreads_and(mbar_wait(smem_u32(mbar + (b ^ 1)), (uint32_t)(((i - 1) >> 1) & 1))) != 0;
+            if (!ok) break;
+        }
+        if (tile + step < tiles) {
+            int n2, x2, y2;
+            coords(tile + step, n2, x2, y2);
+            const uint32_t nH = s0 + (b ^ 1) * kWStage;
+            wgrad_tile_load(nH, nH + kWHaloBytes, x, g, n2, x2, y2, H, W, tid);
+        }
+    }
+    if (ok && i > 0) {
+        const int lb = (int)((i - 1) & 1);
+        ok = __syncthreads_and(mbar_wait(smem_u32(mbar + lb), (uint32_t)(((i - 1) >> 1) & 1))) != 0;
+    }
+    if (ok && i > 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // warp w reads lanes 32w.. = rows (dy = w, ci = lane); dy = 3 is padding
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            uint32_t v[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(tmem + 32 * dx + ((uint32_t)(32 * warp) << 16)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (warp < 3) {
+                const int ci = lane, tap = warp * 3 + dx;
+#pragma unroll
+                for (int co = 0; co < 32; ++co) atomicAdd(dW + ((size_t)co * 32 + ci) * 9 + tap, __uint_as_float(v[co]));
+            }
+        }
+        // db: reduce the 128 pixels' sums per channel, one atomic per warp and channel
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            float v = bsum[c];
+            for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0) atomicAdd(db + c, v);
+        }
+    }
+    if (!ok && tid == 0) atomicCAS(status, 0, EDP_ERR_TIMEOUT_CODE);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
 }  // namespace
+
+int net_wgrad_tc_launch(const void *g, const void *x, int N, int H, int W, float *dW, float *db, int *status,
+                        cudaStream_t st) {
+    const long long tiles = (long long)N * ((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // four blocks per SM: their tensor memory (128 columns each) fills the SM's 512
+    const long long grid = std::min<long long>(tiles, (long long)std::max(1, sms) * 4);
+    cudaFuncSetAttribute(net_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem);
+    net_wgrad_tc<<<(unsigned)grid, 128, kWSmem, st>>>(static_cast<const __nv_bfloat16 *>(g),
+                                                      static_cast<const __nv_bfloat16 *>(x), N, H, W, dW, db, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
 
 int net_prep_tc_launch(const float *w, int flip, void *out, cudaStream_t st) {
     net_prep_tc<<<36, 256, 0, st>>>(w, flip, static_cast<__nv_bfloat16 *>(out));
