@@ -220,9 +220,13 @@ size_t net_status_offset();
 int net_prep_tc_launch(const float *w, int flip, void *out, cudaStream_t st);
 int net_conv_tc_launch(const void *in, int N, int H, int W, const void *wB, const float *bias, int mode, void *out,
                        const void *act, int *status, cudaStream_t st);
-// weight and bias gradients of a 32 -> 32 layer on the tensor cores (added
-// to dW [32][32][9] and db [32])
-int net_wgrad_tc_launch(const void *g, const void *x, int N, int H, int W, float *dW, float *db, int *status,
+// weight and bias gradients of a 32 -> 32 layer on the tensor cores: each
+// block writes its partial sums to part (net_wgrad_tc_max_blocks() x
+// net_wgrad_tc_part_floats() floats), then a reduction adds them to
+// grad = dW [32][32][9] followed by db [32]
+int net_wgrad_tc_max_blocks();
+int net_wgrad_tc_part_floats();
+int net_wgrad_tc_launch(const void *g, const void *x, int N, int H, int W, float *part, float *grad, int *status,
                         cudaStream_t st);
 size_t net_workspace_bytes(long long npix);
 size_t net_activation_offset(long long npix, int layer);

@@ -51,8 +51,11 @@ __global__ void __launch_bounds__(256) net_conv3x3(const __nv_bfloat16 *in, int 
                                                   __nv_bfloat16 *out_bf, float *out_f,
                                                   const __nv_bfloat16 *act) {
     extern __shared__ float sm[];
+    // the tile's pixels are CP = Cin | 1 floats apart (odd), so that the
+    // lanes of a warp, which read neighbouring pixels, hit distinct banks
+    const int CP = Cin | 1;
     float *ws = sm;                                  // [9][Cin][COUT]
-    float *tile = sm + 9 * Cin * COUT;               // [(kT+2)^2][Cin]
+    float *tile = sm + 9 * Cin * COUT;               // [(kT+2)^2][CP]
     const int n = blockIdx.z;
     const int x0 = blockIdx.x * kT, y0 = blockIdx.y * kT;
     for (int e = threadIdx.x; e < 9 * Cin * COUT; e += blockDim.x) ws[e] = wf[e];
@@ -63,7 +66,7 @@ __global__ void __launch_bounds__(256) net_conv3x3(const __nv_bfloat16 *in, int 
         const int y = y0 + ty - 1, x = x0 + tx - 1;
         float v = 0.f;
         if (y >= 0 && y < H && x >= 0 && x < W) v = bf2f(in[(((size_t)n * H + y) * W + x) * Cin + c]);
-        tile[e] = v;
+        tile[p * CP + c] = v;
     }
     __syncthreads();
     const int lx = threadIdx.x % kT, ly = threadIdx.x / kT;
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(256) net_conv3x3(const __nv_bfloat16 *in, int 
     for (int c = 0; c < COUT; ++c) acc[c] = 0.f;
     for (int dy = 0; dy < 3; ++dy)
         for (int dx = 0; dx < 3; ++dx) {
-            const float *t = tile + ((ly + dy) * TW + (lx + dx)) * Cin;
+            const float *t = tile + ((ly + dy) * TW + (lx + dx)) * CP;
             const float *wt = ws + (dy * 3 + dx) * Cin * COUT;
             for (int ci = 0; ci < Cin; ++ci) {
                 const float v = t[ci];
@@ -103,19 +106,22 @@ __global__ void __launch_bounds__(288) net_wgrad(const __nv_bfloat16 *g, const _
                                                  int Ci, int Co, float *dW, float *db) {
     extern __shared__ float sm[];
     const int TW = kT + 2;
-    float *xt = sm;                        // [(kT+2)^2][Ci]
-    float *gt = sm + TW * TW * Ci;         // [kT*kT][Co]
+    // odd strides between pixels: the threads of a warp read different taps
+    // and channel groups of one pixel without sharing a bank
+    const int CiP = Ci | 1, CoP = Co | 1;
+    float *xt = sm;                        // [(kT+2)^2][CiP]
+    float *gt = sm + TW * TW * CiP;        // [kT*kT][CoP]
     const int n = blockIdx.z;
     const int x0 = blockIdx.x * kT, y0 = blockIdx.y * kT;
     for (int e = threadIdx.x; e < TW * TW * Ci; e += blockDim.x) {
         const int c = e % Ci, p = e / Ci;
         const int yy = y0 + p / TW - 1, xx = x0 + p % TW - 1;
-        xt[e] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? bf2f(x[(((size_t)n * H + yy) * W + xx) * Ci + c]) : 0.f;
+        xt[p * CiP + c] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? bf2f(x[(((size_t)n * H + yy) * W + xx) * Ci + c]) : 0.f;
     }
     for (int e = threadIdx.x; e < kT * kT * Co; e += blockDim.x) {
         const int c = e % Co, p = e / Co;
         const int yy = y0 + p / kT, xx = x0 + p % kT;
-        gt[e] = (yy < H && xx < W) ? bf2f(g[(((size_t)n * H + yy) * W + xx) * Co + c]) : 0.f;
+        gt[p * CoP + c] = (yy < H && xx < W) ? bf2f(g[(((size_t)n * H + yy) * W + xx) * Co + c]) : 0.f;
     }
     __syncthreads();
     const int cig = (Ci + 3) / 4, cog = (Co + 7) / 8;
@@ -130,8 +136,8 @@ __global__ void __launch_bounds__(288) net_wgrad(const __nv_bfloat16 *g, const _
             for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
         for (int p = 0; p < kT * kT; ++p) {
             const int py = p / kT, px = p % kT;
-            const float *xr = xt + ((py + dy) * TW + (px + dx)) * Ci;
-            const float *gr = gt + p * Co;
+            const float *xr = xt + ((py + dy) * TW + (px + dx)) * CiP;
+            const float *gr = gt + p * CoP;
             float xv[4], gv[8];
 #pragma unroll
             for (int a = 0; a < 4; ++a) xv[a] = (ci0 + a < Ci) ? xr[ci0 + a] : 0.f;
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(288) net_wgrad(const __nv_bfloat16 *g, const _
     }
     if (t < Co) {
         float s = 0.f;
-        for (int p = 0; p < kT * kT; ++p) s += gt[p * Co + t];
+        for (int p = 0; p < kT * kT; ++p) s += gt[p * CoP + t];
         atomicAdd(db + t, s);
     }
 }
@@ -390,6 +396,7 @@ struct NetLayout {
     size_t g0, g1;        // bf16 gradient ping-pong [N][H][W][32]
     size_t wprep;         // float [9][32][32]
     size_t wtc;           // bf16 B image of a 32 -> 32 layer for the tensor-core convolution
+    size_t wpart;         // float [blocks][32*32*9 + 32]: per-block weight / bias gradients
     size_t end;
 };
 NetLayout net_layout(long long npix) {
@@ -408,6 +415,8 @@ NetLayout net_layout(long long npix) {
     off = al(off + 9 * 32 * 32 * 4);
     L.wtc = off;
     off = al(off + 9 * 32 * 32 * 2);
+    L.wpart = off;
+    off = al(off + (size_t)net_wgrad_tc_max_blocks() * net_wgrad_tc_part_floats() * 4);
     L.end = off;
     return L;
 }
@@ -415,7 +424,7 @@ NetLayout net_layout(long long npix) {
 int conv(const __nv_bfloat16 *in, int N, int H, int W, int Cin, int Cout, const float *wf, const float *bias, int mode,
          __nv_bfloat16 *out_bf, float *out_f, const __nv_bfloat16 *act, cudaStream_t st) {
     dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT, N);
-    const size_t smem = (size_t)(9 * Cin * Cout + (kT + 2) * (kT + 2) * Cin) * 4;
+    const size_t smem = (size_t)(9 * Cin * Cout + (kT + 2) * (kT + 2) * (Cin | 1)) * 4;
     if (Cout == 32) {
         cudaFuncSetAttribute(net_conv3x3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         net_conv3x3<32><<<grid, kT * kT, smem, st>>>(in, N, H, W, Cin, wf, bias, mode, out_bf, out_f, act);
@@ -487,11 +496,11 @@ int net_backward(const float *params, const float *out, const float *target, int
         const long long po = param_offset(l);
         const auto *xin = reinterpret_cast<const __nv_bfloat16 *>(ws + L.act[l]);
         if (g_net_tc && Ci == 32 && Co == 32) {
-            if (net_wgrad_tc_launch(g, xin, N, H, W, grad + po, grad + po + (long long)Co * Ci * 9,
+            if (net_wgrad_tc_launch(g, xin, N, H, W, reinterpret_cast<float *>(ws + L.wpart), grad + po,
                                     reinterpret_cast<int *>(ws + L.status), st))
                 return -2;
         } else {
-            const size_t smw = (size_t)((kT + 2) * (kT + 2) * Ci + kT * kT * Co) * 4;
+            const size_t smw = (size_t)((kT + 2) * (kT + 2) * (Ci | 1) + kT * kT * (Co | 1)) * 4;
             cudaFuncSetAttribute(net_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
             net_wgrad<<<grid, 288, smw, st>>>(g, xin, N, H, W, Ci, Co, grad + po, grad + po + (long long)Co * Ci * 9);
         }

@@ -307,8 +307,14 @@ __device__ __forceinline__ void wgrad_tile_load(uint32_t sH, uint32_t sG, const 
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+constexpr int kPart = 32 * 32 * 9 + 32;  // floats of one block's partial gradients
+constexpr int kWgradBlocksPerSm = 4;      // their tensor memory (128 columns each) fills the SM's 512
+constexpr int kWgradMaxSms = 256;
+
 __global__ void __launch_bounds__(128) net_wgrad_tc(const __nv_bfloat16 *g, const __nv_bfloat16 *x, int N, int H,
-                                                    int W, float *dW, float *db, int *status) {
+                                                    int W, float *part, int *status) {
+    float *const dW = part + (size_t)blockIdx.x * kPart;  // this block's partial sums: [co][ci][9], then [co]
+    float *const db = dW + 32 * 32 * 9;
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned long long *const mbar = reinterpret_cast<unsigned long long *>(sm + 2 * kWStage);
     uint32_t *const taddr = reinterpret_cast<uint32_t *>(sm + 2 * kWStage + 16);
@@ -418,16 +424,19 @@ __global__ void __launch_bounds__(128) net_wgrad_tc(const __nv_bfloat16 *g, cons
             if (warp < 3) {
                 const int ci = lane, tap = warp * 3 + dx;
 #pragma unroll
-                for (int co = 0; co < 32; ++co) atomicAdd(dW + ((size_t)co * 32 + ci) * 9 + tap, __uint_as_float(v[co]));
+                for (int co = 0; co < 32; ++co) dW[((size_t)co * 32 + ci) * 9 + tap] = __uint_as_float(v[co]);
             }
         }
-        // db: reduce the 128 pixels' sums per channel, one atomic per warp and channel
+        // db: reduce the 128 pixels' sums per channel (warps through shared memory)
+        float *const red = reinterpret_cast<float *>(sm);  // the stage buffers are free now
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
             float v = bsum[c];
             for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-            if (lane == 0) atomicAdd(db + c, v);
+            if (lane == 0) red[warp * 32 + c] = v;
         }
+        __syncthreads();
+        if (tid < 32) db[tid] = red[tid] + red[32 + tid] + red[64 + tid] + red[96 + tid];
     }
     if (!ok && tid == 0) atomicCAS(status, 0, EDP_ERR_TIMEOUT_CODE);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -437,19 +446,34 @@ __global__ void __launch_bounds__(128) net_wgrad_tc(const __nv_bfloat16 *g, cons
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
+// grad[e] += sum over blocks of part[block][e] (blocks that ran no tile
+// wrote nothing and are not counted: nb blocks ran one or more)
+__global__ void net_wgrad_reduce(const float *part, int nb, float *grad) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kPart; e += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)b * kPart + e];
+        grad[e] += s;
+    }
+}
+
 }  // namespace
 
-int net_wgrad_tc_launch(const void *g, const void *x, int N, int H, int W, float *dW, float *db, int *status,
+int net_wgrad_tc_max_blocks() { return kWgradMaxSms * kWgradBlocksPerSm; }
+int net_wgrad_tc_part_floats() { return kPart; }
+
+int net_wgrad_tc_launch(const void *g, const void *x, int N, int H, int W, float *part, float *grad, int *status,
                         cudaStream_t st) {
     const long long tiles = (long long)N * ((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // four blocks per SM: their tensor memory (128 columns each) fills the SM's 512
-    const long long grid = std::min<long long>(tiles, (long long)std::max(1, sms) * 4);
+    const long long grid = std::min<long long>(
+        std::min<long long>(tiles, (long long)std::max(1, sms) * kWgradBlocksPerSm), net_wgrad_tc_max_blocks());
     cudaFuncSetAttribute(net_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem);
     net_wgrad_tc<<<(unsigned)grid, 128, kWSmem, st>>>(static_cast<const __nv_bfloat16 *>(g),
-                                                      static_cast<const __nv_bfloat16 *>(x), N, H, W, dW, db, status);
+                                                      static_cast<const __nv_bfloat16 *>(x), N, H, W, part, status);
+    if (cudaGetLastError() != cudaSuccess) return -2;
+    net_wgrad_reduce<<<(kPart + 255) / 256, 256, 0, st>>>(part, (int)grid, grad);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
