@@ -183,6 +183,40 @@ __device__ __forceinline__ void cost_vec_body(const CostArgs &A) {
     }
 }
 
+// The pair cost (mode 0) of one- and two-axis spaces whose axis 0 holds 32
+// labels or more, one warp per pixel: lane l walks the pixel's labels l,
+// l + 32, ... (consecutive lanes: consecutive labels, so the stores of C and
+// the byte loads of one row of I1 coalesce); the label coordinates advance
+// by 32 with at most one wrap of axis 0 per step.
+__global__ void cost_pix_kernel(CostArgs A) {
+    const int lane = threadIdx.x & 31;
+    const long long npix = (long long)A.W * A.H;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int Q = A.Q, Q0 = A.Q0;
+    const int v0 = A.vmin[0], t0 = A.step[0];
+    const int v1 = A.R >= 2 ? A.vmin[1] : 0, t1 = A.R >= 2 ? A.step[1] : 0;
+    for (long long pix = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; pix < npix; pix += nw) {
+        const int y = (int)(pix / A.W), x = (int)(pix - (long long)y * A.W);
+        const int i0 = A.I0[(size_t)y * A.pitch + x];
+        int q0 = lane, q1 = 0;
+        int *out = A.C + pix * Q + lane;
+        for (int q = lane; q < Q; q += 32, out += 32) {
+            const int xs = x + v0 + t0 * q0, ys = y + v1 + t1 * q1;
+            int c = A.cmax;
+            if ((unsigned)xs < (unsigned)A.W && (unsigned)ys < (unsigned)A.H) {
+                const int d = abs((int)A.I1[(size_t)ys * A.pitch + xs] - i0);
+                c = min(A.l2 == 1 ? d : d * d, A.cmax);
+            }
+            *out = c;
+            q0 += 32;
+            if (q0 >= Q0) {
+                q0 -= Q0;
+                ++q1;
+            }
+        }
+    }
+}
+
 __global__ void cost_kernel(CostArgs A) { cost_body(A); }
 __global__ void cost_vec_kernel(CostArgs A) { cost_vec_body(A); }
 
@@ -201,6 +235,13 @@ int launch_cost_batched(const CostBatch &a, long long max_entries, cudaStream_t 
 int launch_cost(const CostArgs &a, cudaStream_t st) {
     const long long n = (long long)a.W * a.H * a.Q;
     const int threads = 256;
+    if (a.mode == 0 && a.R <= 2 && a.Q0 >= 32) {  // one warp per pixel
+        long long blocks = ((long long)a.W * a.H + 7) / 8;
+        if (blocks > 152LL * 16) blocks = 152LL * 16;
+        if (blocks < 1) blocks = 1;
+        cost_pix_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
+        return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    }
     if ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0) {  // four entries per thread and step
         long long blocks = (n / 4 + threads - 1) / threads;
         if (blocks > 152LL * 8) blocks = 152LL * 8;

@@ -91,11 +91,13 @@ def test_cost_volume_pitched_rows(edp_lib):
 ])
 @pytest.mark.parametrize("shift", [0, 1, 2, 3])
 def test_cost_volume_vector_and_scalar_forms(edp_lib, case, shift):
-    """The cost volume written four entries per thread (output 16-byte
-    aligned, shift 0; odd Q puts pixel boundaries inside the 16-byte words,
-    and the bytewise form covers inner labels of the pair cost) and one entry
-    per thread (output shifted by 1..3 entries), on a frame whose borders cut
-    the label windows; I1 also from a base that is not 4-byte aligned."""
+    """The cost volume in each of its forms: one warp per pixel (the pair
+    cost with 32 or more labels on axis 0, any output alignment: the 65 x 65
+    and Q = 63 cases), four entries per thread (output 16-byte aligned,
+    shift 0; odd Q puts pixel boundaries inside the 16-byte words) and one
+    entry per thread (output shifted by 1..3 entries), on a frame whose
+    borders cut the label windows; I1 also from a base that is not 4-byte
+    aligned."""
     import ctypes
     name, space, mode, l2, cmax = case
     rng = np.random.default_rng(len(name) * 7 + shift)
