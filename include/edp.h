@@ -163,6 +163,18 @@ int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, i
  * 1 or 2.  Not thread-safe with concurrent solves. */
 int edp_set_pass_pairs(int mode);
 
+/* Cost volume of edp_solve_images / edp_solve_images_host.  1: where the
+ * pair cost (Eq. Cost_value, cost_mode pair) of a two-axis label space runs
+ * on the split form of the two-axis line kernel, the scan passes and the
+ * energy compute C(x, q) from the images as they need it and no cost volume
+ * is built (the values are those edp_cost_volume stores).  0 (the default):
+ * the cost volume is always built first (measured faster at 640x480 with
+ * 65 x 65 labels: the scan passes' byte loads of 65 image rows per column
+ * cost more than the cost volume saves).  Results never depend on it.
+ * Returns EDP_ERR_INVALID_ARG unless on is 0 or 1.  Not thread-safe with
+ * concurrent solves. */
+int edp_set_fused_cost(int on);
+
 /* Scan-pass launches of the most recent edp_solve, edp_solve_images or
  * edp_solve_windowed call in this process (2 per iteration for paired
  * sweeps, else 4; 0 before the first solve).  The launches are counted as by

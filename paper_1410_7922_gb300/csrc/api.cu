@@ -25,6 +25,7 @@ int g_force_general = 0; // 1: one-axis problems also take the multi-axis pass k
 int g_generic_team = 0;  // 1: multi-axis problems take the generic team body (tests)
 int g_line_mode = 0;     // two-axis line kernel: 0 where it is faster (65-label lines), 1 off, 2 wherever built
 int g_line_split = 1;    // 65 x 65 labels: lines split over lane pairs (0: one lane per line)
+int g_fused_cost = 0;    // edp_solve_images: the split line kernel computes the pair cost from the images
 int g_pass_pairs = 2;    // P1 + P2 and P3 + P4 as paired sweeps: 0 never, 1 always, 2 when every band is resident
 int g_last_launches = 0; // scan-pass launches of the most recent solve
 const char *g_last_kernel = "";  // scan-pass kernel of the most recent solve
@@ -575,12 +576,48 @@ int set_launch(Args &a, int it, int k, int iters, bool pairs) {
     return pass;
 }
 
-// wh / wv: optional per-edge prior multipliers (one-axis kernel only)
+// The pair cost (Eq. Cost_value) as the split line kernel and the energy
+// kernel compute it from the images, in place of a cost volume.
+struct FusedImages {
+    const uint8_t *I0, *I1;
+    int pitch, v0, v1, t0, t1, cmax, l2;
+};
+FusedImages fused_images(const uint8_t *I0, const uint8_t *I1, int pitch, const edp_label_space *s,
+                         const edp_params *p) {
+    FusedImages f;
+    f.I0 = I0;
+    f.I1 = I1;
+    f.pitch = pitch;
+    f.v0 = s->vmin[0];
+    f.v1 = s->R >= 2 ? s->vmin[1] : 0;
+    f.t0 = s->step[0];
+    f.t1 = s->R >= 2 ? s->step[1] : 0;
+    f.cmax = p->cmax;
+    f.l2 = p->l2;
+    return f;
+}
+
+// wh / wv: optional per-edge prior multipliers (one-axis kernel only);
+// fi: the split line kernel computes the pair cost from these images (C is
+// not read); the caller checks that the plan is that kernel
 int run_solve(const int32_t *C, int W, int H, const Geometry &g, const edp_params *p, int32_t *labels,
-              unsigned char *ws, cudaStream_t st, const uint8_t *wh = nullptr, const uint8_t *wv = nullptr) {
+              unsigned char *ws, cudaStream_t st, const uint8_t *wh = nullptr, const uint8_t *wv = nullptr,
+              const FusedImages *fi = nullptr) {
     SolvePlan P;
     int rc = plan_solve(C, W, H, g, p, labels, ws, &P);
     if (rc) return rc;
+    if (fi) {
+        if (!P.line || !P.split) return EDP_ERR_UNSUPPORTED;
+        P.ta.fI0 = fi->I0;
+        P.ta.fI1 = fi->I1;
+        P.ta.fpitch = fi->pitch;
+        P.ta.fv0 = fi->v0;
+        P.ta.fv1 = fi->v1;
+        P.ta.ft0 = fi->t0;
+        P.ta.ft1 = fi->t1;
+        P.ta.fcmax = fi->cmax;
+        P.ta.fl2 = fi->l2;
+    }
     if (wh && !P.r1 && !P.line && !P.ta.lean) return EDP_ERR_UNSUPPORTED;  // not the lane-group form
     P.o.wh = P.ta.wh = wh;
     P.o.wv = P.ta.wv = wv;
@@ -710,9 +747,21 @@ int run_cost(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, int W, int
 
 int run_energy(const int32_t *C, const int32_t *labels, int W, int H, const edp_label_space *s,
                const edp_params *p, int Q, int64_t *out4, cudaStream_t st, const uint8_t *wh = nullptr,
-               const uint8_t *wv = nullptr) {
+               const uint8_t *wv = nullptr, const FusedImages *fi = nullptr) {
     EnergyArgs a;
     memset(&a, 0, sizeof a);
+    if (fi) {  // the data term from the images (C not read)
+        a.I0 = fi->I0;
+        a.I1 = fi->I1;
+        a.pitch = fi->pitch;
+        a.v0 = fi->v0;
+        a.v1 = fi->v1;
+        a.t0 = fi->t0;
+        a.t1 = fi->t1;
+        a.cmax = fi->cmax;
+        a.l2 = fi->l2;
+        C = nullptr;
+    }
     a.wh = wh;
     a.wv = wv;
     a.C = C;
@@ -761,6 +810,12 @@ int edp_set_tuning(int rows_per_block, int labels_per_lane, int warps_per_row, i
     g_generic_team = general_kernel == 2;
     g_line_mode = general_kernel == 3 ? 1 : (general_kernel >= 4 ? 2 : 0);
     g_line_split = general_kernel == 5 ? 0 : 1;
+    return EDP_OK;
+}
+
+int edp_set_fused_cost(int on) {
+    if (on != 0 && on != 1) return EDP_ERR_INVALID_ARG;
+    g_fused_cost = on;
     return EDP_OK;
 }
 
@@ -1046,9 +1101,17 @@ int edp_solve_images(const uint8_t *I0, const uint8_t *I1, const uint8_t *I2, in
     unsigned char *w = static_cast<unsigned char *>(ws);
     const ImagesLayout L = images_layout(W, H, g.Q, g.R, params->iters);
     int32_t *C = reinterpret_cast<int32_t *>(w + L.C);
-    if ((rc = run_cost(I0, I1, I2, W, H, pitch, space, params, g.Q, C, st))) return rc;
-    if ((rc = run_solve(C, W, H, g, params, labels, w, st))) return rc;
-    if (energy4) rc = run_energy(C, labels, W, H, space, params, g.Q, energy4, st);
+    // the pair cost of a two-axis space on the split line kernel: computed
+    // from the images inside the scan passes and the energy, no cost volume
+    bool fuse = false;
+    if (g_fused_cost && params->cost_mode == 0 && space->R == 2) {
+        SolvePlan P;
+        fuse = plan_solve(C, W, H, g, params, labels, w, &P) == EDP_OK && P.line && P.split;
+    }
+    const FusedImages fi = fused_images(I0, I1, pitch, space, params);
+    if (!fuse && (rc = run_cost(I0, I1, I2, W, H, pitch, space, params, g.Q, C, st))) return rc;
+    if ((rc = run_solve(C, W, H, g, params, labels, w, st, nullptr, nullptr, fuse ? &fi : nullptr))) return rc;
+    if (energy4) rc = run_energy(C, labels, W, H, space, params, g.Q, energy4, st, nullptr, nullptr, fuse ? &fi : nullptr);
     return rc;
 }
 

@@ -284,7 +284,17 @@ __device__ __forceinline__ void energy_body(const EnergyArgs &A) {
         const int x = (int)(i % A.W), y = (int)(i / A.W);
         // labels outside [0, Q) are clamped so that every read stays in bounds
         const int l = min(max(A.labels[i], 0), A.Q - 1);
-        if (A.C) e[0] += A.C[i * A.Q + l];
+        if (A.C) {
+            e[0] += A.C[i * A.Q + l];
+        } else if (A.I1) {  // the pair cost of Eq. Cost_value from the images
+            const int xs = x + A.v0 + A.t0 * (l % A.Q0), ys = y + A.v1 + A.t1 * (l / A.Q0);
+            int c = A.cmax;
+            if ((unsigned)xs < (unsigned)A.W && (unsigned)ys < (unsigned)A.H) {
+                const int d = abs((int)A.I1[(size_t)ys * A.pitch + xs] - (int)A.I0[(size_t)y * A.pitch + x]);
+                c = min(A.l2 == 1 ? d : d * d, A.cmax);
+            }
+            e[0] += c;
+        }
         // per-edge multipliers of the locally adaptive prior (null: all 1)
         if (x + 1 < A.W) e[1] += (A.wh ? A.wh[i] : 1) * prior_v(l, min(max(A.labels[i + 1], 0), A.Q - 1), A);
         if (y + 1 < A.H) e[2] += (A.wv ? A.wv[i] : 1) * prior_v(l, min(max(A.labels[i + A.W], 0), A.Q - 1), A);

@@ -25,8 +25,9 @@ __global__ void __launch_bounds__(line::kMaxThreads, 1) edp_pass_line_kernel(Tea
     }
 }
 
-// lines split over lane pairs; CH: global loads per batch and lane
-template <int LA, int LB, int CH>
+// lines split over lane pairs; CH: global loads per batch and lane; FUSED:
+// the pair cost computed from the images instead of read from C
+template <int LA, int LB, int CH, bool FUSED>
 __global__ void __launch_bounds__(line2::kMaxThreads, 1) edp_pass_line2_kernel(TeamArgs A) {
     extern __shared__ __align__(16) int smem_i[];
     __shared__ int s_band;
@@ -39,12 +40,14 @@ __global__ void __launch_bounds__(line2::kMaxThreads, 1) edp_pass_line2_kernel(T
         __syncthreads();
         const int band = s_band;
         if (band >= A.nbands) break;
-        if (!line2_band<LA, LB, CH>(A, band, smem_i, &s_abort)) return;
+        if (!line2_band<LA, LB, CH, FUSED>(A, band, smem_i, &s_abort)) return;
     }
 }
 
-static void *line2_kernel_for(int Q0, int Q1, int l1) {
-    if (l1 == 1 && Q0 == 65 && Q1 == 65) return reinterpret_cast<void *>(edp_pass_line2_kernel<65, 65, 5>);
+static void *line2_kernel_for(int Q0, int Q1, int l1, bool fused = false) {
+    if (l1 == 1 && Q0 == 65 && Q1 == 65)
+        return fused ? reinterpret_cast<void *>(edp_pass_line2_kernel<65, 65, 5, true>)
+                     : reinterpret_cast<void *>(edp_pass_line2_kernel<65, 65, 5, false>);
     return nullptr;
 }
 
@@ -93,7 +96,7 @@ int edp_pass_line_occupancy(int Q0, int Q1, int l1, bool split, int threads, siz
 }
 
 int launch_edp_pass_line(const TeamArgs &a, int Q0, int Q1, bool split, int threads, size_t smem, cudaStream_t st) {
-    void *k = line_kernel_for(Q0, Q1, a.l1, split);
+    void *k = (split && a.fI1) ? line2_kernel_for(Q0, Q1, a.l1, true) : line_kernel_for(Q0, Q1, a.l1, split);
     if (!k) return -1;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     void *args[] = {const_cast<TeamArgs *>(&a)};

@@ -68,6 +68,11 @@ struct TeamArgs {
     long long spin_limit;
     int hold_band;          // test hook: > 0, the first row of this band waits for records never written
     unsigned long long *trace;  // optional: per band {start ns, end ns, 0, sm id}
+    // split line kernel: the pair cost of Eq. Cost_value computed from the
+    // images (fI1 non-null) instead of read from C: offsets (fv0 + ft0 q0,
+    // fv1 + ft1 q1), truncation fcmax, power fl2
+    const uint8_t *fI0, *fI1;
+    int fpitch, fv0, fv1, ft0, ft1, fcmax, fl2;
 };
 int launch_edp_pass_team(const TeamArgs &a, int threads, size_t smem, cudaStream_t st);
 int edp_pass_team_occupancy(int em, int lean, int win, int threads, size_t smem);
@@ -187,6 +192,9 @@ struct EnergyArgs {
     int lam, g, l1, mode;
     const uint8_t *wh, *wv;  // optional per-edge prior multipliers (null: all 1)
     long long *out4;
+    // C null and I1 non-null: the data term is the pair cost from the images
+    const uint8_t *I0, *I1;
+    int pitch, v0, v1, t0, t1, cmax, l2;
 };
 int launch_energy(const EnergyArgs &a, cudaStream_t st);
 int launch_edge_weights(const uint8_t *I, int W, int H, int pitch, int thresh, int factor, uint8_t *wh, uint8_t *wv,

@@ -134,18 +134,45 @@ __device__ __forceinline__ void issue_batch(const int *__restrict__ Mcp, const i
         }
     }
 }
-template <int N, int LB, int CH>
-__device__ __forceinline__ void front_load(const int *__restrict__ Cp, const int *__restrict__ Mcp,
-                                           const int *__restrict__ Mdp, const bool c_ok, const bool d_ok,
-                                           const int n, int (&hv)[N], int (&mcv)[2][CH], int (&mdv)[2][CH]) {
+// The pair cost of Eq. Cost_value for the lane's half column, computed from
+// the images: label i of the half has I1 row ys0 + t1 i at column col (the
+// lane's axis-0 offset); C = cmax outside the image, else
+// min(|I1 - I0(x)|^l2, cmax) -- the same values the cost kernels store.
+struct FusedCost {
+    const uint8_t *col;  // I1 + the lane's column (read only when col_ok)
+    bool col_ok;
+    int ys0, t1, H, pitch, i0, cmax, l2;
+};
+template <int N, int LB, int CH, bool FUSED>
+__device__ __forceinline__ void front_load(const int *__restrict__ Cp, const FusedCost &fc,
+                                           const int *__restrict__ Mcp, const int *__restrict__ Mdp,
+                                           const bool c_ok, const bool d_ok, const int n, int (&hv)[N],
+                                           int (&mcv)[2][CH], int (&mdv)[2][CH]) {
     constexpr int NB = (N + CH - 1) / CH;
+    if constexpr (FUSED) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) hv[i] = i < n ? ld_cs(Cp + i * LB) : kBig;
+        for (int i = 0; i < N; ++i) {
+            if (i < n) {
+                const int ys = fc.ys0 + fc.t1 * i;
+                int c = fc.cmax;
+                if (fc.col_ok && (unsigned)ys < (unsigned)fc.H) {
+                    const int d = abs((int)fc.col[(size_t)ys * fc.pitch] - fc.i0);
+                    c = min(fc.l2 == 1 ? d : d * d, fc.cmax);
+                }
+                hv[i] = c;
+            } else {
+                hv[i] = kBig;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) hv[i] = i < n ? ld_cs(Cp + i * LB) : kBig;
+    }
     issue_batch<N, LB, CH>(Mcp, Mdp, c_ok, d_ok, n, 0, mcv[0], mdv[0]);
     if (NB > 1) issue_batch<N, LB, CH>(Mcp, Mdp, c_ok, d_ok, n, 1, mcv[1], mdv[1]);
 }
-template <int N, int LB, int CH>
-__device__ __forceinline__ void half_load(const int *__restrict__ Cp, const int *__restrict__ Mcp,
+template <int N, int LB, int CH, bool FUSED>
+__device__ __forceinline__ void half_load(const int *__restrict__ Cp, const FusedCost &fc, const int *__restrict__ Mcp,
                                           const int *__restrict__ Mdp, int *__restrict__ Map,
                                           int *__restrict__ Mbp, const int *__restrict__ xa, int *__restrict__ xb,
                                           const bool c_ok, const bool d_ok, const bool has_ma, const bool mbox,
@@ -154,7 +181,7 @@ __device__ __forceinline__ void half_load(const int *__restrict__ Cp, const int 
                                           unsigned long long &key) {
     constexpr int NB = (N + CH - 1) / CH;
     int mcv[2][CH], mdv[2][CH];
-    front_load<N, LB, CH>(Cp, Mcp, Mdp, c_ok, d_ok, n, hv, mcv, mdv);
+    front_load<N, LB, CH, FUSED>(Cp, fc, Mcp, Mdp, c_ok, d_ok, n, hv, mcv, mdv);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int k = b & 1;
@@ -199,7 +226,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // LB x LA labels (axis 0: LB labels, contiguous; axis 1: LA labels), lines
 // split over lane pairs.  Every thread of the block calls it with the same
 // band; returns false when the pass was aborted (a wait timed out).
-template <int LA, int LB, int CH>
+template <int LA, int LB, int CH, bool FUSED>
 __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, int *smem, volatile int *s_abort) {
     using namespace line;
     using line2::kPQ;
@@ -277,11 +304,11 @@ __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, in
                 const int x2 = incx2 ? xs2 : W - 1 - xs2;
                 const size_t p2 = (size_t)y * W + x2;
                 const bool rc2 = (h2 ? A.read_c2 : A.read_c) && (incx2 ? x2 + 1 < W : x2 - 1 >= 0);
-                const int *const pc = A.C + p2 * Q;
+                const int *const pc = FUSED ? nullptr : A.C + p2 * Q;
                 const int *const pm = (incx2 ? A.M[1] : A.M[0]) + p2 * Qm;
                 const int *const pd = Md + p2 * Qm;
                 for (int o = tl * 32; o < Q; o += 32 * 32 * TW) {
-                    prefetch_line_l2(pc + o);
+                    if (!FUSED) prefetch_line_l2(pc + o);
                     if (rc2) prefetch_line_l2(pm + o);
                     if (d_ok) prefetch_line_l2(pd + o);
                 }
@@ -350,7 +377,21 @@ __device__ __forceinline__ bool line2_band(const TeamArgs &A, const int band, in
             int hv[NA];
             if (!bad && colA) {
                 const bool st_a = write_a && has_ma, st_b = write_b && r > 0;
-                line2::half_load<NA, LB, CH>(A.C + pix * Q + q0, Mc + pix * Qm + q0, Md + pix * Qm + q0,
+                line2::FusedCost fc{};
+                if constexpr (FUSED) {
+                    const int xs = x + A.fv0 + A.ft0 * j;
+                    fc.col_ok = (unsigned)xs < (unsigned)W;
+                    fc.col = A.fI1 + (fc.col_ok ? xs : 0);
+                    fc.ys0 = y + A.fv1 + A.ft1 * 32 * hf;
+                    fc.t1 = A.ft1;
+                    fc.H = H;
+                    fc.pitch = A.fpitch;
+                    fc.i0 = A.fI0[(size_t)y * A.fpitch + x];
+                    fc.cmax = A.fcmax;
+                    fc.l2 = A.fl2;
+                }
+                line2::half_load<NA, LB, CH, FUSED>(FUSED ? nullptr : A.C + pix * Q + q0, fc, Mc + pix * Qm + q0,
+                                                    Md + pix * Qm + q0,
                                              Ma + pix * Qm + q0, Mb + pix * Qm + q0, Xa + offA, Xb + offA, c_ok,
                                              d_ok, has_ma, r > 0, st_a, st_b, fin, nA, q0, hv, lmin_a, lmin_b,
                                              key);

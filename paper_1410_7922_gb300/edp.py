@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
         "edp_set_tuning": ([I, I, I, I], I),
         "edp_set_profile_events": ([P, I], I),
         "edp_set_pass_pairs": ([I], I),
+        "edp_set_fused_cost": ([I], I),
         "edp_last_pass_launches": ([], I),
         "edp_last_pass_kernel": ([], ctypes.c_char_p),
         "edp_set_spin_limit": ([ctypes.c_longlong], I),
@@ -127,7 +128,7 @@ def exported_symbols() -> list[str]:
             "edp_net_adam", "edp_net_features", "edp_net_centres", "edp_solve_noalloc",
             "edp_noalloc_get_device_status", "edp_coarse_labels",
             "edp_net_features_labels", "edp_net_centres_residual", "edp_net_targets", "edp_window_edge_count", "edp_scanline_marginals",
-            "edp_set_pass_pairs", "edp_last_pass_launches", "edp_last_pass_kernel", "edp_set_spin_limit",
+            "edp_set_pass_pairs", "edp_set_fused_cost", "edp_last_pass_launches", "edp_last_pass_kernel", "edp_set_spin_limit",
             "edp_test_hold_band", "edp_set_batch_split", "edp_edge_weights", "edp_solve_weighted",
             "edp_energy_weighted", "edp_set_net_tensor_cores", "edp_net_get_device_status"]
 
@@ -564,6 +565,13 @@ def net_workspace(N: int, H: int, W: int, device="cuda"):
 
 
 NET_CHANNELS = (5, 32, 32, 32, 32, 32, 2)
+
+
+def set_fused_cost(on: bool) -> None:
+    """edp_set_fused_cost: edp_solve_images computes the pair cost from the
+    images inside the split line kernel (True) or always builds the cost
+    volume first (False, the default)."""
+    _check(load().edp_set_fused_cost(1 if on else 0), "set_fused_cost")
 
 
 def set_net_tensor_cores(on: bool) -> None:

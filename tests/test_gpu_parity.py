@@ -510,6 +510,72 @@ def test_solve_images_device_and_host(edp_lib):
     assert edp_lib.get_device_status(ws) == 0
 
 
+@pytest.mark.parametrize("W,H,iters", [(10, 24, 1), (7, 33, 2)])
+def test_solve_images_fused_cost_65x65(edp_lib, W, H, iters):
+    """edp_solve_images on a 65 x 65 motion space (the split line kernel):
+    with the pair cost computed from the images inside the scan passes and
+    the energy, and with the cost volume built first (the default); both
+    equal the oracle's labels and energy.  Also through the C ABI with
+    pitched image rows (pitch > W), and through the host entry point, both
+    fused."""
+    import ctypes
+    w = synth.workload_motion_640x480(W=W, H=H)
+    C = oracle.cost_volume(w["I0"], w["I1"], None, w["space"], w["l2"], w["cmax"])
+    want = oracle.edp(C, w["space"], w["prior"], iters=iters, tier=1)
+    e_want = oracle.energy(C, want, w["space"], w["prior"])
+    try:
+        for fused in (True, False):
+            edp_lib.set_fused_cost(fused)
+            lab, e = edp_lib.solve_images(dev(w["I0"]), dev(w["I1"]), None, w["space"], w["prior"], w["l2"],
+                                          w["cmax"], iters=iters)
+            assert edp_lib.last_pass_kernel() == "edp_pass_line2_kernel"
+            assert np.array_equal(host(lab), want), fused
+            assert tuple(int(v) for v in host(e)) == e_want, fused
+        edp_lib.set_fused_cost(True)
+        # pitched rows: the images inside wider buffers
+        P = W + 5
+        big0 = np.zeros((H, P), np.uint8)
+        big1 = np.full((H, P), 255, np.uint8)
+        big0[:, :W], big1[:, :W] = w["I0"], w["I1"]
+        t0, t1 = dev(big0), dev(big1)
+        ws = edp_lib.workspace(edp_lib.OP_SOLVE_IMAGES, W, H, w["space"], w["prior"], iters)
+        lab = torch.empty((H, W), dtype=torch.int32, device="cuda")
+        e4 = torch.empty(4, dtype=torch.int64, device="cuda")
+        ls = edp_lib.label_space(w["space"])
+        pr = edp_lib.params(w["prior"], l2=w["l2"], cmax=w["cmax"], iters=iters)
+        rc = edp_lib.load().edp_solve_images(ctypes.c_void_p(t0.data_ptr()), ctypes.c_void_p(t1.data_ptr()), None,
+                                             W, H, P, ctypes.byref(ls), ctypes.byref(pr),
+                                             ctypes.c_void_p(lab.data_ptr()), ctypes.c_void_p(e4.data_ptr()),
+                                             ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0
+        assert np.array_equal(host(lab), want)
+        assert tuple(int(v) for v in host(e4)) == e_want
+        hl, he = edp_lib.solve_images_host(w["I0"], w["I1"], None, w["space"], w["prior"], w["l2"], w["cmax"], ws,
+                                           iters=iters)
+        assert np.array_equal(hl, want) and tuple(int(v) for v in he) == e_want
+        assert edp_lib.get_device_status(ws) == 0
+    finally:
+        edp_lib.set_fused_cost(False)
+
+
+def test_solve_images_fused_cost_full_frame(edp_lib):
+    """The 640x480 frame with 65 x 65 labels (the bench's launch shape):
+    fused and unfused solves give the same labels and energy."""
+    w = synth.workload_motion_640x480()
+    I0, I1 = dev(w["I0"]), dev(w["I1"])
+    try:
+        out = {}
+        for fused in (True, False):
+            edp_lib.set_fused_cost(fused)
+            lab, e = edp_lib.solve_images(I0, I1, None, w["space"], w["prior"], w["l2"], w["cmax"], iters=1)
+            out[fused] = (host(lab), tuple(int(v) for v in host(e)))
+        assert np.array_equal(out[True][0], out[False][0])
+        assert out[True][1] == out[False][1]
+    finally:
+        edp_lib.set_fused_cost(False)
+
+
 def test_range_and_argument_errors(edp_lib):
     C = torch.zeros((4, 4, 8), dtype=torch.int32, device="cuda")
     with pytest.raises(edp_lib.EdpError) as ei:
