@@ -61,6 +61,14 @@ def test_host_validation_without_gpu(lib):
     assert lib.edp_set_tuning(-1, 0, 0, 0) == edp.ERR_INVALID_ARG
     assert lib.edp_set_tuning(0, 0, 0, 6) == edp.ERR_INVALID_ARG
     assert lib.edp_set_tuning(0, 0, 13, 0) == edp.ERR_INVALID_ARG
+    # the cost-volume and network switches take 0 or 1 (and are left at their defaults)
+    assert lib.edp_set_fused_cost(2) == edp.ERR_INVALID_ARG
+    assert lib.edp_set_fused_cost(-1) == edp.ERR_INVALID_ARG
+    assert lib.edp_set_net_tensor_cores(2) == edp.ERR_INVALID_ARG
+    edp.set_fused_cost(False)
+    edp.set_net_tensor_cores(True)
+    # the network status reader checks its arguments before touching the device
+    assert lib.edp_net_get_device_status(None, 0, None, None) == edp.ERR_INVALID_ARG
     # pass schedule: off, on, or paired when every band is resident (default)
     assert lib.edp_set_pass_pairs(3) == edp.ERR_INVALID_ARG
     assert lib.edp_set_pass_pairs(-1) == edp.ERR_INVALID_ARG
