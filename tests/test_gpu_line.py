@@ -85,6 +85,21 @@ def test_split_kernel_rows_per_block_and_schedule(edp_lib, rows, pairs):
         assert np.array_equal(got, want), prior
 
 
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 7), (7, 1), (2, 2), (3, 19)])
+def test_split_kernel_degenerate_shapes(edp_lib, W, H):
+    """The split form on degenerate frames: one pixel, one column, one row
+    (a single band, no hand-off), and a ragged narrow strip."""
+    rng = np.random.default_rng(W * 100 + H + 7)
+    C = rng.integers(0, 20, size=(H, W, 65 * 65)).astype(np.int32)
+    for mode in ("joint", "per_axis"):
+        prior = {"lam": 4, "g": 3, "l1": 1, "mode": mode}
+        for iters in (1, 2):
+            want = oracle.edp(C, sp((65, 65)), prior, iters=iters, tier=1)
+            got = edp_lib.solve(dev(C), sp((65, 65)), prior, iters=iters).cpu().numpy()
+            assert edp_lib.last_pass_kernel() == LINE2
+            assert np.array_equal(got, want), (mode, iters)
+
+
 def test_split_kernel_lambda_bound(edp_lib):
     """Above the split form's lambda bound the planner takes the one-lane
     form; both equal the oracle."""

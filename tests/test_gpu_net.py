@@ -60,8 +60,9 @@ def assert_close(got, want, what, mags=None):
 
 # 21 x 35: ragged against every conv tile; 96 x 128: several tiles and thread
 # blocks of the conv kernels in both directions; 37 x 61: ragged against the
-# tensor-core tile (8 x 16 pixels) in both directions, one image
-SIZES = [(2, 21, 35), (2, 96, 128), (1, 37, 61)]
+# tensor-core tile (8 x 16 pixels) in both directions, one image; a single
+# pixel, and three tiny images (one partial tile each)
+SIZES = [(2, 21, 35), (2, 96, 128), (1, 37, 61), (1, 1, 1), (3, 5, 9)]
 
 
 @pytest.fixture(params=[True, False], ids=["tensor_cores", "cuda_cores"])
